@@ -1,0 +1,193 @@
+"""FP64 CPU oracle for model-based AR-OAM inversion (arXiv:2009.10173).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+benchmark's CPU-baseline leg import this package; the product path
+(``paper_2009_10173_gb300``) never does, and the two share no code.
+
+* ``patches``, ``slab``, ``slab_column``, ``slab_time_slice``: the sensor
+  discretisation of Eq. 3 and the per-position model slab of Eq. 4
+  (Methods, Forward modeling), computed in C (``oam_oracle.c``).
+* ``forward`` / ``adjoint``: A and its transpose as lateral correlations of
+  the slab with the volume (Methods, Efficient reconstruction based on
+  scanning symmetries).
+* ``oracle.solvers``: LSQR for Eq. 5 with Eq. 6 (MB-L2) and FISTA for Eq. 5
+  with Eq. 7 (MB-L1), written from the published algorithms the paper names.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``orc_params`` in ``oam_oracle.c``; SI units (m, s, Hz)."""
+
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "focal_m", "aperture_m", "hole_m", "c_mps", "fc_hz", "frac_bw", "trunc_sigma",
+        "dx_m", "dy_m", "dz_m", "z0_rel_m", "fs_hz", "t0_s")] + [
+        (n, ctypes.c_int32) for n in ("n_patches", "px", "py", "nz", "nt", "win")]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER(Params)
+        dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+        ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        i32, f64 = ctypes.c_int32, ctypes.c_double
+        L.orc_patch_count_rings.argtypes = [P]
+        L.orc_patches.argtypes = [P, dp, dp, dp, dp]
+        L.orc_eir.argtypes = [P, f64]
+        L.orc_eir.restype = f64
+        L.orc_eir_dot.argtypes = [P, f64]
+        L.orc_eir_dot.restype = f64
+        L.orc_distance_range.argtypes = [P, ctypes.POINTER(f64), ctypes.POINTER(f64)]
+        L.orc_t0.argtypes = [P, ctypes.POINTER(f64)]
+        L.orc_slab_column.argtypes = [P, f64, i32, i32, i32, dp]
+        L.orc_slab.argtypes = [P, f64, dp]
+        L.orc_slab_time_slice.argtypes = [P, f64, i32, dp]
+        L.orc_forward.argtypes = [dp, i32, i32, i32, i32, i32, dp, dp]
+        L.orc_adjoint.argtypes = [dp, i32, i32, i32, i32, i32, dp, dp]
+        L.orc_forward_at.argtypes = [dp, i32, i32, i32, i32, dp, i32, ip, ip, ip, dp]
+        for f in ("orc_patch_count_rings", "orc_patches", "orc_distance_range", "orc_t0",
+                  "orc_slab_column", "orc_slab", "orc_slab_time_slice", "orc_forward",
+                  "orc_adjoint", "orc_forward_at"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc):
+    if rc < 0:
+        raise OracleError({-1: "invalid argument", -2: "arrival window outside [0, Nt)",
+                           -3: "out of memory"}.get(rc, f"error {rc}"))
+    return rc
+
+
+def params(cfg) -> Params:
+    """Build the oracle's parameter block from a config mapping (SI units)."""
+    p = Params()
+    for name, _ in Params._fields_:
+        v = cfg.get(name, None)
+        if v is None:
+            if name == "t0_s":
+                v = math.nan
+            elif name == "hole_m":
+                v = 0.0
+            elif name == "trunc_sigma":
+                v = 5.0
+            else:
+                raise KeyError(name)
+        setattr(p, name, v)
+    return p
+
+
+def patches(cfg):
+    """Sensor patches (Eq. 3): unit normals (nx, ny, nz) and areas w (m^2)."""
+    p = params(cfg)
+    M = p.n_patches
+    nx, ny, nz, w = (np.zeros(M) for _ in range(4))
+    _check(lib().orc_patches(ctypes.byref(p), nx, ny, nz, w))
+    return nx, ny, nz, w
+
+
+def ring_count(cfg) -> int:
+    p = params(cfg)
+    return _check(lib().orc_patch_count_rings(ctypes.byref(p)))
+
+
+def eir(cfg, tau):
+    p = params(cfg)
+    return np.array([lib().orc_eir(ctypes.byref(p), float(t)) for t in np.ravel(tau)])
+
+
+def eir_dot(cfg, tau):
+    p = params(cfg)
+    return np.array([lib().orc_eir_dot(ctypes.byref(p), float(t)) for t in np.ravel(tau)])
+
+
+def distance_range(cfg):
+    p = params(cfg)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib().orc_distance_range(ctypes.byref(p), ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def t0(cfg) -> float:
+    """Time of sample 0 (explicit, or the automatic rule) after the window check."""
+    p = params(cfg)
+    out = ctypes.c_double()
+    _check(lib().orc_t0(ctypes.byref(p), ctypes.byref(out)))
+    return out.value
+
+
+def slab(cfg, t0_s=None):
+    """Dense slab S[win][win][nz][nt] (Eq. 4), FP64."""
+    p = params(cfg)
+    t = t0(cfg) if t0_s is None else t0_s
+    S = np.zeros((p.win, p.win, p.nz, p.nt))
+    _check(lib().orc_slab(ctypes.byref(p), t, S))
+    return S
+
+
+def slab_column(cfg, b, a, k, t0_s=None):
+    """One slab column S[b, a, k, :] with b, a in [-R, R]."""
+    p = params(cfg)
+    t = t0(cfg) if t0_s is None else t0_s
+    out = np.zeros(p.nt)
+    _check(lib().orc_slab_column(ctypes.byref(p), t, b, a, k, out))
+    return out
+
+
+def slab_time_slice(cfg, n, t0_s=None):
+    """S[:, :, :, n] for every tap and depth."""
+    p = params(cfg)
+    t = t0(cfg) if t0_s is None else t0_s
+    out = np.zeros((p.win, p.win, p.nz))
+    _check(lib().orc_slab_time_slice(ctypes.byref(p), t, int(n), out))
+    return out
+
+
+def forward(S, H):
+    """A H for a dense slab S[win][win][nz][nt] and volume H[py][px][nz]."""
+    S = np.ascontiguousarray(S, np.float64)
+    H = np.ascontiguousarray(H, np.float64)
+    win, _, nz, nt = S.shape
+    py, px, _ = H.shape
+    s = np.zeros((py, px, nt))
+    _check(lib().orc_forward(S, win, nz, nt, py, px, H, s))
+    return s
+
+
+def adjoint(S, s):
+    """A^T s for a dense slab and signals s[py][px][nt]."""
+    S = np.ascontiguousarray(S, np.float64)
+    s = np.ascontiguousarray(s, np.float64)
+    win, _, nz, nt = S.shape
+    py, px, _ = s.shape
+    H = np.zeros((py, px, nz))
+    _check(lib().orc_adjoint(S, win, nz, nt, py, px, s, H))
+    return H
+
+
+def forward_at(slices, H, ys, xs, which):
+    """(A H)[y, x, n_i] at chosen points from time slices of the slab."""
+    slices = np.ascontiguousarray(slices, np.float64)
+    H = np.ascontiguousarray(H, np.float64)
+    win, nz = slices.shape[1], slices.shape[3]
+    py, px, _ = H.shape
+    ys, xs, which = (np.ascontiguousarray(v, np.int32) for v in (ys, xs, which))
+    out = np.zeros(len(ys))
+    _check(lib().orc_forward_at(slices, win, nz, py, px, H, len(ys), ys, xs, which, out))
+    return out

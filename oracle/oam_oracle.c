@@ -1,0 +1,376 @@
+/*
+ * FP64 CPU oracle for model-based AR-OAM inversion (Li et al., arXiv:2009.10173).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg do.  It shares no code, header, table or constant generator
+ * with the CUDA path.
+ *
+ * What it computes, each in the plainest form that follows the paper:
+ *   - the sensor-surface patches of Eq. 3 (sub-elements x_j with areas dx_j),
+ *     laid out as rings uniform in polar angle with 8*u_r patches per ring
+ *     (reading of the unspecified patch layout; axial symmetry, Results);
+ *   - the per-position model slab of Eq. 4 (A_s = sum_j A_j dx_j), with the
+ *     point-voxel reading of Eq. 1: a voxel at distance d from patch j adds
+ *     (dx_j / d) * de/dtau(tau - D_j) to the signal, D_j = fs*(d/c - t0), where
+ *     e is the electrical impulse response (Gaussian-windowed cosine) and the
+ *     time derivative of Eq. 1 is moved onto e (arbitrary units, Eq. 2);
+ *   - the forward operator A and its transpose as lateral correlations of that
+ *     slab with the volume ("two coordinate systems", Efficient reconstruction
+ *     based on scanning symmetries), zero outside the scan and voxel grids.
+ *
+ * Lengths enter in metres and are converted to millimetres so that a weight
+ * dx_j/d_j is in mm.  All arithmetic is IEEE double; the build uses
+ * -ffp-contract=off so that x86 and Arm hosts produce the same bits.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+typedef struct {
+  double focal_m, aperture_m, hole_m, c_mps;
+  double fc_hz, frac_bw, trunc_sigma;
+  double dx_m, dy_m, dz_m, z0_rel_m, fs_hz, t0_s; /* t0_s: NaN = automatic */
+  int32_t n_patches, px, py, nz, nt, win;
+} orc_params;
+
+enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_EWINDOW = -2, ORC_ENOMEM = -3 };
+
+/* ------------------------------------------------------------------------ */
+/* Sensor surface patches (Eq. 3).                                          */
+/* The spherical cap of radius F and aperture D (optional central hole h)   */
+/* spans polar angles [asin(h/2F), asin(D/2F)] about the acoustic axis.     */
+/* Rings are uniform in polar angle (at most M/8 of them); ring r gets 8*u_r patches with */
+/* sum u_r = M/8, each ring at least one unit and the rest shared in        */
+/* proportion to ring area by largest remainder (ties to the inner ring).   */
+/* Patch j: unit normal n_j (pointing from the surface to the focus is -n), */
+/* surface point q_j = -F n_j about the focus, area w_j.                    */
+/* ------------------------------------------------------------------------ */
+int orc_patch_count_rings(const orc_params *p) {
+  double F = p->focal_m, D = p->aperture_m, h = p->hole_m;
+  int M = p->n_patches;
+  if (!(F > 0) || !(D > 0) || !(D < 2 * F) || h < 0 || !(h < D) || M <= 0 || M % 8)
+    return ORC_EINVAL;
+  double tmin = asin(h / (2 * F)), tmax = asin(D / (2 * F));
+  double atot = 2 * M_PI * F * F * (cos(tmin) - cos(tmax));
+  long nr = lround((tmax - tmin) * F * sqrt((double)M / atot));
+  if (nr < 1) nr = 1;
+  if (nr > M / 8) nr = M / 8; /* every ring needs at least one unit of 8 patches */
+  return (int)nr;
+}
+
+int orc_patches(const orc_params *p, double *nx, double *ny, double *nz, double *w) {
+  int nr = orc_patch_count_rings(p);
+  if (nr < 0) return nr;
+  double F = p->focal_m, D = p->aperture_m, h = p->hole_m;
+  int M = p->n_patches, U = M / 8;
+  double tmin = asin(h / (2 * F)), tmax = asin(D / (2 * F));
+  double atot = 2 * M_PI * F * F * (cos(tmin) - cos(tmax));
+  double *ar = malloc(sizeof(double) * nr), *frac = malloc(sizeof(double) * nr);
+  int *u = malloc(sizeof(int) * nr), *bonus = calloc(nr, sizeof(int));
+  if (!ar || !frac || !u || !bonus) { free(ar); free(frac); free(u); free(bonus); return ORC_ENOMEM; }
+  int rest = U - nr, given = 0;
+  for (int r = 0; r < nr; ++r) {
+    double t0 = tmin + (tmax - tmin) * r / nr, t1 = tmin + (tmax - tmin) * (r + 1) / nr;
+    ar[r] = 2 * M_PI * F * F * (cos(t0) - cos(t1));
+    double q = rest * ar[r] / atot;
+    double f = floor(q);
+    u[r] = 1 + (int)f;
+    frac[r] = q - f;
+    given += (int)f;
+  }
+  for (int left = rest - given; left > 0; --left) { /* largest remainder, ties to lower r */
+    int best = -1;
+    for (int r = 0; r < nr; ++r)
+      if (!bonus[r] && (best < 0 || frac[r] > frac[best])) best = r;
+    bonus[best] = 1;
+    u[best] += 1;
+  }
+  int j = 0;
+  for (int r = 0; r < nr; ++r) {
+    double t0 = tmin + (tmax - tmin) * r / nr, t1 = tmin + (tmax - tmin) * (r + 1) / nr;
+    double ct = 0.5 * (cos(t0) + cos(t1));
+    double st = sqrt(1.0 - ct * ct);
+    int n = 8 * u[r];
+    for (int m = 0; m < n; ++m, ++j) {
+      double phi = (m + 0.5) * 2 * M_PI / n;
+      nx[j] = st * cos(phi);
+      ny[j] = st * sin(phi);
+      nz[j] = ct;
+      w[j] = ar[r] / n;
+    }
+  }
+  free(ar); free(frac); free(u); free(bonus);
+  return j; /* == M */
+}
+
+/* ------------------------------------------------------------------------ */
+/* Electrical impulse response and its time derivative, in sample units.    */
+/* e(tau) = exp(-tau^2 / (2 s^2)) cos(w tau), s = fs / (2 pi sf),           */
+/* sf = fc * frac_bw / (2 sqrt(2 ln 2)) (the -6 dB amplitude width of the   */
+/* Gaussian spectrum equals frac_bw * fc), w = 2 pi fc / fs;                 */
+/* zero for |tau| > trunc_sigma * s.                                        */
+/* ------------------------------------------------------------------------ */
+static void eir_consts(const orc_params *p, double *sig, double *om, double *cut) {
+  double sf = p->fc_hz * p->frac_bw / (2.0 * sqrt(2.0 * log(2.0)));
+  *sig = p->fs_hz / (2 * M_PI * sf);
+  *om = 2 * M_PI * p->fc_hz / p->fs_hz;
+  *cut = p->trunc_sigma * (*sig);
+}
+
+double orc_eir(const orc_params *p, double tau) {
+  double s, w, cut;
+  eir_consts(p, &s, &w, &cut);
+  if (fabs(tau) > cut) return 0.0;
+  return exp(-tau * tau / (2 * s * s)) * cos(w * tau);
+}
+
+double orc_eir_dot(const orc_params *p, double tau) {
+  double s, w, cut;
+  eir_consts(p, &s, &w, &cut);
+  if (fabs(tau) > cut) return 0.0;
+  double g = exp(-tau * tau / (2 * s * s));
+  return -g * ((tau / (s * s)) * cos(w * tau) + w * sin(w * tau));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry.  Origin at the focus of the sensor at scan position (0,0), z   */
+/* into depth.  The voxel at tap (b, a), depth k sits at                    */
+/* r = (a dx, b dy, z0_rel + k dz); its distance to patch j is |r - q_j|.   */
+/* ------------------------------------------------------------------------ */
+static double dist(const orc_params *p, double rx, double ry, double rz,
+                   double nx, double ny, double nz) {
+  double F = p->focal_m;
+  double ex = rx + F * nx, ey = ry + F * ny, ez = rz + F * nz;
+  return sqrt(ex * ex + ey * ey + ez * ez);
+}
+
+typedef struct {
+  int M;
+  double *nx, *ny, *nz, *w;
+} patchset;
+
+static int load_patches(const orc_params *p, patchset *ps) {
+  ps->M = p->n_patches;
+  ps->nx = malloc(sizeof(double) * 4 * (size_t)ps->M);
+  if (!ps->nx) return ORC_ENOMEM;
+  ps->ny = ps->nx + ps->M; ps->nz = ps->ny + ps->M; ps->w = ps->nz + ps->M;
+  int r = orc_patches(p, ps->nx, ps->ny, ps->nz, ps->w);
+  if (r < 0) { free(ps->nx); return r; }
+  return ORC_OK;
+}
+
+/* Minimum and maximum distance over every slab voxel and patch. */
+int orc_distance_range(const orc_params *p, double *dmin, double *dmax) {
+  patchset ps;
+  int rc = load_patches(p, &ps);
+  if (rc) return rc;
+  int R = (p->win - 1) / 2, W = p->win;
+  double lo = INFINITY, hi = -INFINITY;
+#pragma omp parallel for reduction(min : lo) reduction(max : hi) schedule(static)
+  for (int t = 0; t < W * W; ++t) {
+    int b = t / W - R, a = t % W - R;
+    for (int k = 0; k < p->nz; ++k)
+      for (int j = 0; j < ps.M; ++j) {
+        double d = dist(p, a * p->dx_m, b * p->dy_m, p->z0_rel_m + k * p->dz_m,
+                        ps.nx[j], ps.ny[j], ps.nz[j]);
+        if (d < lo) lo = d;
+        if (d > hi) hi = d;
+      }
+  }
+  free(ps.nx);
+  *dmin = lo; *dmax = hi;
+  return ORC_OK;
+}
+
+/* Time origin.  The paper does not state one; sample n is at time
+ * t0 + n/fs with t0 = (floor(fs dmin / c - T s) - 2) / fs, and the window
+ * must hold the latest arrival: fs (dmax/c - t0) + T s < Nt. */
+int orc_t0(const orc_params *p, double *t0) {
+  if (p->win < 1 || p->win % 2 == 0 || p->nz < 1 || p->nt < 1 || !(p->fs_hz > 0) ||
+      !(p->c_mps > 0) || !(p->trunc_sigma > 0) || !(p->fc_hz > 0) || !(p->frac_bw > 0))
+    return ORC_EINVAL;
+  double dmin, dmax, s, w, cut;
+  int rc = orc_distance_range(p, &dmin, &dmax);
+  if (rc) return rc;
+  eir_consts(p, &s, &w, &cut);
+  double t = isnan(p->t0_s) ? (floor(p->fs_hz * dmin / p->c_mps - cut) - 2.0) / p->fs_hz : p->t0_s;
+  if (p->fs_hz * (dmin / p->c_mps - t) - cut < 0) return ORC_EWINDOW;
+  if (p->fs_hz * (dmax / p->c_mps - t) + cut >= p->nt) return ORC_EWINDOW;
+  *t0 = t;
+  return ORC_OK;
+}
+
+/* Accumulate one voxel's signal (Eq. 3 summed over patches) into out[0..nt). */
+static void voxel_signal(const orc_params *p, const patchset *ps, double t0,
+                         double rx, double ry, double rz, double *out) {
+  double s, w, cut;
+  eir_consts(p, &s, &w, &cut);
+  for (int j = 0; j < ps->M; ++j) {
+    double d = dist(p, rx, ry, rz, ps->nx[j], ps->ny[j], ps->nz[j]);
+    double Dj = p->fs_hz * (d / p->c_mps - t0);
+    double wt = ps->w[j] / d * 1e3; /* mm^2 / mm */
+    int n0 = (int)ceil(Dj - cut), n1 = (int)floor(Dj + cut);
+    if (n0 < 0) n0 = 0;
+    if (n1 > p->nt - 1) n1 = p->nt - 1;
+    for (int n = n0; n <= n1; ++n) out[n] += wt * orc_eir_dot(p, n - Dj);
+  }
+}
+
+/* One slab column S[b, a, k, 0..nt) (Eq. 4). */
+int orc_slab_column(const orc_params *p, double t0, int b, int a, int k, double *out) {
+  patchset ps;
+  int rc = load_patches(p, &ps);
+  if (rc) return rc;
+  memset(out, 0, sizeof(double) * p->nt);
+  voxel_signal(p, &ps, t0, a * p->dx_m, b * p->dy_m, p->z0_rel_m + k * p->dz_m, out);
+  free(ps.nx);
+  return ORC_OK;
+}
+
+/* Whole slab S[win][win][nz][nt]. */
+int orc_slab(const orc_params *p, double t0, double *S) {
+  patchset ps;
+  int rc = load_patches(p, &ps);
+  if (rc) return rc;
+  int R = (p->win - 1) / 2, W = p->win;
+  size_t nt = p->nt;
+  memset(S, 0, sizeof(double) * (size_t)W * W * p->nz * nt);
+#pragma omp parallel for schedule(dynamic)
+  for (int c = 0; c < W * W * p->nz; ++c) {
+    int t = c / p->nz, k = c % p->nz;
+    int b = t / W - R, a = t % W - R;
+    voxel_signal(p, &ps, t0, a * p->dx_m, b * p->dy_m, p->z0_rel_m + k * p->dz_m, S + (size_t)c * nt);
+  }
+  free(ps.nx);
+  return ORC_OK;
+}
+
+/* Slab at one time sample n for every tap and depth: out[win][win][nz]. */
+int orc_slab_time_slice(const orc_params *p, double t0, int n, double *out) {
+  patchset ps;
+  int rc = load_patches(p, &ps);
+  if (rc) return rc;
+  int R = (p->win - 1) / 2, W = p->win;
+  double s, w, cut;
+  eir_consts(p, &s, &w, &cut);
+#pragma omp parallel for schedule(dynamic)
+  for (int c = 0; c < W * W * p->nz; ++c) {
+    int t = c / p->nz, k = c % p->nz;
+    int b = t / W - R, a = t % W - R;
+    double acc = 0;
+    for (int j = 0; j < ps.M; ++j) {
+      double d = dist(p, a * p->dx_m, b * p->dy_m, p->z0_rel_m + k * p->dz_m, ps.nx[j], ps.ny[j], ps.nz[j]);
+      double tau = n - p->fs_hz * (d / p->c_mps - t0);
+      if (fabs(tau) <= cut) acc += ps.w[j] / d * 1e3 * orc_eir_dot(p, tau);
+    }
+    out[c] = acc;
+  }
+  free(ps.nx);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward operator A (Eq. 4 applied through the scanning symmetry):        */
+/*   s[y][x][n] = sum_{b,a,k} S[b,a,k,n] H[y+b][x+a][k],                    */
+/* H = 0 outside the grid.  Layouts: H[py][px][nz], s[py][px][nt].          */
+/* Columns that are zero outside [first,last] contribute exact zeros, so    */
+/* the loop visits only that range (no change to any sum).                  */
+/* ------------------------------------------------------------------------ */
+static void column_ranges(const double *S, size_t ncol, int nt, int *first, int *last) {
+  for (size_t c = 0; c < ncol; ++c) {
+    const double *col = S + c * nt;
+    int f = nt, l = -1;
+    for (int n = 0; n < nt; ++n)
+      if (col[n] != 0.0) { if (f == nt) f = n; l = n; }
+    first[c] = f; last[c] = l;
+  }
+}
+
+int orc_forward(const double *S, int win, int nz, int nt, int py, int px, const double *H, double *s) {
+  int R = (win - 1) / 2;
+  size_t ncol = (size_t)win * win * nz;
+  int *first = malloc(sizeof(int) * ncol), *last = malloc(sizeof(int) * ncol);
+  if (!first || !last) { free(first); free(last); return ORC_ENOMEM; }
+  column_ranges(S, ncol, nt, first, last);
+#pragma omp parallel for schedule(dynamic)
+  for (int pos = 0; pos < py * px; ++pos) {
+    int y = pos / px, x = pos % px;
+    double *out = s + (size_t)pos * nt;
+    for (int n = 0; n < nt; ++n) out[n] = 0.0;
+    for (int b = -R; b <= R; ++b) {
+      if (y + b < 0 || y + b >= py) continue;
+      for (int a = -R; a <= R; ++a) {
+        if (x + a < 0 || x + a >= px) continue;
+        const double *h = H + ((size_t)(y + b) * px + (x + a)) * nz;
+        for (int k = 0; k < nz; ++k) {
+          size_t c = ((size_t)(b + R) * win + (a + R)) * nz + k;
+          const double *col = S + c * nt;
+          for (int n = first[c]; n <= last[c]; ++n) out[n] += col[n] * h[k];
+        }
+      }
+    }
+  }
+  free(first); free(last);
+  return ORC_OK;
+}
+
+/* Transpose: H[y][x][k] = sum_{b,a,n} S[b,a,k,n] s[y-b][x-a][n]. */
+int orc_adjoint(const double *S, int win, int nz, int nt, int py, int px, const double *s, double *H) {
+  int R = (win - 1) / 2;
+  size_t ncol = (size_t)win * win * nz;
+  int *first = malloc(sizeof(int) * ncol), *last = malloc(sizeof(int) * ncol);
+  if (!first || !last) { free(first); free(last); return ORC_ENOMEM; }
+  column_ranges(S, ncol, nt, first, last);
+#pragma omp parallel for schedule(dynamic)
+  for (int pos = 0; pos < py * px; ++pos) {
+    int y = pos / px, x = pos % px;
+    double *out = H + (size_t)pos * nz;
+    for (int k = 0; k < nz; ++k) out[k] = 0.0;
+    for (int b = -R; b <= R; ++b) {
+      if (y - b < 0 || y - b >= py) continue;
+      for (int a = -R; a <= R; ++a) {
+        if (x - a < 0 || x - a >= px) continue;
+        const double *sig = s + ((size_t)(y - b) * px + (x - a)) * nt;
+        for (int k = 0; k < nz; ++k) {
+          size_t c = ((size_t)(b + R) * win + (a + R)) * nz + k;
+          const double *col = S + c * nt;
+          double acc = 0.0;
+          for (int n = first[c]; n <= last[c]; ++n) acc += col[n] * sig[n];
+          out[k] += acc;
+        }
+      }
+    }
+  }
+  free(first); free(last);
+  return ORC_OK;
+}
+
+/* Forward output at chosen (position, sample) pairs, from time slices of the
+ * slab: s[y][x][n] = sum_{b,a,k} slice_n[b][a][k] H[y+b][x+a][k].  slices
+ * holds one [win][win][nz] slice per entry of which[]. */
+int orc_forward_at(const double *slices, int win, int nz, int py, int px, const double *H,
+                   int count, const int *ys, const int *xs, const int *which, double *out) {
+  int R = (win - 1) / 2;
+  for (int i = 0; i < count; ++i) {
+    const double *sl = slices + (size_t)which[i] * win * win * nz;
+    double acc = 0.0;
+    int y = ys[i], x = xs[i];
+    for (int b = -R; b <= R; ++b) {
+      if (y + b < 0 || y + b >= py) continue;
+      for (int a = -R; a <= R; ++a) {
+        if (x + a < 0 || x + a >= px) continue;
+        const double *h = H + ((size_t)(y + b) * px + (x + a)) * nz;
+        const double *c = sl + ((size_t)(b + R) * win + (a + R)) * nz;
+        for (int k = 0; k < nz; ++k) acc += c[k] * h[k];
+      }
+    }
+    out[i] = acc;
+  }
+  return ORC_OK;
+}
