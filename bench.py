@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark: model-based AR-OAM reconstructions per second on GB300.
+
+One step = one full reconstruction of a 200x200-position scan (200x200x300
+voxels, 1024 samples, 61x61 slab window): build the model slab on the
+device, run 50 LSQR iterations (MB-L2) and 100 FISTA iterations (MB-L1,
+20 power iterations for L, lambda = 1e-3 max|A^T s|, non-negative) on
+signals already resident in HBM.  value = volumes/s over all ranks.
+
+Each rank reconstructs its own seeded volume (independent replicas, weak
+scaling); there is no data-path collective.  ``--impl reference`` times the
+FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LSQR/FISTA volumes/s and A+A^T TFLOP/s at <=1e-3 rel err vs FP64; p50/p99"
+WORKLOAD = "volume_200x200x300"
+LSQR_ITERS, FISTA_ITERS, POWER_ITERS, LAMBDA_REL = 50, 100, 20, 1e-3
+# operator applications per step: LSQR 1 + 2*50; FISTA 2*20 power + 1 lambda + 2*100
+OPS_PER_STEP = (1 + 2 * LSQR_ITERS) + (2 * POWER_ITERS + 1 + 2 * FISTA_ITERS)
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16x3"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def config_dict(prec_name):
+    from paper_2009_10173_gb300 import configs
+    c = configs.VOLUME_200
+    return {"workload": WORKLOAD, "scan": f"{c['py']}x{c['px']} positions at {c['dx_m']*1e6:g} um",
+            "voxels": f"{c['py']}x{c['px']}x{c['nz']} ({c['dx_m']*1e6:g} um lateral, {c['dz_m']*1e6:g} um axial)",
+            "nt": c["nt"], "fs_hz": c["fs_hz"], "slab_window": f"{c['win']}x{c['win']}",
+            "sensor": "F=4 mm, D=3 mm, 2000 patches, EIR 30 MHz 100% BW", "lsqr_iters": LSQR_ITERS,
+            "fista_iters": FISTA_ITERS, "power_iters": POWER_ITERS, "lambda_rel": LAMBDA_REL, "nonneg": True,
+            "phantom": "seeded vessel tree + 50 microspheres, 20 dB Gaussian noise", "precision": prec_name,
+            "step": "slab build + 50 LSQR + 100 FISTA (+20 power iterations) per volume",
+            "l2": "inputs larger than L2 (164 MB signals) and a 256 MB L2 flush between timed steps",
+            "parallelism": "independent replicas (one volume per GPU per step)"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (SM clock, reasons) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample():
+    """Time the FP64 oracle on a bounded sample of the workload and scale it
+    to one full reconstruction.  Sample: the full workload's depths (300) and
+    samples (1024) on a 40x40-position scan with an 11x11 slab window; the
+    slab cost scales per column, the operator cost per algorithmic flop."""
+    import numpy as np
+
+    import oracle
+    from paper_2009_10173_gb300 import configs, inputs
+    full = configs.VOLUME_200
+    samp = configs.scaled(full, px=40, py=40, win=11)
+    t = time.perf_counter()
+    t0 = oracle.t0(samp)
+    S = oracle.slab(samp, t0)
+    t_slab = time.perf_counter() - t
+    nnz_col = (S != 0).sum(axis=3).sum(axis=2)  # [win][win]
+    R = 5
+    flops = 0.0
+    for b in range(-R, R + 1):
+        for a in range(-R, R + 1):
+            flops += 2.0 * (40 - abs(b)) * (40 - abs(a)) * nnz_col[b + R, a + R]
+    H = inputs.phantom(samp, 1, kind="spheres", count=8)
+    t = time.perf_counter()
+    s = oracle.forward(S, H)
+    oracle.adjoint(S, s)
+    t_ops = time.perf_counter() - t
+    rate = 2 * flops / t_ops  # flop/s of the direct FP64 operators
+    cols_full = full["win"] ** 2 * full["nz"]
+    cols_samp = samp["win"] ** 2 * samp["nz"]
+    slab_full = t_slab * cols_full / cols_samp
+    return dict(t_slab=t_slab, t_ops=t_ops, rate=rate, slab_full=slab_full, flops_sample=flops)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def cpu_baseline_entry(flops_per_op):
+    m = oracle_sample()
+    per_volume = m["slab_full"] + OPS_PER_STEP * flops_per_op / m["rate"]
+    return {"value": 1.0 / per_volume, "unit": "volumes/s", "cores": int(os.environ.get("OMP_NUM_THREADS", cpu_cores())),
+            "kind": "oracle",
+            "sample": (f"FP64 oracle: slab of a 40x40-position, 11x11-window, 300-depth, 1024-sample grid "
+                       f"({m['t_slab']:.1f} s) and one direct A + A^T on it ({m['t_ops']:.1f} s, "
+                       f"{m['rate']/1e9:.2f} GFLOP/s); scaled to the full volume by slab columns "
+                       f"({m['slab_full']:.0f} s) and by algorithmic flops ({OPS_PER_STEP} operator "
+                       f"applications of {flops_per_op:.3e} flop)"),
+            "seconds_per_volume": per_volume}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2009_10173_gb300 import configs
+    full = configs.VOLUME_200
+    times, vals = [], []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        m = oracle_sample()
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            times.append(dt)
+            vals.append(m)
+    # Full-size algorithmic flops: the band width grows with lateral offset, so
+    # take the mean nonzero count of a spread of full-size oracle slab columns.
+    R = 30
+    t0 = oracle.t0(full)
+    widths = []
+    for (b, a) in ((0, 0), (0, 10), (10, 10), (0, 20), (20, 20), (0, 30), (30, 30), (15, 25)):
+        for k in (0, 100, 200, 299):
+            widths.append(int((oracle.slab_column(full, b, a, k, t0) != 0).sum()))
+    mean_w = float(np.mean(widths))
+    flops_full = 0.0
+    for b in range(-R, R + 1):
+        for a in range(-R, R + 1):
+            flops_full += 2.0 * (200 - abs(b)) * (200 - abs(a)) * full["nz"] * mean_w
+    m = vals[-1]
+    per_volume = m["slab_full"] + OPS_PER_STEP * flops_full / m["rate"]
+    value = 1.0 / per_volume
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "volumes/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict("fp64 oracle (direct form)"),
+            "cpu_baseline": {"value": value, "unit": "volumes/s", "kind": "oracle", "cores": cpu_cores(),
+                             "sample": "each step: FP64 oracle slab (40x40 scan, 11x11 window, 300 depths, 1024 "
+                                       "samples) plus one direct A and A^T on it, scaled to a full 200x200x300 "
+                                       "reconstruction by slab columns and algorithmic flops"},
+            "e2e": {"value": value, "unit": "volumes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "seconds_per_volume": per_volume}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_2009_10173_gb300 import binding as B
+    from paper_2009_10173_gb300 import configs, inputs
+    from paper_2009_10173_gb300.model import Model
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    cfg = configs.VOLUME_200
+
+    def make_model(prec):
+        return Model(cfg, precision=prec)
+
+    # precision: the tensor-core form when it is built, else plain FP32
+    if args.prec == "fp32":
+        prec = B.OAM_PREC_FP32
+    elif args.prec == "bf16x3":
+        prec = B.OAM_PREC_BF16X3
+    else:
+        try:
+            make_model(B.OAM_PREC_BF16X3).close()
+            prec = B.OAM_PREC_BF16X3
+        except B.OamError as e:
+            if e.code != B.OAM_ERR_UNSUPPORTED:
+                raise
+            prec = B.OAM_PREC_FP32
+    prec_name = {B.OAM_PREC_FP32: "fp32 CUDA-core operators",
+                 B.OAM_PREC_BF16X3: "split-BF16 (hi*hi+hi*lo+lo*hi) tcgen05 operators, FP32 accumulate"}[prec]
+
+    # synthetic input for this rank: vessel tree + microspheres, clean signals by A, 20 dB noise
+    seed = 1 + rank
+    H = inputs.phantom(cfg, seed, kind="vessels", count=50)
+    m0 = make_model(B.OAM_PREC_FP32)
+    clean = m0.forward(torch.from_numpy(H.astype(np.float32)).cuda()).cpu().numpy()
+    info0 = m0.info
+    m0.close()
+    s_host = torch.from_numpy(inputs.add_noise(clean, 20.0, seed + 10 ** 6).astype(np.float32)).pin_memory()
+    s_dev = s_host.cuda()
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    vol_bytes = int(np.prod(H.shape)) * 4
+
+    keep = []
+
+    def step(s_in, profile=False):
+        m = make_model(prec)
+        if profile:
+            B.oam_profile_enable(m.handle, True)
+        x2, _ = m.lsqr(s_in, LSQR_ITERS, want_info=False)
+        x1, _ = m.fista(s_in, FISTA_ITERS, power_iters=POWER_ITERS, lambda_rel=LAMBDA_REL, nonneg=True,
+                        want_info=False)
+        return m, x2, x1
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        m, _, _ = step(s_dev)
+        m.close()
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = B.oam_launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    t_wall = time.perf_counter()
+    ev[0].record()
+    for i in range(args.steps):
+        m, x2, x1 = step(s_dev, profile=True)
+        keep.append(m)
+        flush.zero_()
+        ev[i + 1].record()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    launches = B.oam_launch_count() - launches0 - 0  # the flush is a torch kernel, not counted
+    clk = clocks.stop()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    elapsed_ms = ev[0].elapsed_time(ev[-1])
+    prof = [B.oam_profile_read(mm.handle) for mm in keep]
+    info = keep[0].info
+    for mm in keep:
+        mm.close()
+    keep.clear()
+
+    # end to end through the public API: pinned host signals in, both images out
+    img2 = torch.empty(H.shape, dtype=torch.float32).pin_memory()
+    img1 = torch.empty(H.shape, dtype=torch.float32).pin_memory()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        s_in = s_host.cuda(non_blocking=True)
+        m, x2, x1 = step(s_in)
+        img2.copy_(x2, non_blocking=True)
+        img1.copy_(x1, non_blocking=True)
+        torch.cuda.synchronize()
+        m.close()
+    e1.record()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+
+    if dist:
+        t = torch.tensor([elapsed_ms, e2e_ms], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        elapsed_ms, e2e_ms = t.tolist()
+    if rank != 0:
+        return
+
+    per_step = elapsed_ms / args.steps
+    value = world * args.steps / (elapsed_ms / 1e3)
+    fwd_ms = sum(p.forward_ms for p in prof) / max(1, sum(p.forward_calls for p in prof))
+    adj_ms = sum(p.adjoint_ms for p in prof) / max(1, sum(p.adjoint_calls for p in prof))
+    fwd_tot = sum(p.forward_ms for p in prof)
+    adj_tot = sum(p.adjoint_ms for p in prof)
+    dom, dom_ms = ("adjoint", adj_ms) if adj_tot >= fwd_tot else ("forward", fwd_ms)
+    achieved = info.flops_per_op / (dom_ms * 1e-3) / 1e12
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    if prec == B.OAM_PREC_FP32:
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": f"{dom} (FP32 FFMA)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:g} MHz"}
+    else:
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "tensor", "kernel": f"{dom} (tcgen05 split-BF16)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+    line = {"metric": METRIC, "value": value, "unit": "volumes/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == B.OAM_PREC_FP32 else "bf16", "data": "synthetic",
+            "config": config_dict(prec_name),
+            "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+            "op_tflops_algorithmic": OPS_PER_STEP * info.flops_per_op / (per_step * 1e-3) / 1e12,
+            "op_ms": {"forward": fwd_ms, "adjoint": adj_ms}, "flops_per_op": info.flops_per_op,
+            "roofline": roof, "gpu_launches": int(launches),
+            "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "volumes/s",
+                    "h2d_bytes_per_step": int(s_host.numel() * 4), "d2h_bytes_per_step": 2 * vol_bytes},
+            "clocks": clk, "wall_s_timed": wall}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_entry(info.flops_per_op)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    rank = int(os.environ.get("RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

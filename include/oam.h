@@ -1,0 +1,207 @@
+/*
+ * oam.h - C ABI of liboam.so: GB300 (sm_103a) model-based AR-OAM inversion.
+ *
+ * Method: Li et al., "Broadband model-based inversion enables optoacoustic
+ * microscopy beyond the acoustic diffraction limit" (arXiv:2009.10173).
+ *
+ * Data layouts (all device arrays are FP32, row-major, caller-owned):
+ *   volume  H[py][px][nz]   voxel (y, x, depth k), depth fastest;
+ *   signals s[py][px][nt]   A-mode signal of scan position (y, x), time fastest.
+ * Voxel (y, x) sits under scan position (y, x): the lateral voxel grid equals
+ * the scan grid (Results: the voxels' lateral positions match the scanning
+ * positions).  Depth k is at z0_rel + k*dz relative to the focal depth, sample
+ * n at time t0 + n/fs.
+ *
+ * Model slab (Eqs. 3-4 and "Efficient reconstruction based on scanning
+ * symmetries"): S[b][a][k][n], b, a in [-R, R], R = (win-1)/2, is the signal
+ * at sample n from a unit voxel at lateral offset (a*dx, b*dy) and depth k
+ * relative to one scan position.  It sums, over M sensor-surface patches j of
+ * area w_j at distance d_j, (w_j[mm^2] / d_j[mm]) * e'(n - fs*(d_j/c - t0)),
+ * where e is the electrical impulse response (a Gaussian-windowed cosine at
+ * fc whose -6 dB amplitude bandwidth is frac_bw*fc, cut at trunc_sigma
+ * standard deviations) and e' its time derivative (the d/dt of Eq. 1).
+ *
+ *   forward  (Eq. 4, s = A_s H):  s[y][x][n] = sum_{b,a,k} S[b][a][k][n] H[y+b][x+a][k]
+ *   adjoint  (A_s^T):             H[y][x][k] = sum_{b,a,n} S[b][a][k][n] s[y-b][x-a][n]
+ * with H and s zero outside their grids (no wrap-around).
+ *
+ * Conventions for every entry point:
+ *   - Returns an oam_status; nothing throws or aborts across the ABI.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued asynchronously on it; results are valid after the stream
+ *     is synchronised, unless the function says it synchronises.
+ *   - Device pointers must be distinct, non-overlapping and 16-byte aligned.
+ *   - The library owns a model and its device memory; the caller owns every
+ *     other buffer.  A model serves one stream at a time: concurrent calls on
+ *     the same model race on its internal staging buffers.
+ *   - Invalid arguments are rejected before any allocation or launch.
+ */
+#ifndef OAM_H
+#define OAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OAM_OK = 0,
+  OAM_ERR_INVALID_ARG = 1, /* bad pointer, size or parameter */
+  OAM_ERR_WINDOW = 2,      /* arrivals fall outside [0, nt) for the time origin */
+  OAM_ERR_OOM = 3,         /* device or host allocation failed */
+  OAM_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  OAM_ERR_DEVICE = 5,      /* a kernel reported an internal inconsistency */
+  OAM_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out */
+  OAM_ERR_BUSY = 7,        /* resource in use (batch / server) */
+  OAM_ERR_UNSUPPORTED = 8  /* option not implemented, or GPU is not sm_103 */
+} oam_status;
+
+typedef enum {
+  OAM_PREC_FP32 = 0,  /* plain FP32 slab and FP32 CUDA-core operators */
+  OAM_PREC_BF16X3 = 1 /* split-BF16 (hi+lo) slab and iterate on tcgen05 tensor cores,
+                         FP32 accumulation in tensor memory: hi*hi + hi*lo + lo*hi */
+} oam_precision;
+
+/* Spherically focused sensor (AR-OAM set-up): focal length F, aperture
+ * diameter D < 2F, optional central hole h < D, speed of sound c, and the
+ * number M of surface patches (Eq. 3), a positive multiple of 8. */
+typedef struct {
+  double focal_m, aperture_m, hole_m, c_mps;
+  int32_t n_patches;
+} oam_sensor;
+
+/* Scan / voxel / time grid.  win odd, 1 <= win; nt a multiple of 4.
+ * t0_s = NaN selects the automatic time origin
+ * t0 = (floor(fs*dmin/c - trunc_sigma*sigma_s) - 2) / fs, dmin the shortest
+ * voxel-patch distance in the slab; the window check then requires
+ * fs*(dmax/c - t0) + trunc_sigma*sigma_s < nt (else OAM_ERR_WINDOW). */
+typedef struct {
+  int32_t px, py, nz, nt, win;
+  double dx_m, dy_m, dz_m, z0_rel_m, fs_hz, t0_s;
+} oam_grid;
+
+/* Electrical impulse response: centre frequency, fractional -6 dB amplitude
+ * bandwidth, truncation in standard deviations (Results: EIR / SIR split). */
+typedef struct {
+  double fc_hz, frac_bw, trunc_sigma;
+} oam_eir;
+
+typedef struct oam_model oam_model; /* opaque */
+
+typedef struct {
+  double t0_s;         /* time of sample 0 */
+  int32_t n_lo, n_hi;  /* every slab entry is zero outside samples [n_lo, n_hi) */
+  int32_t n_orbits;    /* distinct lateral offsets stored (mirror symmetry) */
+  int32_t precision;   /* oam_precision of forward / adjoint */
+  int64_t nnz;         /* nonzero slab entries over all win*win*nz columns */
+  double flops_per_op; /* algorithmic flops of one forward (= one adjoint): 2*px*py*nnz_in_grid */
+  size_t device_bytes; /* device memory owned by the model */
+} oam_model_info;
+
+/* Build the model slab on the device (Methods: Forward modeling, Eqs. 1-4;
+ * "it was sufficient to generate the model matrix for a single scanning
+ * position").  Synchronises `stream` (the time origin and band layout are
+ * planned from device results).  On success *out owns all device memory.
+ * Errors: OAM_ERR_INVALID_ARG, OAM_ERR_WINDOW, OAM_ERR_OOM, OAM_ERR_CUDA,
+ * OAM_ERR_UNSUPPORTED (no sm_103 device). */
+oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
+                           oam_precision precision, void *stream, oam_model **out);
+
+/* Release a model (NULL is accepted).  Synchronises the device first. */
+oam_status oam_model_free(oam_model *model);
+
+/* Fill *info (host memory). */
+oam_status oam_model_get_info(const oam_model *model, oam_model_info *info);
+
+/* Write slab column S[b][a][k][0..nt) to device memory d_out (nt floats),
+ * b, a in [-R, R], 0 <= k < nz.  For inspection and tests. */
+oam_status oam_model_slab_column(const oam_model *model, int32_t b, int32_t a, int32_t k,
+                                 float *d_out, void *stream);
+
+/* s = A H (Eq. 4 applied over the scan grid).  d_H: py*px*nz floats (input),
+ * d_s: py*px*nt floats (output, fully overwritten). */
+oam_status oam_forward(const oam_model *model, const float *d_H, float *d_s, void *stream);
+
+/* H = A^T s.  d_s: py*px*nt floats (input), d_H: py*px*nz floats (output,
+ * fully overwritten). */
+oam_status oam_adjoint(const oam_model *model, const float *d_s, float *d_H, void *stream);
+
+/* ---------------------------------------------------------------- solvers */
+/* MB-L2: Eq. 5 with the Tikhonov term of Eq. 6 (lambda = damp^2), solved by
+ * LSQR (Paige & Saunders) from x0 = 0 for `iters` iterations.  Vectors are
+ * FP32; norms, the bidiagonalisation scalars and the plane-rotation
+ * recurrence are FP64 on the device; no host synchronisation inside the loop.
+ * An exact zero alpha or beta stops early (stop_reason 1). */
+typedef struct {
+  int32_t iters;
+  double damp;
+} oam_lsqr_opts;
+
+typedef struct {
+  int32_t iters_done, stop_reason;
+  double rnorm;  /* |phibar|: ||s - A x|| (damp = 0) */
+  double arnorm; /* |phibar * alpha * c| */
+  double anorm;  /* Frobenius-norm estimate of the bidiagonal */
+} oam_lsqr_info;
+
+/* d_s: signals (input), d_x: volume (output).  d_work / work_bytes: caller
+ * workspace of at least oam_solver_work_bytes(model, 0) bytes, 256-byte
+ * aligned.  If info != NULL the call synchronises `stream` and fills it. */
+oam_status oam_lsqr(const oam_model *model, const float *d_s, float *d_x, const oam_lsqr_opts *opts,
+                    oam_lsqr_info *info, void *d_work, size_t work_bytes, void *stream);
+
+/* MB-L1: Eq. 5 with the L1 term of Eq. 7, f(H) = ||s - A H||^2 + lambda ||H||_1
+ * (no factor 1/2), solved by FISTA (Beck & Teboulle) with constant step 1/L:
+ * grad = 2 A^T (A Y - s), x = prox(Y - grad/L, lambda/L), t' = (1 + sqrt(1+4t^2))/2,
+ * Y = x + ((t-1)/t')(x - x_prev), from x0 = Y = 0, t = 1.
+ * L <= 0: L = 2 * 1.01 * mu, mu from `power_iters` steps of A^T A started at
+ * d_power_v0 (volume-sized; NULL = all ones).  lambda < 0: lambda =
+ * lambda_rel * max|A^T s|.  nonneg != 0 projects onto H >= 0. */
+typedef struct {
+  int32_t iters, power_iters, nonneg, compute_objective;
+  double lambda, lambda_rel, L;
+  const float *d_power_v0;
+} oam_fista_opts;
+
+typedef struct {
+  int32_t iters_done;
+  double L, lambda, mu;
+  double objective; /* f at the returned x when compute_objective, else NaN */
+} oam_fista_info;
+
+oam_status oam_l1_fista(const oam_model *model, const float *d_s, float *d_x, const oam_fista_opts *opts,
+                        oam_fista_info *info, void *d_work, size_t work_bytes, void *stream);
+
+/* Workspace bytes for solver 0 = LSQR, 1 = FISTA. */
+oam_status oam_solver_work_bytes(const oam_model *model, int32_t solver, size_t *bytes);
+
+/* ---------------------------------------------------------------- timing */
+/* Device time of the operator kernels, measured with CUDA events recorded on
+ * the caller's stream around the main kernel of every forward / adjoint
+ * (including those inside the solvers). */
+typedef struct {
+  int64_t forward_calls, adjoint_calls;
+  double forward_ms, adjoint_ms; /* summed event-to-event durations */
+} oam_profile;
+
+/* enable != 0 starts (and resets) event timing on this model; 0 stops it. */
+oam_status oam_profile_enable(oam_model *model, int32_t enable);
+
+/* Synchronise on the last recorded event and fill *out (host memory). */
+oam_status oam_profile_read(oam_model *model, oam_profile *out);
+
+/* Number of kernel launches this library has issued in this process. */
+int64_t oam_launch_count(void);
+
+/* Static description of a status code. */
+const char *oam_status_string(oam_status status);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t oam_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OAM_H */

@@ -1,0 +1,211 @@
+"""Thin ctypes binding of ``liboam.so`` (argument marshalling only).
+
+Every function keeps the C name and argument order of ``include/oam.h``;
+device buffers are torch CUDA tensors (FP32, contiguous) and the stream is
+the current torch stream unless one is given.  A missing or unloadable
+library raises immediately: there is no CPU fallback.
+"""
+import ctypes
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liboam.so")
+
+OAM_OK, OAM_ERR_INVALID_ARG, OAM_ERR_WINDOW, OAM_ERR_OOM, OAM_ERR_CUDA = 0, 1, 2, 3, 4
+OAM_ERR_DEVICE, OAM_ERR_TIMEOUT, OAM_ERR_BUSY, OAM_ERR_UNSUPPORTED = 5, 6, 7, 8
+OAM_PREC_FP32, OAM_PREC_BF16X3 = 0, 1
+
+EXPORTED = ("oam_build_model", "oam_model_free", "oam_model_get_info", "oam_model_slab_column", "oam_forward",
+            "oam_adjoint", "oam_lsqr", "oam_l1_fista", "oam_solver_work_bytes", "oam_status_string",
+            "oam_version", "oam_profile_enable", "oam_profile_read", "oam_launch_count")
+
+
+class OamSensor(ctypes.Structure):
+    _fields_ = [("focal_m", ctypes.c_double), ("aperture_m", ctypes.c_double), ("hole_m", ctypes.c_double),
+                ("c_mps", ctypes.c_double), ("n_patches", ctypes.c_int32)]
+
+
+class OamGrid(ctypes.Structure):
+    _fields_ = [("px", ctypes.c_int32), ("py", ctypes.c_int32), ("nz", ctypes.c_int32), ("nt", ctypes.c_int32),
+                ("win", ctypes.c_int32), ("dx_m", ctypes.c_double), ("dy_m", ctypes.c_double),
+                ("dz_m", ctypes.c_double), ("z0_rel_m", ctypes.c_double), ("fs_hz", ctypes.c_double),
+                ("t0_s", ctypes.c_double)]
+
+
+class OamEir(ctypes.Structure):
+    _fields_ = [("fc_hz", ctypes.c_double), ("frac_bw", ctypes.c_double), ("trunc_sigma", ctypes.c_double)]
+
+
+class OamModelInfo(ctypes.Structure):
+    _fields_ = [("t0_s", ctypes.c_double), ("n_lo", ctypes.c_int32), ("n_hi", ctypes.c_int32),
+                ("n_orbits", ctypes.c_int32), ("precision", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("flops_per_op", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
+class OamLsqrOpts(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("damp", ctypes.c_double)]
+
+
+class OamLsqrInfo(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int32), ("stop_reason", ctypes.c_int32), ("rnorm", ctypes.c_double),
+                ("arnorm", ctypes.c_double), ("anorm", ctypes.c_double)]
+
+
+class OamFistaOpts(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("power_iters", ctypes.c_int32), ("nonneg", ctypes.c_int32),
+                ("compute_objective", ctypes.c_int32), ("lambda_", ctypes.c_double),
+                ("lambda_rel", ctypes.c_double), ("L", ctypes.c_double), ("d_power_v0", ctypes.c_void_p)]
+
+
+class OamFistaInfo(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int32), ("L", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("mu", ctypes.c_double), ("objective", ctypes.c_double)]
+
+
+class OamProfile(ctypes.Structure):
+    _fields_ = [("forward_calls", ctypes.c_int64), ("adjoint_calls", ctypes.c_int64),
+                ("forward_ms", ctypes.c_double), ("adjoint_ms", ctypes.c_double)]
+
+
+class OamError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} failed: {status_string(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load liboam.so (raises if it is missing: build it with ``build_lib.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"{LIB_PATH} is missing; run paper_2009_10173_gb300.build_lib.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+        P = ctypes.POINTER
+        L.oam_build_model.argtypes = [P(OamSensor), P(OamGrid), P(OamEir), ctypes.c_int, vp, P(vp)]
+        L.oam_model_free.argtypes = [vp]
+        L.oam_model_get_info.argtypes = [vp, P(OamModelInfo)]
+        L.oam_model_slab_column.argtypes = [vp, i32, i32, i32, vp, vp]
+        L.oam_forward.argtypes = [vp, vp, vp, vp]
+        L.oam_adjoint.argtypes = [vp, vp, vp, vp]
+        L.oam_lsqr.argtypes = [vp, vp, vp, P(OamLsqrOpts), P(OamLsqrInfo), vp, sz, vp]
+        L.oam_l1_fista.argtypes = [vp, vp, vp, P(OamFistaOpts), P(OamFistaInfo), vp, sz, vp]
+        L.oam_solver_work_bytes.argtypes = [vp, i32, P(sz)]
+        L.oam_status_string.argtypes = [ctypes.c_int]
+        L.oam_status_string.restype = ctypes.c_char_p
+        L.oam_version.restype = i32
+        L.oam_profile_enable.argtypes = [vp, i32]
+        L.oam_profile_read.argtypes = [vp, P(OamProfile)]
+        L.oam_launch_count.restype = ctypes.c_int64
+        for f in EXPORTED:
+            if f not in ("oam_status_string", "oam_version", "oam_launch_count"):
+                getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(code):
+    return lib().oam_status_string(int(code)).decode()
+
+
+def _check(fn, code):
+    if code != OAM_OK:
+        raise OamError(fn, code)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def structs_from_config(cfg):
+    """oam_sensor / oam_grid / oam_eir from a workload mapping (SI units)."""
+    s = OamSensor(cfg["focal_m"], cfg["aperture_m"], cfg.get("hole_m", 0.0), cfg["c_mps"], cfg["n_patches"])
+    t0 = cfg.get("t0_s", math.nan)
+    g = OamGrid(cfg["px"], cfg["py"], cfg["nz"], cfg["nt"], cfg["win"], cfg["dx_m"], cfg["dy_m"], cfg["dz_m"],
+                cfg["z0_rel_m"], cfg["fs_hz"], math.nan if t0 is None else t0)
+    e = OamEir(cfg["fc_hz"], cfg["frac_bw"], cfg.get("trunc_sigma", 5.0))
+    return s, g, e
+
+
+def oam_build_model(sensor, grid, eir, precision=OAM_PREC_FP32, stream=None):
+    h = ctypes.c_void_p()
+    _check("oam_build_model", lib().oam_build_model(ctypes.byref(sensor), ctypes.byref(grid), ctypes.byref(eir),
+                                                     int(precision), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def oam_model_free(model):
+    _check("oam_model_free", lib().oam_model_free(model))
+
+
+def oam_model_get_info(model):
+    info = OamModelInfo()
+    _check("oam_model_get_info", lib().oam_model_get_info(model, ctypes.byref(info)))
+    return info
+
+
+def oam_model_slab_column(model, b, a, k, out, stream=None):
+    _check("oam_model_slab_column", lib().oam_model_slab_column(model, b, a, k, _ptr(out), _stream(stream)))
+
+
+def oam_forward(model, H, s, stream=None):
+    _check("oam_forward", lib().oam_forward(model, _ptr(H), _ptr(s), _stream(stream)))
+
+
+def oam_adjoint(model, s, H, stream=None):
+    _check("oam_adjoint", lib().oam_adjoint(model, _ptr(s), _ptr(H), _stream(stream)))
+
+
+def oam_solver_work_bytes(model, solver):
+    n = ctypes.c_size_t()
+    _check("oam_solver_work_bytes", lib().oam_solver_work_bytes(model, int(solver), ctypes.byref(n)))
+    return n.value
+
+
+def oam_lsqr(model, s, x, opts, work, stream=None, want_info=True):
+    info = OamLsqrInfo()
+    _check("oam_lsqr", lib().oam_lsqr(model, _ptr(s), _ptr(x), ctypes.byref(opts),
+                                      ctypes.byref(info) if want_info else None, _ptr(work),
+                                      work.numel() * work.element_size(), _stream(stream)))
+    return info
+
+
+def oam_l1_fista(model, s, x, opts, work, stream=None, want_info=True):
+    info = OamFistaInfo()
+    _check("oam_l1_fista", lib().oam_l1_fista(model, _ptr(s), _ptr(x), ctypes.byref(opts),
+                                              ctypes.byref(info) if want_info else None, _ptr(work),
+                                              work.numel() * work.element_size(), _stream(stream)))
+    return info
+
+
+def oam_version():
+    return lib().oam_version()
+
+
+def oam_profile_enable(model, enable=True):
+    _check("oam_profile_enable", lib().oam_profile_enable(model, int(bool(enable))))
+
+
+def oam_profile_read(model):
+    p = OamProfile()
+    _check("oam_profile_read", lib().oam_profile_read(model, ctypes.byref(p)))
+    return p
+
+
+def oam_launch_count():
+    return lib().oam_launch_count()

@@ -1,0 +1,160 @@
+// Plain FP32 forward and adjoint operators on CUDA cores.
+//
+// Both are lateral correlations of the single-position slab with the volume or
+// the signals ("two coordinate systems": the absolute index of a voxel and its
+// offset relative to each scan position; Methods, Efficient reconstruction
+// based on scanning symmetries).  Voxels and samples outside the grids are zero.
+//
+// forward: block = (row y, 64 positions, 64-sample time tile); it walks every
+//   tap (b, a) and the depths whose band meets the time tile, staging 16 depths
+//   of the shifted volume row and the packed slab rows in shared memory.
+// adjoint: block = (row y, 64 positions, 16-depth tile); it walks every tap and
+//   the samples of the tile's band union, 64 samples at a time.
+#include "internal.cuh"
+
+using namespace oam;
+
+namespace {
+
+constexpr int kPos = 64;
+
+__global__ void __launch_bounds__(256) k_fwd_fp32(const float *__restrict__ H, float *__restrict__ s, int px, int py,
+                                                  int nz, int nt, int R, const int *__restrict__ tap_orbit, int n_tt,
+                                                  const int *__restrict__ krange, const long long *__restrict__ off,
+                                                  const float *__restrict__ P) {
+  const int x0 = blockIdx.x * kPos, y = blockIdx.y, T = blockIdx.z;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int W = 2 * R + 1;
+  __shared__ float Hs[kPos][kDepthTile + 1];
+  __shared__ float4 Ps[kDepthTile][kTimeTile / 4];
+  float acc[4][4] = {};
+  for (int b = -R; b <= R; ++b) {
+    const int yy = y + b;
+    if (yy < 0 || yy >= py) continue;
+    for (int a = -R; a <= R; ++a) {
+      const int xs = x0 + a;
+      if (xs + kPos <= 0 || xs >= px) continue;
+      const int oi = tap_orbit[(b + R) * W + (a + R)] * n_tt + T;
+      const int klo = krange[2 * oi], khi = krange[2 * oi + 1];
+      if (klo >= khi) continue;
+      const float4 *P4 = reinterpret_cast<const float4 *>(P + off[oi]);
+      for (int kc = klo; kc < khi; kc += kDepthTile) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int e = tid + 256 * r, p = e >> 4, kk = e & 15;
+          const int x = xs + p, k = kc + kk;
+          Hs[p][kk] = (x >= 0 && x < px && k < khi) ? H[((size_t)yy * px + x) * nz + k] : 0.0f;
+        }
+        {
+          const int row = tid >> 4, c4 = tid & 15;
+          Ps[row][c4] = (kc + row < khi) ? P4[(size_t)(kc - klo + row) * (kTimeTile / 4) + c4]
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kDepthTile; ++kk) {
+          const float4 p = Ps[kk][tx];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float h = Hs[4 * ty + i][kk];
+            acc[i][0] = fmaf(h, p.x, acc[i][0]);
+            acc[i][1] = fmaf(h, p.y, acc[i][1]);
+            acc[i][2] = fmaf(h, p.z, acc[i][2]);
+            acc[i][3] = fmaf(h, p.w, acc[i][3]);
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  const int n = T * kTimeTile + 4 * tx;
+  if (n >= nt) return;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int x = x0 + 4 * ty + i;
+    if (x < px)
+      *reinterpret_cast<float4 *>(s + ((size_t)y * px + x) * nt + n) =
+          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_adj_fp32(const float *__restrict__ s, float *__restrict__ H, int px, int py,
+                                                  int nz, int nt, int R, const int *__restrict__ tap_orbit, int n_kt,
+                                                  const int *__restrict__ nrange, const long long *__restrict__ off,
+                                                  const float *__restrict__ Q) {
+  const int x0 = blockIdx.x * kPos, y = blockIdx.y, K = blockIdx.z;
+  const int tid = threadIdx.x, p = tid & 63, kq = tid >> 6;
+  const int W = 2 * R + 1;
+  __shared__ float4 Ss[kPos][kTimeTile / 4 + 1];
+  __shared__ float4 Qs[kDepthTile][kTimeTile / 4];
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int b = -R; b <= R; ++b) {
+    const int yy = y - b;
+    if (yy < 0 || yy >= py) continue;
+    for (int a = -R; a <= R; ++a) {
+      const int xs = x0 - a;
+      if (xs + kPos <= 0 || xs >= px) continue;
+      const int oi = tap_orbit[(b + R) * W + (a + R)] * n_kt + K;
+      const int nlo = nrange[2 * oi], nlen = nrange[2 * oi + 1];
+      if (nlen <= 0) continue;
+      const float4 *Q4 = reinterpret_cast<const float4 *>(Q + off[oi]);
+      for (int nc = 0; nc < nlen; nc += kTimeTile) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int e = tid + 256 * r, pp = e >> 4, j4 = e & 15;
+          const int x = xs + pp, j = nc + 4 * j4;
+          Ss[pp][j4] = (x >= 0 && x < px && j < nlen)
+                           ? *reinterpret_cast<const float4 *>(s + ((size_t)yy * px + x) * nt + nlo + j)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        {
+          const int row = tid >> 4, j4 = tid & 15, j = nc + 4 * j4;
+          Qs[row][j4] = (j < nlen) ? Q4[((size_t)row * nlen + j) >> 2] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j4 = 0; j4 < kTimeTile / 4; ++j4) {
+          const float4 v = Ss[p][j4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float4 q = Qs[4 * kq + i][j4];
+            acc[i] = fmaf(v.x, q.x, acc[i]);
+            acc[i] = fmaf(v.y, q.y, acc[i]);
+            acc[i] = fmaf(v.z, q.z, acc[i]);
+            acc[i] = fmaf(v.w, q.w, acc[i]);
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  const int x = x0 + p;
+  if (x >= px) return;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = K * kDepthTile + 4 * kq + i;
+    if (k < nz) H[((size_t)y * px + x) * nz + k] = acc[i];
+  }
+}
+
+}  // namespace
+
+oam_status oam::forward_fp32(const oam_model *m, const float *H, float *s, cudaStream_t st) {
+  const oam_grid &g = m->grid;
+  dim3 grid((g.px + kPos - 1) / kPos, g.py, m->n_ttiles);
+  ProfScope prof(m, st, true);
+  k_fwd_fp32<<<grid, 256, 0, st>>>(H, s, g.px, g.py, g.nz, g.nt, m->R, m->d_tap_orbit, m->n_ttiles, m->d_fwd_krange,
+                                   m->d_fwd_off, m->d_fwd);
+  OAM_LAUNCHED();
+  return OAM_OK;
+}
+
+oam_status oam::adjoint_fp32(const oam_model *m, const float *s, float *H, cudaStream_t st) {
+  const oam_grid &g = m->grid;
+  dim3 grid((g.px + kPos - 1) / kPos, g.py, m->n_ktiles);
+  ProfScope prof(m, st, false);
+  k_adj_fp32<<<grid, 256, 0, st>>>(s, H, g.px, g.py, g.nz, g.nt, m->R, m->d_tap_orbit, m->n_ktiles, m->d_adj_nrange,
+                                   m->d_adj_off, m->d_adj);
+  OAM_LAUNCHED();
+  return OAM_OK;
+}

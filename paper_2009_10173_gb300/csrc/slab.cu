@@ -1,0 +1,348 @@
+// Model slab builder (Methods, Forward modeling, Eqs. 1-4): per-orbit bands
+// of the single-position model, and the FP32 operator layouts packed from them.
+//
+// Distances use the cancellation-free form d - F = (2F r.n + |r|^2) / (d + F)
+// in FP64, so the arrival sample fs*(d/c - t0) = (fs/c)(d - F) + fs(F/c - t0)
+// keeps full precision; the EIR derivative is evaluated in FP32 at
+// tau = n - D_j (|tau| <= trunc_sigma * sigma_s) and summed in FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+
+using namespace oam;
+
+namespace {
+
+struct Geo {
+  double F, dx, dy, dz, z0;
+  double ks;      // fs / c, samples per metre
+  double G;       // fs * (F/c - t0)
+  double cut;     // truncation, samples
+  float inv2s2;   // 1 / (2 sigma_s^2)
+  float invs2;    // 1 / sigma_s^2
+  float omega;    // 2 pi fc / fs
+};
+
+// d - F for the voxel at lateral offset (a dx, b dy), depth k, and patch normal n.
+__device__ __forceinline__ double delta_dist(const Geo &g, int b, int a, int k, Patch p) {
+  double rx = a * g.dx, ry = b * g.dy, rz = g.z0 + k * g.dz;
+  double rn = __dadd_rn(__dadd_rn(__dmul_rn(rx, p.x), __dmul_rn(ry, p.y)), __dmul_rn(rz, p.z));
+  double r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
+  double num = __dadd_rn(__dmul_rn(2.0 * g.F, rn), r2);
+  double d = sqrt(__dadd_rn(__dmul_rn(g.F, g.F), num));
+  return __ddiv_rn(num, __dadd_rn(d, g.F));
+}
+
+// Per (orbit, depth): min and max of d - F over the patches.
+__global__ void k_delta_range(Geo g, const Patch *__restrict__ patch, int M, const int *orb_b,
+                              const int *orb_a, int nz, double2 *out) {
+  const int o = blockIdx.x, k = blockIdx.y;
+  const int b = orb_b[o], a = orb_a[o];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    double dd = delta_dist(g, b, a, k, patch[j]);
+    lo = fmin(lo, dd);
+    hi = fmax(hi, dd);
+  }
+  for (int off = 16; off; off >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+  }
+  __shared__ double slo[32], shi[32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { slo[w] = lo; shi[w] = hi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) { lo = fmin(lo, slo[i]); hi = fmax(hi, shi[i]); }
+    out[o * nz + k] = make_double2(lo, hi);
+  }
+}
+
+constexpr int kPatchChunk = 512;
+
+// Band values: thread i of block (o, k) owns sample lo + i (+ blockDim.x ...).
+// Patches are visited in index order, so every entry is a fixed-order sum.
+__global__ void k_slab_values(Geo g, const Patch *__restrict__ patch, int M, const int *orb_b,
+                              const int *orb_a, int nz, const int *band_lo, const int *band_hi,
+                              int band_w, float *band) {
+  const int o = blockIdx.x, k = blockIdx.y;
+  const int b = orb_b[o], a = orb_a[o];
+  const int lo = band_lo[o * nz + k], hi = band_hi[o * nz + k];
+  __shared__ double sD[kPatchChunk];
+  __shared__ float sW[kPatchChunk];
+  const int per = (band_w + blockDim.x - 1) / blockDim.x;  // samples per thread (<= 4)
+  double acc[4] = {0, 0, 0, 0};
+  for (int j0 = 0; j0 < M; j0 += kPatchChunk) {
+    const int cnt = min(kPatchChunk, M - j0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+      Patch p = patch[j0 + j];
+      double dd = delta_dist(g, b, a, k, p);
+      sD[j] = __dadd_rn(__dmul_rn(g.ks, dd), g.G);
+      sW[j] = (float)(p.w / ((g.F + dd) * 1e3));  // mm^2 / mm
+    }
+    __syncthreads();
+    for (int r = 0; r < per; ++r) {
+      const int n = lo + threadIdx.x + r * blockDim.x;
+      if (n >= hi) break;
+      double s = acc[r];
+      for (int j = 0; j < cnt; ++j) {
+        double t = (double)n - sD[j];
+        if (fabs(t) <= g.cut) {
+          float tau = (float)t;
+          float sn, cs;
+          sincosf(g.omega * tau, &sn, &cs);
+          float env = expf(-tau * tau * g.inv2s2);
+          float v = -env * (tau * g.invs2 * cs + g.omega * sn);
+          s += (double)(sW[j] * v);
+        }
+      }
+      acc[r] = s;
+    }
+  }
+  float *row = band + ((size_t)o * nz + k) * band_w;
+  for (int r = 0; r < per; ++r) {
+    const int i = threadIdx.x + r * blockDim.x;
+    if (i >= band_w) break;
+    const int n = lo + i;
+    row[i] = (n < hi) ? (float)acc[r] : 0.0f;
+  }
+}
+
+// FP32 forward layout: rows k in [klo, khi) of kTimeTile samples of tile T.
+__global__ void k_pack_fwd(const float *band, const int *band_lo, const int *band_hi, int band_w, int nz,
+                           int n_ttiles, const int *krange, const long long *off, float *out) {
+  const int ot = blockIdx.x;
+  const int o = ot / n_ttiles, T = ot % n_ttiles;
+  const int klo = krange[2 * ot], khi = krange[2 * ot + 1];
+  const long long base = off[ot];
+  const int total = (khi - klo) * kTimeTile;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int k = klo + i / kTimeTile, n = T * kTimeTile + i % kTimeTile;
+    const int lo = band_lo[o * nz + k], hi = band_hi[o * nz + k];
+    out[base + i] = (n >= lo && n < hi) ? band[((size_t)o * nz + k) * band_w + (n - lo)] : 0.0f;
+  }
+}
+
+// FP32 adjoint layout: kDepthTile rows (depths) of nlen samples from nlo.
+__global__ void k_pack_adj(const float *band, const int *band_lo, const int *band_hi, int band_w, int nz,
+                           int n_ktiles, const int *nrange, const long long *off, float *out) {
+  const int ok = blockIdx.x;
+  const int o = ok / n_ktiles, K = ok % n_ktiles;
+  const int nlo = nrange[2 * ok], nlen = nrange[2 * ok + 1];
+  const long long base = off[ok];
+  const int total = kDepthTile * nlen;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int k = K * kDepthTile + i / nlen, n = nlo + i % nlen;
+    float v = 0.0f;
+    if (k < nz) {
+      const int lo = band_lo[o * nz + k], hi = band_hi[o * nz + k];
+      if (n >= lo && n < hi) v = band[((size_t)o * nz + k) * band_w + (n - lo)];
+    }
+    out[base + i] = v;
+  }
+}
+
+__global__ void k_slab_column(const float *band, const int *band_lo, int band_w, int nz, int nt, int o, int k,
+                              float *out) {
+  const int lo = band_lo[o * nz + k];
+  const float *row = band + ((size_t)o * nz + k) * band_w;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nt; n += gridDim.x * blockDim.x) {
+    const int i = n - lo;
+    out[n] = (i >= 0 && i < band_w) ? row[i] : 0.0f;
+  }
+}
+
+}  // namespace
+
+oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
+  const oam_grid &gr = m->grid;
+  const int nz = gr.nz, nt = gr.nt, O = m->n_orb;
+  oam_status rc;
+  int *d_orb_b = nullptr, *d_orb_a = nullptr;
+  double2 *d_range = nullptr;
+  if ((rc = dev_alloc(m, &m->d_tap_orbit, m->W * m->W))) return rc;
+  OAM_CUDA_TRY(cudaMemcpyAsync(m->d_tap_orbit, m->h_tap_orbit.data(), sizeof(int) * m->W * m->W,
+                               cudaMemcpyHostToDevice, st));
+  OAM_CUDA_TRY(cudaMallocAsync((void **)&d_orb_b, sizeof(int) * O, st));
+  OAM_CUDA_TRY(cudaMallocAsync((void **)&d_orb_a, sizeof(int) * O, st));
+  OAM_CUDA_TRY(cudaMallocAsync((void **)&d_range, sizeof(double2) * O * nz, st));
+  OAM_CUDA_TRY(cudaMemcpyAsync(d_orb_b, m->h_orb_b.data(), sizeof(int) * O, cudaMemcpyHostToDevice, st));
+  OAM_CUDA_TRY(cudaMemcpyAsync(d_orb_a, m->h_orb_a.data(), sizeof(int) * O, cudaMemcpyHostToDevice, st));
+
+  Geo g{};
+  g.F = m->sensor.focal_m;
+  g.dx = gr.dx_m;
+  g.dy = gr.dy_m;
+  g.dz = gr.dz_m;
+  g.z0 = gr.z0_rel_m;
+  g.ks = gr.fs_hz / m->sensor.c_mps;
+  g.cut = m->cut;
+  g.inv2s2 = (float)(1.0 / (2.0 * m->sigma_s * m->sigma_s));
+  g.invs2 = (float)(1.0 / (m->sigma_s * m->sigma_s));
+  g.omega = (float)m->omega;
+
+  k_delta_range<<<dim3(O, nz), 256, 0, st>>>(g, m->d_patch, m->M, d_orb_b, d_orb_a, nz, d_range);
+  OAM_LAUNCHED();
+  std::vector<double2> h_range((size_t)O * nz);
+  OAM_CUDA_TRY(cudaMemcpyAsync(h_range.data(), d_range, sizeof(double2) * O * nz, cudaMemcpyDeviceToHost, st));
+  OAM_CUDA_TRY(cudaStreamSynchronize(st));
+
+  // time origin and window check
+  double dmin = INFINITY, dmax = -INFINITY;
+  for (const double2 &r : h_range) {
+    dmin = std::min(dmin, r.x);
+    dmax = std::max(dmax, r.y);
+  }
+  const double fs = gr.fs_hz, c = m->sensor.c_mps, F = m->sensor.focal_m;
+  const double t0 = std::isnan(gr.t0_s) ? (std::floor(fs * (F + dmin) / c - m->cut) - 2.0) / fs : gr.t0_s;
+  m->t0 = t0;
+  g.G = fs * (F / c - t0);
+  if (g.ks * dmin + g.G - m->cut < 0 || g.ks * dmax + g.G + m->cut >= nt) {
+    cudaFreeAsync(d_orb_b, st);
+    cudaFreeAsync(d_orb_a, st);
+    cudaFreeAsync(d_range, st);
+    return OAM_ERR_WINDOW;
+  }
+  m->G = g.G;
+
+  // bands [lo, hi) per (orbit, depth)
+  m->h_band_lo.resize((size_t)O * nz);
+  m->h_band_hi.resize((size_t)O * nz);
+  int wmax = 1;
+  m->n_lo = nt;
+  m->n_hi = 0;
+  for (size_t i = 0; i < h_range.size(); ++i) {
+    int lo = (int)std::ceil(g.ks * h_range[i].x + g.G - m->cut);
+    int hi = (int)std::floor(g.ks * h_range[i].y + g.G + m->cut) + 1;
+    lo = std::max(lo, 0);
+    hi = std::min(hi, nt);
+    if (hi < lo) hi = lo;
+    m->h_band_lo[i] = lo;
+    m->h_band_hi[i] = hi;
+    wmax = std::max(wmax, hi - lo);
+    if (hi > lo) {
+      m->n_lo = std::min(m->n_lo, lo);
+      m->n_hi = std::max(m->n_hi, hi);
+    }
+  }
+  m->band_w = (wmax + 3) & ~3;
+  if (m->band_w > 512) return OAM_ERR_UNSUPPORTED;
+
+  // algorithmic work: entries in bands, and multiply-adds over in-grid voxel/position pairs
+  {
+    std::vector<long long> orb_sum(O, 0);
+    for (int o = 0; o < O; ++o)
+      for (int k = 0; k < nz; ++k) orb_sum[o] += m->h_band_hi[(size_t)o * nz + k] - m->h_band_lo[(size_t)o * nz + k];
+    long long nnz = 0;
+    double fl = 0;
+    for (int b = -m->R; b <= m->R; ++b)
+      for (int a = -m->R; a <= m->R; ++a) {
+        long long s = orb_sum[m->h_tap_orbit[(b + m->R) * m->W + (a + m->R)]];
+        nnz += s;
+        long long pairs = (long long)std::max(0, gr.py - std::abs(b)) * std::max(0, gr.px - std::abs(a));
+        fl += 2.0 * (double)pairs * (double)s;
+      }
+    m->nnz = nnz;
+    m->flops = fl;
+  }
+
+  int *d_band_hi = nullptr;
+  if ((rc = dev_alloc(m, &m->d_band_lo, (size_t)O * nz))) return rc;
+  OAM_CUDA_TRY(cudaMallocAsync((void **)&d_band_hi, sizeof(int) * O * nz, st));
+  OAM_CUDA_TRY(cudaMemcpyAsync(m->d_band_lo, m->h_band_lo.data(), sizeof(int) * O * nz, cudaMemcpyHostToDevice, st));
+  OAM_CUDA_TRY(cudaMemcpyAsync(d_band_hi, m->h_band_hi.data(), sizeof(int) * O * nz, cudaMemcpyHostToDevice, st));
+  if ((rc = dev_alloc(m, &m->d_band, (size_t)O * nz * m->band_w))) return rc;
+  const int threads = m->band_w <= 128 ? 128 : 256;
+  k_slab_values<<<dim3(O, nz), threads, 0, st>>>(g, m->d_patch, m->M, d_orb_b, d_orb_a, nz, m->d_band_lo,
+                                                  d_band_hi, m->band_w, m->d_band);
+  OAM_LAUNCHED();
+
+  // FP32 forward layout
+  m->n_ttiles = (nt + kTimeTile - 1) / kTimeTile;
+  {
+    const int NT = m->n_ttiles;
+    std::vector<int> kr((size_t)O * NT * 2, 0);
+    std::vector<long long> off((size_t)O * NT, 0);
+    long long total = 0;
+    for (int o = 0; o < O; ++o)
+      for (int T = 0; T < NT; ++T) {
+        int klo = nz, khi = 0;
+        for (int k = 0; k < nz; ++k) {
+          int lo = m->h_band_lo[(size_t)o * nz + k], hi = m->h_band_hi[(size_t)o * nz + k];
+          if (hi > lo && lo < (T + 1) * kTimeTile && hi > T * kTimeTile) {
+            klo = std::min(klo, k);
+            khi = std::max(khi, k + 1);
+          }
+        }
+        if (khi <= klo) klo = khi = 0;
+        size_t i = (size_t)o * NT + T;
+        kr[2 * i] = klo;
+        kr[2 * i + 1] = khi;
+        off[i] = total;
+        total += (long long)(khi - klo) * kTimeTile;
+      }
+    if ((rc = dev_alloc(m, &m->d_fwd_krange, kr.size()))) return rc;
+    if ((rc = dev_alloc(m, &m->d_fwd_off, off.size()))) return rc;
+    if ((rc = dev_alloc(m, &m->d_fwd, (size_t)total))) return rc;
+    OAM_CUDA_TRY(cudaMemcpyAsync(m->d_fwd_krange, kr.data(), sizeof(int) * kr.size(), cudaMemcpyHostToDevice, st));
+    OAM_CUDA_TRY(cudaMemcpyAsync(m->d_fwd_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, st));
+    k_pack_fwd<<<O * NT, 256, 0, st>>>(m->d_band, m->d_band_lo, d_band_hi, m->band_w, nz, NT, m->d_fwd_krange,
+                                       m->d_fwd_off, m->d_fwd);
+    OAM_LAUNCHED();
+    OAM_CUDA_TRY(cudaStreamSynchronize(st));  // host tables above go out of scope
+  }
+  // FP32 adjoint layout
+  m->n_ktiles = (nz + kDepthTile - 1) / kDepthTile;
+  {
+    const int NK = m->n_ktiles;
+    std::vector<int> nr((size_t)O * NK * 2, 0);
+    std::vector<long long> off((size_t)O * NK, 0);
+    long long total = 0;
+    for (int o = 0; o < O; ++o)
+      for (int K = 0; K < NK; ++K) {
+        int nlo = nt, nhi = 0;
+        for (int k = K * kDepthTile; k < std::min(nz, (K + 1) * kDepthTile); ++k) {
+          int lo = m->h_band_lo[(size_t)o * nz + k], hi = m->h_band_hi[(size_t)o * nz + k];
+          if (hi > lo) {
+            nlo = std::min(nlo, lo);
+            nhi = std::max(nhi, hi);
+          }
+        }
+        if (nhi <= nlo) {
+          nlo = 0;
+          nhi = 0;
+        }
+        nlo &= ~3;
+        nhi = std::min((nhi + 3) & ~3, nt);
+        size_t i = (size_t)o * NK + K;
+        nr[2 * i] = nlo;
+        nr[2 * i + 1] = nhi - nlo;
+        off[i] = total;
+        total += (long long)kDepthTile * (nhi - nlo);
+      }
+    if ((rc = dev_alloc(m, &m->d_adj_nrange, nr.size()))) return rc;
+    if ((rc = dev_alloc(m, &m->d_adj_off, off.size()))) return rc;
+    if ((rc = dev_alloc(m, &m->d_adj, (size_t)total))) return rc;
+    OAM_CUDA_TRY(cudaMemcpyAsync(m->d_adj_nrange, nr.data(), sizeof(int) * nr.size(), cudaMemcpyHostToDevice, st));
+    OAM_CUDA_TRY(cudaMemcpyAsync(m->d_adj_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, st));
+    k_pack_adj<<<O * NK, 256, 0, st>>>(m->d_band, m->d_band_lo, d_band_hi, m->band_w, nz, NK, m->d_adj_nrange,
+                                       m->d_adj_off, m->d_adj);
+    OAM_LAUNCHED();
+    OAM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  cudaFreeAsync(d_orb_b, st);
+  cudaFreeAsync(d_orb_a, st);
+  cudaFreeAsync(d_range, st);
+  cudaFreeAsync(d_band_hi, st);
+  return OAM_OK;
+}
+
+oam_status oam::slab_column(const oam_model *m, int b, int a, int k, float *d_out, cudaStream_t st) {
+  const int o = m->h_tap_orbit[(b + m->R) * m->W + (a + m->R)];
+  k_slab_column<<<(m->grid.nt + 255) / 256, 256, 0, st>>>(m->d_band, m->d_band_lo, m->band_w, m->grid.nz,
+                                                          m->grid.nt, o, k, d_out);
+  OAM_LAUNCHED();
+  return OAM_OK;
+}

@@ -1,0 +1,458 @@
+// LSQR (MB-L2, Eq. 5 with Eq. 6) and FISTA (MB-L1, Eq. 5 with Eq. 7) on the
+// device: FP32 vectors, FP64 norms and scalar recurrences, no host
+// synchronisation inside the iteration loop.
+//
+// Reductions are deterministic: each block reduces a fixed grid-stride slice
+// in a fixed tree, writes one FP64 partial, and the last block to finish (an
+// atomic ticket) sums the partials in index order and runs the scalar update.
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+using namespace oam;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Scalars {
+  // LSQR
+  double alpha, beta, rhobar, phibar, damp;
+  double inv_alpha, inv_beta, cx, cw;
+  double anorm2, arnorm;
+  int iters_done, stop_at;
+  // FISTA / power iteration
+  double mu, L, lambda, t, inv_norm, sum_a, sum_b;
+  unsigned int ticket;
+  unsigned int pad;
+  double partial_a[kRedBlocks];
+  double partial_b[kRedBlocks];
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum (or max) of one double per thread; result valid in thread 0.
+template <bool kMax>
+__device__ double block_reduce(double v) {
+  __shared__ double sh[kThreads / 32];
+  v = kMax ? warp_max(v) : warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < kThreads / 32) ? sh[l] : (kMax ? -INFINITY : 0.0);
+    v = kMax ? warp_max(v) : warp_sum(v);
+  }
+  return v;
+}
+
+// Store this block's partial(s); returns true in every thread of the last block,
+// whose thread 0 then holds the combined totals in *ta / *tb.
+template <bool kMax>
+__device__ bool finish_blocks(Scalars *S, double a, double b, double *ta, double *tb) {
+  __shared__ bool last;
+  a = block_reduce<kMax>(a);
+  b = block_reduce<kMax>(b);
+  if (threadIdx.x == 0) {
+    S->partial_a[blockIdx.x] = a;
+    S->partial_b[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(&S->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double sa = kMax ? -INFINITY : 0.0, sb = kMax ? -INFINITY : 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    const double pa = ((volatile double *)S->partial_a)[i], pb = ((volatile double *)S->partial_b)[i];
+    sa = kMax ? fmax(sa, pa) : sa + pa;
+    sb = kMax ? fmax(sb, pb) : sb + pb;
+  }
+  sa = block_reduce<kMax>(sa);
+  sb = block_reduce<kMax>(sb);
+  if (threadIdx.x == 0) {
+    *ta = sa;
+    *tb = sb;
+    S->ticket = 0;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ generic
+__global__ void k_fill(float *x, size_t n, float v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) x[i] = v;
+}
+
+// dst = src * (*scale); skipped when the iteration is past a stop.
+__global__ void k_scale(float *dst, const float *src, size_t n, const double *scale, const Scalars *S, int it) {
+  if (S && it > S->stop_at) return;
+  const float f = (float)*scale;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i] * f;
+}
+
+// ------------------------------------------------------------------ LSQR
+// beta_1 = ||s||
+__global__ void k_lsqr_beta0(const float *s, size_t n, Scalars *S) {
+  double acc = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = s[i];
+    acc += (double)(v * v);
+  }
+  double ta, tb;
+  if (finish_blocks<false>(S, acc, 0.0, &ta, &tb) && threadIdx.x == 0) {
+    S->beta = sqrt(ta);
+    S->inv_beta = S->beta > 0 ? 1.0 / S->beta : 0.0;
+    S->stop_at = S->beta > 0 ? 0x7fffffff : -1;
+    S->iters_done = 0;
+  }
+}
+
+// alpha_1 = ||A^T u_1||, rhobar = alpha, phibar = beta
+__global__ void k_lsqr_alpha0(const float *th, size_t n, Scalars *S) {
+  double acc = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = th[i];
+    acc += (double)(v * v);
+  }
+  double ta, tb;
+  if (finish_blocks<false>(S, acc, 0.0, &ta, &tb) && threadIdx.x == 0) {
+    S->alpha = sqrt(ta);
+    S->inv_alpha = S->alpha > 0 ? 1.0 / S->alpha : 0.0;
+    if (!(S->alpha > 0)) S->stop_at = -1;
+    S->rhobar = S->alpha;
+    S->phibar = S->beta;
+    S->anorm2 = S->alpha * S->alpha;
+    S->arnorm = S->alpha * S->beta;
+  }
+}
+
+// v = th / alpha, w = v, x = 0
+__global__ void k_lsqr_vw0(const float *th, float *v, float *w, float *x, size_t n, const Scalars *S) {
+  const float ia = (float)S->inv_alpha;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float t = th[i] * ia;
+    v[i] = t;
+    w[i] = t;
+    x[i] = 0.0f;
+  }
+}
+
+// beta u = A v - alpha u   (u updated in place, unnormalised; beta from its norm)
+__global__ void k_lsqr_u(const float *ts, float *u, size_t n, Scalars *S, int it) {
+  if (it > S->stop_at) return;
+  const float al = (float)S->alpha;
+  double acc = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = fmaf(-al, u[i], ts[i]);
+    u[i] = v;
+    acc += (double)(v * v);
+  }
+  double ta, tb;
+  if (finish_blocks<false>(S, acc, 0.0, &ta, &tb) && threadIdx.x == 0) {
+    S->beta = sqrt(ta);
+    S->inv_beta = S->beta > 0 ? 1.0 / S->beta : 0.0;
+    S->anorm2 += S->beta * S->beta + S->damp * S->damp;
+    if (!(S->beta > 0)) S->stop_at = it;
+  }
+}
+
+// alpha v = A^T u - beta v, then the plane rotations (FP64).
+__global__ void k_lsqr_v(const float *th, float *v, size_t n, Scalars *S, int it) {
+  if (it > S->stop_at) return;
+  const float be = (float)S->beta;
+  double acc = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float t = fmaf(-be, v[i], th[i]);
+    v[i] = t;
+    acc += (double)(t * t);
+  }
+  double ta, tb;
+  if (finish_blocks<false>(S, acc, 0.0, &ta, &tb) && threadIdx.x == 0) {
+    const double alpha = sqrt(ta);
+    S->alpha = alpha;
+    S->inv_alpha = alpha > 0 ? 1.0 / alpha : 0.0;
+    S->anorm2 += alpha * alpha;
+    if (!(alpha > 0) && S->stop_at > it) S->stop_at = it;
+    double rhobar = S->rhobar, phibar = S->phibar;
+    double rhobar1 = rhobar;
+    if (S->damp > 0) {
+      rhobar1 = sqrt(rhobar * rhobar + S->damp * S->damp);
+      phibar = (rhobar / rhobar1) * phibar;
+    }
+    const double rho = sqrt(rhobar1 * rhobar1 + S->beta * S->beta);
+    const double c = rhobar1 / rho, sn = S->beta / rho;
+    const double theta = sn * alpha;
+    S->rhobar = -c * alpha;
+    const double phi = c * phibar;
+    S->phibar = sn * phibar;
+    S->cx = phi / rho;
+    S->cw = theta / rho;
+    S->arnorm = fabs(S->phibar * alpha * c);
+    S->iters_done = it + 1;
+  }
+}
+
+// v = vhat / alpha; x += (phi/rho) w; w = v - (theta/rho) w
+__global__ void k_lsqr_xw(float *v, float *w, float *x, size_t n, const Scalars *S, int it) {
+  if (it > S->stop_at) return;
+  const float ia = (float)S->inv_alpha, cx = (float)S->cx, cw = (float)S->cw;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float vv = v[i] * ia;
+    const float ww = w[i];
+    x[i] = fmaf(cx, ww, x[i]);
+    w[i] = fmaf(-cw, ww, vv);
+    v[i] = vv;
+  }
+}
+
+// ------------------------------------------------------------------ FISTA
+// mu = ||A^T A v|| / ||v||, inv_norm = 1 / ||A^T A v||
+__global__ void k_power_norms(const float *th, const float *v, size_t n, Scalars *S) {
+  double a = 0, b = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float p = th[i], q = v[i];
+    a += (double)(p * p);
+    b += (double)(q * q);
+  }
+  double ta, tb;
+  if (finish_blocks<false>(S, a, b, &ta, &tb) && threadIdx.x == 0) {
+    const double nt = sqrt(ta), nv = sqrt(tb);
+    S->mu = nv > 0 ? nt / nv : 0.0;
+    S->inv_norm = nt > 0 ? 1.0 / nt : 0.0;
+    S->L = 2.0 * 1.01 * S->mu;
+  }
+}
+
+// lambda = lambda_rel * max |A^T s|
+__global__ void k_lambda_rel(const float *th, size_t n, Scalars *S, double lambda_rel) {
+  double m = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    m = fmax(m, (double)fabsf(th[i]));
+  double ta, tb;
+  if (finish_blocks<true>(S, m, 0.0, &ta, &tb) && threadIdx.x == 0) S->lambda = lambda_rel * ta;
+}
+
+// r = A Y - s
+__global__ void k_sub(float *r, const float *s, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    r[i] -= s[i];
+}
+
+// x_new = prox(Y - (2/L) g, lambda/L); Y = x_new + ((t-1)/t') (x_new - x); x = x_new; t = t'
+__global__ void k_fista_step(const float *g, float *Y, float *x, size_t n, Scalars *S, int nonneg) {
+  const double t = S->t;
+  const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+  const float mom = (float)((t - 1.0) / tn);
+  const float step = (float)(2.0 / S->L), thr = (float)(S->lambda / S->L);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float z = fmaf(-step, g[i], Y[i]);
+    float xn;
+    if (nonneg)
+      xn = fmaxf(z - thr, 0.0f);
+    else
+      xn = copysignf(fmaxf(fabsf(z) - thr, 0.0f), z);
+    const float xo = x[i];
+    Y[i] = fmaf(mom, xn - xo, xn);
+    x[i] = xn;
+  }
+  double ta, tb;
+  if (finish_blocks<false>(S, 0.0, 0.0, &ta, &tb) && threadIdx.x == 0) S->t = tn;
+}
+
+// objective pieces: sum (A x - s)^2 over signals, sum |x| over the volume
+__global__ void k_objective(const float *ax, const float *s, size_t ns, const float *x, size_t nv, Scalars *S) {
+  double a = 0, b = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ns; i += (size_t)gridDim.x * blockDim.x) {
+    const float r = ax[i] - s[i];
+    a += (double)(r * r);
+  }
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nv; i += (size_t)gridDim.x * blockDim.x)
+    b += (double)fabsf(x[i]);
+  double ta, tb;
+  if (finish_blocks<false>(S, a, b, &ta, &tb) && threadIdx.x == 0) {
+    S->sum_a = ta;
+    S->sum_b = tb;
+  }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct WorkLayout {
+  size_t scal, sig, vol;
+  size_t total(int solver) const {
+    return solver == 0 ? scal + 2 * sig + 3 * vol : scal + sig + 3 * vol;
+  }
+};
+
+WorkLayout layout(const oam_model *m) {
+  WorkLayout L;
+  L.scal = align256(sizeof(Scalars));
+  L.sig = align256(sig_elems(m) * sizeof(float));
+  L.vol = align256(vol_elems(m) * sizeof(float));
+  return L;
+}
+
+int red_grid(const oam_model *m) { return std::min(kRedBlocks, 2 * std::max(1, m->sm_count)); }
+int vec_grid(const oam_model *m) { return 4 * std::max(1, m->sm_count); }
+
+}  // namespace
+
+extern "C" oam_status oam_solver_work_bytes(const oam_model *m, int32_t solver, size_t *bytes) {
+  if (!m || !bytes || (solver != 0 && solver != 1)) return OAM_ERR_INVALID_ARG;
+  *bytes = layout(m).total(solver);
+  return OAM_OK;
+}
+
+#define OAM_LAUNCH_CHECK() OAM_LAUNCHED()
+#define OAM_TRY(expr)               \
+  do {                              \
+    oam_status _r = (expr);         \
+    if (_r != OAM_OK) return _r;    \
+  } while (0)
+
+extern "C" oam_status oam_lsqr(const oam_model *m, const float *d_s, float *d_x, const oam_lsqr_opts *opts,
+                               oam_lsqr_info *info, void *d_work, size_t work_bytes, void *stream) {
+  if (!m || !d_s || !d_x || !opts || !d_work) return OAM_ERR_INVALID_ARG;
+  if (opts->iters < 0 || !(opts->damp >= 0) || !std::isfinite(opts->damp)) return OAM_ERR_INVALID_ARG;
+  const WorkLayout L = layout(m);
+  if (work_bytes < L.total(0) || (reinterpret_cast<uintptr_t>(d_work) & 255)) return OAM_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_s) | reinterpret_cast<uintptr_t>(d_x)) & 15) return OAM_ERR_INVALID_ARG;
+  cudaStream_t st = as_stream(stream);
+  char *base = static_cast<char *>(d_work);
+  Scalars *S = reinterpret_cast<Scalars *>(base);
+  float *u = reinterpret_cast<float *>(base + L.scal);
+  float *ts = reinterpret_cast<float *>(base + L.scal + L.sig);
+  float *v = reinterpret_cast<float *>(base + L.scal + 2 * L.sig);
+  float *w = reinterpret_cast<float *>(base + L.scal + 2 * L.sig + L.vol);
+  float *th = reinterpret_cast<float *>(base + L.scal + 2 * L.sig + 2 * L.vol);
+  const size_t ns = sig_elems(m), nv = vol_elems(m);
+  const int RG = red_grid(m), VG = vec_grid(m);
+
+  OAM_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(Scalars), st));
+  Scalars init{};
+  init.damp = opts->damp;
+  OAM_CUDA_TRY(cudaMemcpyAsync(&S->damp, &init.damp, sizeof(double), cudaMemcpyHostToDevice, st));
+  k_lsqr_beta0<<<RG, kThreads, 0, st>>>(d_s, ns, S);
+  OAM_LAUNCH_CHECK();
+  k_scale<<<VG, kThreads, 0, st>>>(u, d_s, ns, &S->inv_beta, nullptr, 0);
+  OAM_LAUNCH_CHECK();
+  OAM_TRY(apply_adjoint(m, u, th, st));
+  k_lsqr_alpha0<<<RG, kThreads, 0, st>>>(th, nv, S);
+  OAM_LAUNCH_CHECK();
+  k_lsqr_vw0<<<VG, kThreads, 0, st>>>(th, v, w, d_x, nv, S);
+  OAM_LAUNCH_CHECK();
+  for (int it = 0; it < opts->iters; ++it) {
+    OAM_TRY(apply_forward(m, v, ts, st));
+    k_lsqr_u<<<RG, kThreads, 0, st>>>(ts, u, ns, S, it);
+    OAM_LAUNCH_CHECK();
+    k_scale<<<VG, kThreads, 0, st>>>(u, u, ns, &S->inv_beta, S, it);
+    OAM_LAUNCH_CHECK();
+    OAM_TRY(apply_adjoint(m, u, th, st));
+    k_lsqr_v<<<RG, kThreads, 0, st>>>(th, v, nv, S, it);
+    OAM_LAUNCH_CHECK();
+    k_lsqr_xw<<<VG, kThreads, 0, st>>>(v, w, d_x, nv, S, it);
+    OAM_LAUNCH_CHECK();
+  }
+  if (info) {
+    Scalars h;
+    OAM_CUDA_TRY(cudaMemcpyAsync(&h, S, offsetof(Scalars, partial_a), cudaMemcpyDeviceToHost, st));
+    OAM_CUDA_TRY(cudaStreamSynchronize(st));
+    info->iters_done = h.iters_done;
+    info->stop_reason = (h.stop_at != 0x7fffffff) ? 1 : 0;
+    info->rnorm = std::fabs(h.phibar);
+    info->arnorm = h.arnorm;
+    info->anorm = std::sqrt(h.anorm2);
+  }
+  return OAM_OK;
+}
+
+extern "C" oam_status oam_l1_fista(const oam_model *m, const float *d_s, float *d_x, const oam_fista_opts *opts,
+                                   oam_fista_info *info, void *d_work, size_t work_bytes, void *stream) {
+  if (!m || !d_s || !d_x || !opts || !d_work) return OAM_ERR_INVALID_ARG;
+  if (opts->iters < 0 || opts->power_iters < 0 || !std::isfinite(opts->lambda) || !std::isfinite(opts->L) ||
+      !std::isfinite(opts->lambda_rel))
+    return OAM_ERR_INVALID_ARG;
+  if (opts->L <= 0 && opts->power_iters < 1) return OAM_ERR_INVALID_ARG;
+  if (opts->lambda < 0 && opts->lambda_rel < 0) return OAM_ERR_INVALID_ARG;
+  const WorkLayout L = layout(m);
+  if (work_bytes < L.total(1) || (reinterpret_cast<uintptr_t>(d_work) & 255)) return OAM_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_s) | reinterpret_cast<uintptr_t>(d_x) |
+       reinterpret_cast<uintptr_t>(opts->d_power_v0)) & 15)
+    return OAM_ERR_INVALID_ARG;
+  cudaStream_t st = as_stream(stream);
+  char *base = static_cast<char *>(d_work);
+  Scalars *S = reinterpret_cast<Scalars *>(base);
+  float *Y = reinterpret_cast<float *>(base + L.scal);
+  float *th = reinterpret_cast<float *>(base + L.scal + L.vol);
+  float *v = reinterpret_cast<float *>(base + L.scal + 2 * L.vol);
+  float *ts = reinterpret_cast<float *>(base + L.scal + 3 * L.vol);
+  const size_t ns = sig_elems(m), nv = vol_elems(m);
+  const int RG = red_grid(m), VG = vec_grid(m);
+
+  OAM_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(Scalars), st));
+  Scalars init{};
+  init.t = 1.0;
+  init.L = opts->L;
+  init.lambda = opts->lambda;
+  OAM_CUDA_TRY(cudaMemcpyAsync(&S->t, &init.t, sizeof(double), cudaMemcpyHostToDevice, st));
+  OAM_CUDA_TRY(cudaMemcpyAsync(&S->L, &init.L, sizeof(double), cudaMemcpyHostToDevice, st));
+  OAM_CUDA_TRY(cudaMemcpyAsync(&S->lambda, &init.lambda, sizeof(double), cudaMemcpyHostToDevice, st));
+  if (opts->L <= 0) {
+    if (opts->d_power_v0)
+      OAM_CUDA_TRY(cudaMemcpyAsync(v, opts->d_power_v0, nv * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    else
+      k_fill<<<VG, kThreads, 0, st>>>(v, nv, 1.0f);
+    OAM_LAUNCH_CHECK();
+    for (int it = 0; it < opts->power_iters; ++it) {
+      OAM_TRY(apply_forward(m, v, ts, st));
+      OAM_TRY(apply_adjoint(m, ts, th, st));
+      k_power_norms<<<RG, kThreads, 0, st>>>(th, v, nv, S);
+      OAM_LAUNCH_CHECK();
+      k_scale<<<VG, kThreads, 0, st>>>(v, th, nv, &S->inv_norm, nullptr, 0);
+      OAM_LAUNCH_CHECK();
+    }
+  }
+  if (opts->lambda < 0) {
+    OAM_TRY(apply_adjoint(m, d_s, th, st));
+    k_lambda_rel<<<RG, kThreads, 0, st>>>(th, nv, S, opts->lambda_rel);
+    OAM_LAUNCH_CHECK();
+  }
+  k_fill<<<VG, kThreads, 0, st>>>(Y, nv, 0.0f);
+  OAM_LAUNCH_CHECK();
+  k_fill<<<VG, kThreads, 0, st>>>(d_x, nv, 0.0f);
+  OAM_LAUNCH_CHECK();
+  for (int it = 0; it < opts->iters; ++it) {
+    OAM_TRY(apply_forward(m, Y, ts, st));
+    k_sub<<<VG, kThreads, 0, st>>>(ts, d_s, ns);
+    OAM_LAUNCH_CHECK();
+    OAM_TRY(apply_adjoint(m, ts, th, st));
+    k_fista_step<<<RG, kThreads, 0, st>>>(th, Y, d_x, nv, S, opts->nonneg);
+    OAM_LAUNCH_CHECK();
+  }
+  if (opts->compute_objective) {
+    OAM_TRY(apply_forward(m, d_x, ts, st));
+    k_objective<<<RG, kThreads, 0, st>>>(ts, d_s, ns, d_x, nv, S);
+    OAM_LAUNCH_CHECK();
+  }
+  if (info) {
+    Scalars h;
+    OAM_CUDA_TRY(cudaMemcpyAsync(&h, S, offsetof(Scalars, partial_a), cudaMemcpyDeviceToHost, st));
+    OAM_CUDA_TRY(cudaStreamSynchronize(st));
+    info->iters_done = opts->iters;
+    info->L = h.L;
+    info->lambda = h.lambda;
+    info->mu = h.mu;
+    info->objective = opts->compute_objective ? h.sum_a + h.lambda * h.sum_b : NAN;
+  }
+  return OAM_OK;
+}
