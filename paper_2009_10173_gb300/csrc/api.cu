@@ -103,7 +103,7 @@ void free_model(oam_model *m) {
   if (!m) return;
   tc_free(m);
   for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
-  void *ptrs[] = {m->d_tap_orbit, m->d_patch, m->d_band_lo, m->d_band, m->d_fwd_krange, m->d_fwd_off,
+  void *ptrs[] = {m->d_status, m->d_tap_orbit, m->d_patch, m->d_band_lo, m->d_band, m->d_fwd_krange, m->d_fwd_off,
                   m->d_fwd, m->d_adj_nrange, m->d_adj_off, m->d_adj};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -243,7 +243,9 @@ oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const
   m->cut = eir->trunc_sigma * m->sigma_s;
   plan_orbits(m);
   cudaStream_t st = as_stream(stream);
-  rc = upload_patches(m, st);
+  rc = dev_alloc(m, &m->d_status, 1);
+  if (!rc && cudaMemsetAsync(m->d_status, 0, sizeof(int), st) != cudaSuccess) rc = OAM_ERR_CUDA;
+  if (!rc) rc = upload_patches(m, st);
   if (!rc) rc = build_slab(m, st);
   if (!rc && precision == OAM_PREC_BF16X3) rc = tc_build(m, st);
   if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = OAM_ERR_CUDA;

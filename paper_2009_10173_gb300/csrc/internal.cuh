@@ -72,9 +72,15 @@ struct oam_model {
   long long *d_adj_off = nullptr;
   float *d_adj = nullptr;
 
-  // tensor-core layouts (OAM_PREC_BF16X3)
+  // tensor-core layouts (OAM_PREC_BF16X3) and the staging buffer for the
+  // split-BF16 copy of the operator input ([chunks][qtot][8] hi, then lo)
   oam::TcLayout *tc_fwd = nullptr;
   oam::TcLayout *tc_adj = nullptr;
+  uint8_t *d_tc_pack = nullptr;
+  size_t tc_pack_bytes = 0;
+  long long tc_qtot = 0;
+
+  int *d_status = nullptr;  // device error word (bounded waits that ran out)
 
   // operator timing (oam_profile_enable / oam_profile_read)
   struct Prof {
@@ -136,6 +142,7 @@ oam_status tc_build(oam_model *m, cudaStream_t st);
 void tc_free(oam_model *m);
 oam_status forward_tc(const oam_model *m, const float *H, float *s, cudaStream_t st);
 oam_status adjoint_tc(const oam_model *m, const float *s, float *H, cudaStream_t st);
+double tc_exec_flops(const oam_model *m);
 
 // dispatch on the model's precision
 oam_status apply_forward(const oam_model *m, const float *H, float *s, cudaStream_t st);
