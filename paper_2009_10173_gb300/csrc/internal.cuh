@@ -79,6 +79,8 @@ struct oam_model {
   uint8_t *d_tc_pack = nullptr;
   size_t tc_pack_bytes = 0;
   long long tc_qtot = 0;
+  float *d_tc_part = nullptr;  // per-part partial sums of the tensor-core operators
+  int tc_rows_per_part = 0;
 
   int *d_status = nullptr;  // device error word (bounded waits that ran out)
 

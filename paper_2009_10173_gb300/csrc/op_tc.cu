@@ -33,6 +33,7 @@ constexpr int kStageK = 32;        // K elements per staged strip (two 16-deep M
 constexpr int kTileM = 128;        // positions per block
 constexpr int kThreads = 192;      // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
 constexpr int kSmemLimit = 227 * 1024;
+constexpr int kRowsPerPart = 1;    // tap rows per block (split over blockIdx.y)
 
 struct TcItem {
   long long off;  // byte offset of the item's tiles in data
@@ -74,8 +75,9 @@ struct CorrParams {
   const uint8_t *data;
   int slot_bytes, n_slots, strip_rows;
   int acc_cols, tmem_cols;
-  float *out;
-  int out_len, out_lo;
+  float *part;            // partial sums [parts][py*px][acc_cols]
+  size_t part_stride;     // py*px
+  int rows_per_part;      // tap rows (b) handled by one part (blockIdx.y)
   int *status;
   long long budget;
 };
@@ -138,7 +140,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
     if (lane == 0) {
       int it_strip = 0, it_slab = 0;
       bool ok = true;
-      for (int b = -p.R; b <= p.R && ok; ++b) {
+      const int b_lo = -p.R + (int)blockIdx.y * p.rows_per_part, b_hi = min(p.R, b_lo + p.rows_per_part - 1);
+      for (int b = b_lo; b <= b_hi && ok; ++b) {
         if (row_skipped(p, tile, b)) continue;
         const long long q_base =
             (long long)(p.R + 1) * p.wp + (long long)tile * kTileM + (long long)(p.dir == 0 ? b : -b) * p.wp - p.R;
@@ -189,7 +192,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
       ptx::tc_fence_after();
       int it_strip = 0, it_slab = 0;
       const uint32_t lbo_a = (uint32_t)L * 16u;
-      for (int b = -p.R; b <= p.R && ok; ++b) {
+      const int b_lo = -p.R + (int)blockIdx.y * p.rows_per_part, b_hi = min(p.R, b_lo + p.rows_per_part - 1);
+      for (int b = b_lo; b <= b_hi && ok; ++b) {
         if (row_skipped(p, tile, b)) continue;
         for (int st = 0; st < p.stages && ok; ++st) {
           const int s = it_strip & 1;
@@ -251,42 +255,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
     const long long qf = (long long)tile * kTileM + m;
     const int y = (int)(qf / p.wp), x = (int)(qf % p.wp);
     const bool valid = ok && y < p.py && x < p.px;
-    float *row = p.out + ((size_t)y * p.px + x) * p.out_len;
-    const bool vec = (p.out_len & 3) == 0 && (p.out_lo & 3) == 0;
-    if (valid) {
-      if (vec)
-        for (int n = 0; n < p.out_lo && n < p.out_len; n += 4)
-          *reinterpret_cast<float4 *>(row + n) = make_float4(0.f, 0.f, 0.f, 0.f);
-      else
-        for (int n = 0; n < p.out_lo && n < p.out_len; ++n) row[n] = 0.0f;
-    }
+    // this part's partial sums: part[blockIdx.y][y*px + x][0 .. acc_cols)
+    float *row = p.part + ((size_t)blockIdx.y * p.part_stride + (size_t)y * p.px + x) * p.acc_cols;
     if (ok) {
       for (int col = 0; col < p.acc_cols; col += 32) {
         uint32_t r[32];
         ptx::tmem_ld32(tmem + lane_base + (uint32_t)col, r);
         ptx::tmem_wait_ld();
         if (valid) {
-          const int n0 = p.out_lo + col;
-          if (n0 + 32 <= p.out_len && vec) {
-            float4 *dst = reinterpret_cast<float4 *>(row + n0);
+          float4 *dst = reinterpret_cast<float4 *>(row + col);
+          const int nv = min(8, (p.acc_cols - col) >> 2);
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
+          for (int j = 0; j < 8; ++j)
+            if (j < nv)
               dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
                                    __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (n0 + j < p.out_len) row[n0 + j] = __uint_as_float(r[j]);
-          }
         }
       }
-    }
-    if (valid) {
-      if (vec)
-        for (int n = p.out_lo + p.acc_cols; n < p.out_len; n += 4)
-          *reinterpret_cast<float4 *>(row + n) = make_float4(0.f, 0.f, 0.f, 0.f);
-      else
-        for (int n = p.out_lo + p.acc_cols; n < p.out_len; ++n) row[n] = 0.0f;
     }
     ptx::tc_fence_before();
   }
@@ -355,6 +340,23 @@ __global__ void k_pack_input(const float *__restrict__ in, int len, int first, i
     }
     out_hi[i] = *reinterpret_cast<uint4 *>(h);
     out_lo[i] = *reinterpret_cast<uint4 *>(l);
+  }
+}
+
+// out[pos][n] = sum over parts (in index order) of part[.][pos][n - out_lo] for n
+// in the accumulator range, 0 elsewhere.  Every element of out is written.
+__global__ void k_sum_parts(const float *__restrict__ part, int parts, size_t npos, int acc_cols, int out_lo,
+                            int out_len, float *__restrict__ out) {
+  const size_t total = npos * (size_t)out_len;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t pos = i / out_len;
+    const int n = (int)(i % out_len), c = n - out_lo;
+    float v = 0.0f;
+    if (c >= 0 && c < acc_cols) {
+      const float *src = part + pos * acc_cols + c;
+      for (int q = 0; q < parts; ++q) v += src[(size_t)q * npos * acc_cols];
+    }
+    out[i] = v;
   }
 }
 
@@ -464,6 +466,7 @@ oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d
 
 oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int in_len, float *out, int out_len,
                     cudaStream_t st) {
+  if (!m->d_tc_part) return OAM_ERR_UNSUPPORTED;
   const int R = m->R, wp = m->grid.px + R;
   const long long qtot = m->tc_qtot;
   uint8_t *hi = m->d_tc_pack, *lo = m->d_tc_pack + (size_t)L->chunks8 * qtot * 16;
@@ -495,16 +498,23 @@ oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int 
   if (p.n_slots < 2) return OAM_ERR_UNSUPPORTED;
   p.acc_cols = L->acc_cols;
   p.tmem_cols = L->tmem_cols;
-  p.out = out;
-  p.out_len = out_len;
-  p.out_lo = L->out_lo;
+  p.part = m->d_tc_part;
+  p.part_stride = (size_t)m->grid.py * m->grid.px;
+  p.rows_per_part = m->tc_rows_per_part;
   p.status = m->d_status;
   p.budget = 4000000000LL;  // ~2 s at 2 GHz
   const size_t smem = 512 + 2 * (size_t)strip_bytes + (size_t)p.n_slots * p.slot_bytes;
   OAM_CUDA_TRY(cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int n_tiles = (int)(((long long)m->grid.py * wp + kTileM - 1) / kTileM);
-  ProfScope prof(m, st, L->dir == 0);
-  k_corr_tc<<<n_tiles, kThreads, smem, st>>>(p);
+  const int parts = (m->W + m->tc_rows_per_part - 1) / m->tc_rows_per_part;
+  {
+    ProfScope prof(m, st, L->dir == 0);
+    k_corr_tc<<<dim3(n_tiles, parts), kThreads, smem, st>>>(p);
+    OAM_LAUNCHED();
+  }
+  const size_t npos = (size_t)m->grid.py * m->grid.px;
+  const int blocks = (int)std::min<size_t>((npos * out_len + 255) / 256, 16ull * m->sm_count);
+  k_sum_parts<<<blocks, 256, 0, st>>>(m->d_tc_part, parts, npos, L->acc_cols, L->out_lo, out_len, out);
   OAM_LAUNCHED();
   return OAM_OK;
 }
@@ -530,6 +540,13 @@ oam_status oam::tc_build(oam_model *m, cudaStream_t st) {
   m->tc_pack_bytes = 2ull * chunks * m->tc_qtot * 16;
   rc = dev_alloc(m, &m->d_tc_pack, m->tc_pack_bytes);
   if (rc) return rc;
+  // Split of the tap rows over blocks: bounds the MMA steps summed into one
+  // tensor-memory accumulator; the parts are added in FP32 in a fixed order.
+  m->tc_rows_per_part = kRowsPerPart;
+  const int parts = (m->W + kRowsPerPart - 1) / kRowsPerPart;
+  const int acc = std::max(m->tc_fwd->acc_cols, m->tc_adj->acc_cols);
+  rc = dev_alloc(m, &m->d_tc_part, (size_t)parts * m->grid.py * m->grid.px * acc);
+  if (rc) return rc;
   OAM_CUDA_TRY(cudaMemsetAsync(m->d_tc_pack, 0, m->tc_pack_bytes, st));
   return OAM_OK;
 }
@@ -544,6 +561,8 @@ void oam::tc_free(oam_model *m) {
   m->tc_fwd = m->tc_adj = nullptr;
   if (m->d_tc_pack) cudaFree(m->d_tc_pack);
   m->d_tc_pack = nullptr;
+  if (m->d_tc_part) cudaFree(m->d_tc_part);
+  m->d_tc_part = nullptr;
 }
 
 double oam::tc_exec_flops(const oam_model *m) {
