@@ -1,0 +1,58 @@
+"""Run one operator (or solver) repeatedly on a synthetic workload.
+
+A small command-line driver for profiling and timing through the C-ABI:
+
+    python -m paper_2009_10173_gb300.run_op --op forward --prec bf16x3 \\
+        --px 96 --py 96 --nz 300 --nt 1024 --win 61 --reps 3
+
+prints one JSON line with the mean CUDA-event time per call.
+"""
+import argparse
+import json
+
+import torch
+
+from . import binding as B
+from . import configs, inputs
+from .model import Model
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--op", default="forward", choices=["forward", "adjoint", "lsqr", "fista"])
+    p.add_argument("--prec", default="bf16x3", choices=["fp32", "bf16x3"])
+    p.add_argument("--workload", default="volume_200x200x300", choices=sorted(configs.WORKLOADS))
+    for k in ("px", "py", "nz", "nt", "win", "iters"):
+        p.add_argument(f"--{k}", type=int, default=None)
+    p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=1)
+    a = p.parse_args()
+    over = {k: getattr(a, k) for k in ("px", "py", "nz", "nt", "win") if getattr(a, k) is not None}
+    cfg = configs.scaled(configs.WORKLOADS[a.workload], **over)
+    prec = B.OAM_PREC_BF16X3 if a.prec == "bf16x3" else B.OAM_PREC_FP32
+    m = Model(cfg, precision=prec)
+    H = torch.from_numpy(inputs.phantom(cfg, 1, count=20)).float().cuda()
+    s = m.forward(H)
+    iters = a.iters or 5
+    run = {"forward": lambda: m.forward(H, out=s), "adjoint": lambda: m.adjoint(s),
+           "lsqr": lambda: m.lsqr(s, iters, want_info=False),
+           "fista": lambda: m.fista(s, iters, power_iters=2, want_info=False)}[a.op]
+    for _ in range(a.warmup):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    print(json.dumps({"op": a.op, "prec": a.prec, "grid": [cfg["py"], cfg["px"], cfg["nz"], cfg["nt"], cfg["win"]],
+                      "ms_per_call": ms, "flops_per_op": m.info.flops_per_op,
+                      "alg_tflops": m.info.flops_per_op / ms / 1e9 if a.op in ("forward", "adjoint") else None,
+                      "model_bytes": m.info.device_bytes}))
+    m.close()
+
+
+if __name__ == "__main__":
+    main()
