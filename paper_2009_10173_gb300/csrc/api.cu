@@ -276,6 +276,8 @@ oam_status oam_model_get_info(const oam_model *m, oam_model_info *info) {
   info->nnz = m->nnz;
   info->flops_per_op = m->flops;
   info->device_bytes = m->bytes;
+  info->exec_flops_forward = tc_exec_flops(m, 0);
+  info->exec_flops_adjoint = tc_exec_flops(m, 1);
   return OAM_OK;
 }
 

@@ -80,7 +80,6 @@ struct oam_model {
   size_t tc_pack_bytes = 0;
   long long tc_qtot = 0;
   float *d_tc_part = nullptr;  // per-part partial sums of the tensor-core operators
-  int tc_rows_per_part = 0;
 
   int *d_status = nullptr;  // device error word (bounded waits that ran out)
 
@@ -144,7 +143,7 @@ oam_status tc_build(oam_model *m, cudaStream_t st);
 void tc_free(oam_model *m);
 oam_status forward_tc(const oam_model *m, const float *H, float *s, cudaStream_t st);
 oam_status adjoint_tc(const oam_model *m, const float *s, float *H, cudaStream_t st);
-double tc_exec_flops(const oam_model *m);
+double tc_exec_flops(const oam_model *m, int dir);
 
 // dispatch on the model's precision
 oam_status apply_forward(const oam_model *m, const float *H, float *s, cudaStream_t st);

@@ -33,13 +33,12 @@ constexpr int kStageK = 32;        // K elements per staged strip (two 16-deep M
 constexpr int kTileM = 128;        // positions per block
 constexpr int kThreads = 192;      // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
 constexpr int kSmemLimit = 227 * 1024;
-constexpr int kRowsPerPart = 1;    // tap rows per block (split over blockIdx.y)
 
-struct TcItem {
-  long long off;  // byte offset of the item's tiles in data
-  int bytes;      // total bytes (hi + lo of both tiles)
-  short col[2];   // accumulator column of each tile
-  short n[2];     // MMA N of each tile (0 = no tile)
+struct __align__(16) TcItem {
+  uint32_t off16;    // byte offset of the item's tiles in data, in 16-byte units
+  uint32_t bytes;    // total bytes (hi + lo of both tiles)
+  uint16_t col[2];   // accumulator column of each tile
+  uint16_t n[2];     // MMA N of each tile (0 = no tile)
 };
 
 struct TcTile {
@@ -73,11 +72,10 @@ struct CorrParams {
   const int *tap_orbit;
   const TcItem *items;  // [n_orb][stages]
   const uint8_t *data;
-  int slot_bytes, n_slots, strip_rows;
+  int slot_bytes, n_slots, strip_rows, items_bytes;
   int acc_cols, tmem_cols;
-  float *part;            // partial sums [parts][py*px][acc_cols]
+  float *part;            // partial sums [W][py*px][acc_cols], one slice per tap row b
   size_t part_stride;     // py*px
-  int rows_per_part;      // tap rows (b) handled by one part (blockIdx.y)
   int *status;
   long long budget;
 };
@@ -100,11 +98,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
   volatile int *never = reinterpret_cast<volatile int *>(smem + 264);  // stays 0: waits that ignore abort
   const int L = p.strip_rows;
   const uint32_t strip_bytes = (uint32_t)L * 16u * 4u * 2u;  // 4 chunks of 8, hi + lo
-  uint8_t *strips = smem + 512;
+  TcItem *sitems = reinterpret_cast<TcItem *>(smem + 512);  // [stages][W] for this block's row
+  uint8_t *strips = smem + 512 + p.items_bytes;
   uint8_t *slots = strips + 2 * strip_bytes;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x;
+  const int b = (int)blockIdx.y - p.R;  // this block's tap row
+  const bool skip_row = row_skipped(p, tile, b);
 
   if (threadIdx.x == 0) {
     ptx::mbar_init(&strip_full[0], 1);
@@ -120,6 +121,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
     *abort_flag = 0;
     *never = 0;
     ptx::mbar_fence_init();
+  }
+  if (warp == 0 && !skip_row) {
+    const int n = p.stages * p.W;
+    for (int i = lane; i < n; i += 32) {
+      const int st = i / p.W, ai = i % p.W;
+      sitems[i] = p.items[p.tap_orbit[(b + p.R) * p.W + ai] * p.stages + st];
+    }
   }
   if (warp == 1) {
     ptx::tmem_alloc(tmem_slot, p.tmem_cols);
@@ -140,9 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
     if (lane == 0) {
       int it_strip = 0, it_slab = 0;
       bool ok = true;
-      const int b_lo = -p.R + (int)blockIdx.y * p.rows_per_part, b_hi = min(p.R, b_lo + p.rows_per_part - 1);
-      for (int b = b_lo; b <= b_hi && ok; ++b) {
-        if (row_skipped(p, tile, b)) continue;
+      if (!skip_row) {
         const long long q_base =
             (long long)(p.R + 1) * p.wp + (long long)tile * kTileM + (long long)(p.dir == 0 ? b : -b) * p.wp - p.R;
         for (int st = 0; st < p.stages && ok; ++st) {
@@ -160,17 +166,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
             ptx::bulk_g2s(dst + (4 + c) * L * 16, p.in_lo + src, L * 16, &strip_full[s]);
           }
           ++it_strip;
-          for (int a = -p.R; a <= p.R; ++a) {
-            const TcItem item = p.items[p.tap_orbit[(b + p.R) * p.W + (a + p.R)] * p.stages + st];
+          const TcItem *row_items = sitems + st * p.W;
+          for (int ai = 0; ai < p.W; ++ai) {
+            const TcItem item = row_items[ai];
             const int slot = it_slab % p.n_slots;
             if (!ptx::mbar_wait(&slab_empty[slot], ((it_slab / p.n_slots) & 1) ^ 1, abort_flag, p.budget)) {
               fail(2);
               ok = false;
               break;
             }
-            ptx::mbar_arrive_expect_tx(&slab_full[slot], (uint32_t)item.bytes);
+            ptx::mbar_arrive_expect_tx(&slab_full[slot], item.bytes);
             if (item.bytes > 0)
-              ptx::bulk_g2s(slots + (size_t)slot * p.slot_bytes, p.data + item.off, (uint32_t)item.bytes,
+              ptx::bulk_g2s(slots + (size_t)slot * p.slot_bytes, p.data + (size_t)item.off16 * 16, item.bytes,
                             &slab_full[slot]);
             ++it_slab;
           }
@@ -192,9 +199,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
       ptx::tc_fence_after();
       int it_strip = 0, it_slab = 0;
       const uint32_t lbo_a = (uint32_t)L * 16u;
-      const int b_lo = -p.R + (int)blockIdx.y * p.rows_per_part, b_hi = min(p.R, b_lo + p.rows_per_part - 1);
-      for (int b = b_lo; b <= b_hi && ok; ++b) {
-        if (row_skipped(p, tile, b)) continue;
+      if (!skip_row) {
         for (int st = 0; st < p.stages && ok; ++st) {
           const int s = it_strip & 1;
           if (!ptx::mbar_wait(&strip_full[s], (it_strip >> 1) & 1, abort_flag, p.budget)) {
@@ -204,8 +209,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
           }
           const uint32_t a_hi = ptx::smem_addr(strips + s * strip_bytes);
           const uint32_t a_lo = a_hi + 4u * lbo_a;
-          for (int a = -p.R; a <= p.R; ++a) {
-            const TcItem item = p.items[p.tap_orbit[(b + p.R) * p.W + (a + p.R)] * p.stages + st];
+          const TcItem *row_items = sitems + st * p.W;
+          for (int ai = 0; ai < p.W; ++ai) {
+            const TcItem item = row_items[ai];
             const int slot = it_slab % p.n_slots;
             if (!ptx::mbar_wait(&slab_full[slot], (it_slab / p.n_slots) & 1, abort_flag, p.budget)) {
               fail(16);
@@ -213,18 +219,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
               break;
             }
             ptx::tc_fence_after();
-            const uint32_t shift = (uint32_t)(p.dir == 0 ? a + p.R : p.R - a) * 16u;
+            // tap a = ai - R: forward reads row m + R + a, adjoint row m + R - a
+            const uint32_t shift = (uint32_t)(p.dir == 0 ? ai : 2 * p.R - ai) * 16u;
             uint32_t b_addr = ptx::smem_addr(slots + (size_t)slot * p.slot_bytes);
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-              const uint32_t N = (uint32_t)item.n[c];
+              const uint32_t N = item.n[c];
               if (N == 0) continue;
               const uint32_t idesc = ptx::idesc_bf16_f32(kTileM, N);
               const uint64_t dah = ptx::smem_desc(a_hi + 2u * c * lbo_a + shift, lbo_a, 128);
               const uint64_t dal = ptx::smem_desc(a_lo + 2u * c * lbo_a + shift, lbo_a, 128);
               const uint64_t dbh = ptx::smem_desc(b_addr, N * 16u, 128);
               const uint64_t dbl = ptx::smem_desc(b_addr + N * 32u, N * 16u, 128);
-              const uint32_t d = tmem + (uint32_t)item.col[c];
+              const uint32_t d = tmem + item.col[c];
               ptx::mma_bf16(d, dah, dbh, idesc, 1);
               ptx::mma_bf16(d, dah, dbl, idesc, 1);
               ptx::mma_bf16(d, dal, dbh, idesc, 1);
@@ -394,7 +401,9 @@ oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d
   for (int o = 0; o < O; ++o) {
     for (int s = 0; s < L->stages; ++s) {
       TcItem it{};
-      it.off = off;
+      const long long item_off = off;
+      if (off / 16 > 0xFFFFFFFFLL) return OAM_ERR_UNSUPPORTED;
+      it.off16 = (uint32_t)(off / 16);
       for (int c = 0; c < 2; ++c) {
         const int chunk = 2 * s + c;
         int lo = 1 << 30, hi = -1;
@@ -424,28 +433,39 @@ oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d
         const int col = lo & ~15;
         const int n = ((hi - col) + 15) & ~15;
         if (n > 256 || col + n > L->acc_cols) return OAM_ERR_UNSUPPORTED;
-        it.col[c] = (short)col;
-        it.n[c] = (short)n;
+        it.col[c] = (uint16_t)col;
+        it.n[c] = (uint16_t)n;
         tiles.push_back(TcTile{o, chunk, col, n, off});
         off += 64LL * n;  // hi + lo: 2 x (n rows x 16 elements x 2 bytes)
         flops_cols += 16.0 * n;
       }
-      it.bytes = (int)(off - it.off);
-      max_item = std::max(max_item, it.bytes);
+      it.bytes = (uint32_t)(off - item_off);
+      max_item = std::max(max_item, (int)it.bytes);
       items[(size_t)o * L->stages + s] = it;
     }
   }
   L->slot_bytes = (max_item + 127) & ~127;
   L->data_bytes = (size_t)std::max<long long>(off, 16);
-  // executed MMA flops of one application: per tap (via its orbit) and in-grid position tile
+  // executed MMA flops of one application: 3 products x 2 x M x (16 x N) summed
+  // over the (position tile, tap row) blocks whose row meets the grid
   {
     std::vector<double> orb_cols(O, 0.0);
     for (const TcTile &t : tiles) orb_cols[t.orbit] += 16.0 * t.n;
-    const int wp = m->grid.px + m->R;
-    const double n_tiles = std::ceil((double)m->grid.py * wp / kTileM);
-    double per_tile = 0;
-    for (int t = 0; t < m->W * m->W; ++t) per_tile += orb_cols[m->h_tap_orbit[t]];
-    L->exec_flops = 3.0 * 2.0 * kTileM * per_tile * n_tiles;  // upper bound: rows beyond the grid are skipped
+    const int wp = m->grid.px + m->R, W = m->W, R = m->R;
+    const long long n_tiles = ((long long)m->grid.py * wp + kTileM - 1) / kTileM;
+    std::vector<double> row_cols(W, 0.0);
+    for (int bi = 0; bi < W; ++bi)
+      for (int ai = 0; ai < W; ++ai) row_cols[bi] += orb_cols[m->h_tap_orbit[bi * W + ai]];
+    double total = 0;
+    for (long long t = 0; t < n_tiles; ++t) {
+      const long long yf = t * kTileM / wp, yl = (t * kTileM + kTileM - 1) / wp;
+      for (int bi = 0; bi < W; ++bi) {
+        const int off = dir == 0 ? bi - R : R - bi;
+        if (yl + off < 0 || yf + off >= m->grid.py) continue;
+        total += row_cols[bi];
+      }
+    }
+    L->exec_flops = 3.0 * 2.0 * kTileM * total;
   }
   oam_status rc;
   if ((rc = dev_alloc(m, &L->d_items, items.size()))) return rc;
@@ -494,19 +514,19 @@ oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int 
   p.slot_bytes = L->slot_bytes;
   p.strip_rows = kTileM + 2 * R;
   const int strip_bytes = p.strip_rows * 16 * 8;
-  p.n_slots = std::min(12, (kSmemLimit - 512 - 2 * strip_bytes) / L->slot_bytes);
+  p.n_slots = std::min(12, (kSmemLimit - 512 - p.items_bytes - 2 * strip_bytes) / L->slot_bytes);
   if (p.n_slots < 2) return OAM_ERR_UNSUPPORTED;
   p.acc_cols = L->acc_cols;
   p.tmem_cols = L->tmem_cols;
   p.part = m->d_tc_part;
   p.part_stride = (size_t)m->grid.py * m->grid.px;
-  p.rows_per_part = m->tc_rows_per_part;
+  p.items_bytes = (int)((sizeof(TcItem) * L->stages * m->W + 127) & ~size_t(127));
   p.status = m->d_status;
   p.budget = 4000000000LL;  // ~2 s at 2 GHz
-  const size_t smem = 512 + 2 * (size_t)strip_bytes + (size_t)p.n_slots * p.slot_bytes;
+  const size_t smem = 512 + (size_t)p.items_bytes + 2 * (size_t)strip_bytes + (size_t)p.n_slots * p.slot_bytes;
   OAM_CUDA_TRY(cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int n_tiles = (int)(((long long)m->grid.py * wp + kTileM - 1) / kTileM);
-  const int parts = (m->W + m->tc_rows_per_part - 1) / m->tc_rows_per_part;
+  const int parts = m->W;  // one tap row per block
   {
     ProfScope prof(m, st, L->dir == 0);
     k_corr_tc<<<dim3(n_tiles, parts), kThreads, smem, st>>>(p);
@@ -540,10 +560,9 @@ oam_status oam::tc_build(oam_model *m, cudaStream_t st) {
   m->tc_pack_bytes = 2ull * chunks * m->tc_qtot * 16;
   rc = dev_alloc(m, &m->d_tc_pack, m->tc_pack_bytes);
   if (rc) return rc;
-  // Split of the tap rows over blocks: bounds the MMA steps summed into one
-  // tensor-memory accumulator; the parts are added in FP32 in a fixed order.
-  m->tc_rows_per_part = kRowsPerPart;
-  const int parts = (m->W + kRowsPerPart - 1) / kRowsPerPart;
+  // One block per (position tile, tap row): bounds the MMA steps summed into
+  // one tensor-memory accumulator; the rows are added in FP32 in a fixed order.
+  const int parts = m->W;
   const int acc = std::max(m->tc_fwd->acc_cols, m->tc_adj->acc_cols);
   rc = dev_alloc(m, &m->d_tc_part, (size_t)parts * m->grid.py * m->grid.px * acc);
   if (rc) return rc;
@@ -565,8 +584,9 @@ void oam::tc_free(oam_model *m) {
   m->d_tc_part = nullptr;
 }
 
-double oam::tc_exec_flops(const oam_model *m) {
-  return m->tc_fwd ? m->tc_fwd->exec_flops + 0.0 : 0.0;
+double oam::tc_exec_flops(const oam_model *m, int dir) {
+  const TcLayout *L = dir == 0 ? m->tc_fwd : m->tc_adj;
+  return L ? L->exec_flops : 0.0;
 }
 
 oam_status oam::forward_tc(const oam_model *m, const float *H, float *s, cudaStream_t st) {
