@@ -88,6 +88,22 @@ __device__ bool finish_blocks(Scalars *S, double a, double b, double *ta, double
 }
 
 // ------------------------------------------------------------------ generic
+// Reset the scalar block (ticket, partials untouched: each reduction writes
+// its partials before reading them) and set the solver's starting scalars.
+__global__ void k_init_scalars(Scalars *S, double damp, double t, double L, double lambda) {
+  S->alpha = S->beta = S->rhobar = S->phibar = 0.0;
+  S->inv_alpha = S->inv_beta = S->cx = S->cw = 0.0;
+  S->anorm2 = S->arnorm = 0.0;
+  S->iters_done = 0;
+  S->stop_at = 0x7fffffff;
+  S->mu = S->inv_norm = S->sum_a = S->sum_b = 0.0;
+  S->damp = damp;
+  S->t = t;
+  S->L = L;
+  S->lambda = lambda;
+  S->ticket = 0;
+}
+
 __global__ void k_fill(float *x, size_t n, float v) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) x[i] = v;
 }
@@ -338,10 +354,8 @@ extern "C" oam_status oam_lsqr(const oam_model *m, const float *d_s, float *d_x,
   const size_t ns = sig_elems(m), nv = vol_elems(m);
   const int RG = red_grid(m), VG = vec_grid(m);
 
-  OAM_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(Scalars), st));
-  Scalars init{};
-  init.damp = opts->damp;
-  OAM_CUDA_TRY(cudaMemcpyAsync(&S->damp, &init.damp, sizeof(double), cudaMemcpyHostToDevice, st));
+  k_init_scalars<<<1, 1, 0, st>>>(S, opts->damp, 1.0, 0.0, 0.0);
+  OAM_LAUNCH_CHECK();
   k_lsqr_beta0<<<RG, kThreads, 0, st>>>(d_s, ns, S);
   OAM_LAUNCH_CHECK();
   k_scale<<<VG, kThreads, 0, st>>>(u, d_s, ns, &S->inv_beta, nullptr, 0);
@@ -399,14 +413,8 @@ extern "C" oam_status oam_l1_fista(const oam_model *m, const float *d_s, float *
   const size_t ns = sig_elems(m), nv = vol_elems(m);
   const int RG = red_grid(m), VG = vec_grid(m);
 
-  OAM_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(Scalars), st));
-  Scalars init{};
-  init.t = 1.0;
-  init.L = opts->L;
-  init.lambda = opts->lambda;
-  OAM_CUDA_TRY(cudaMemcpyAsync(&S->t, &init.t, sizeof(double), cudaMemcpyHostToDevice, st));
-  OAM_CUDA_TRY(cudaMemcpyAsync(&S->L, &init.L, sizeof(double), cudaMemcpyHostToDevice, st));
-  OAM_CUDA_TRY(cudaMemcpyAsync(&S->lambda, &init.lambda, sizeof(double), cudaMemcpyHostToDevice, st));
+  k_init_scalars<<<1, 1, 0, st>>>(S, 0.0, 1.0, opts->L, opts->lambda);
+  OAM_LAUNCH_CHECK();
   if (opts->L <= 0) {
     if (opts->d_power_v0)
       OAM_CUDA_TRY(cudaMemcpyAsync(v, opts->d_power_v0, nv * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -456,3 +464,4 @@ extern "C" oam_status oam_l1_fista(const oam_model *m, const float *d_s, float *
   }
   return OAM_OK;
 }
+
