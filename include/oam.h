@@ -98,6 +98,9 @@ typedef struct {
   int64_t nnz;         /* nonzero slab entries over all win*win*nz columns */
   double flops_per_op; /* algorithmic flops of one forward (= one adjoint): 2*px*py*nnz_in_grid */
   size_t device_bytes; /* device memory owned by the model */
+  double exec_flops_forward, exec_flops_adjoint; /* tensor-core flops issued per application
+                                                    (3 BF16 products, band and tile padding);
+                                                    0 for OAM_PREC_FP32 */
 } oam_model_info;
 
 /* Build the model slab on the device (Methods: Forward modeling, Eqs. 1-4;
@@ -173,6 +176,23 @@ typedef struct {
 
 oam_status oam_l1_fista(const oam_model *model, const float *d_s, float *d_x, const oam_fista_opts *opts,
                         oam_fista_info *info, void *d_work, size_t work_bytes, void *stream);
+
+/* LSQR without any device allocation (the paper has no counterpart; this is a
+ * library service).  For callers that cannot call cudaMalloc at solve time:
+ * hosts that reserve all device memory up front for their own allocator, and
+ * latency-critical loops that cannot take an allocation's implicit device
+ * synchronisation.  Same arguments and results as oam_lsqr, but the workspace
+ * is a 32 MiB array in this library's static device memory (every GPU that
+ * loads the library holds it until the process exits), so problems whose
+ * oam_solver_work_bytes(model, 0) exceeds 32 MiB are rejected with
+ * OAM_ERR_INVALID_ARG.  The first call on each device looks the array's
+ * device address up (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call on a device shares the one array, which keeps
+ * the previous call's contents (each call initialises what it reads); calls
+ * that overlap on the GPU race and give wrong results.  No cudaMalloc,
+ * cudaFree or allocating library routine is called. */
+oam_status oam_lsqr_noalloc(const oam_model *model, const float *d_s, float *d_x, const oam_lsqr_opts *opts,
+                            oam_lsqr_info *info, void *stream);
 
 /* Workspace bytes for solver 0 = LSQR, 1 = FISTA. */
 oam_status oam_solver_work_bytes(const oam_model *model, int32_t solver, size_t *bytes);

@@ -18,7 +18,7 @@ OAM_PREC_FP32, OAM_PREC_BF16X3 = 0, 1
 
 EXPORTED = ("oam_build_model", "oam_model_free", "oam_model_get_info", "oam_model_slab_column", "oam_forward",
             "oam_adjoint", "oam_lsqr", "oam_l1_fista", "oam_solver_work_bytes", "oam_status_string",
-            "oam_version", "oam_profile_enable", "oam_profile_read", "oam_launch_count")
+            "oam_version", "oam_profile_enable", "oam_profile_read", "oam_launch_count", "oam_lsqr_noalloc")
 
 
 class OamSensor(ctypes.Structure):
@@ -40,7 +40,8 @@ class OamEir(ctypes.Structure):
 class OamModelInfo(ctypes.Structure):
     _fields_ = [("t0_s", ctypes.c_double), ("n_lo", ctypes.c_int32), ("n_hi", ctypes.c_int32),
                 ("n_orbits", ctypes.c_int32), ("precision", ctypes.c_int32), ("nnz", ctypes.c_int64),
-                ("flops_per_op", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+                ("flops_per_op", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+                ("exec_flops_forward", ctypes.c_double), ("exec_flops_adjoint", ctypes.c_double)]
 
 
 class OamLsqrOpts(ctypes.Structure):
@@ -95,6 +96,7 @@ def lib():
         L.oam_lsqr.argtypes = [vp, vp, vp, P(OamLsqrOpts), P(OamLsqrInfo), vp, sz, vp]
         L.oam_l1_fista.argtypes = [vp, vp, vp, P(OamFistaOpts), P(OamFistaInfo), vp, sz, vp]
         L.oam_solver_work_bytes.argtypes = [vp, i32, P(sz)]
+        L.oam_lsqr_noalloc.argtypes = [vp, vp, vp, P(OamLsqrOpts), P(OamLsqrInfo), vp]
         L.oam_status_string.argtypes = [ctypes.c_int]
         L.oam_status_string.restype = ctypes.c_char_p
         L.oam_version.restype = i32
@@ -182,6 +184,14 @@ def oam_lsqr(model, s, x, opts, work, stream=None, want_info=True):
     _check("oam_lsqr", lib().oam_lsqr(model, _ptr(s), _ptr(x), ctypes.byref(opts),
                                       ctypes.byref(info) if want_info else None, _ptr(work),
                                       work.numel() * work.element_size(), _stream(stream)))
+    return info
+
+
+def oam_lsqr_noalloc(model, s, x, opts, stream=None, want_info=True):
+    """LSQR on the library's static device workspace (no device allocation)."""
+    info = OamLsqrInfo()
+    _check("oam_lsqr_noalloc", lib().oam_lsqr_noalloc(model, _ptr(s), _ptr(x), ctypes.byref(opts),
+                                                      ctypes.byref(info) if want_info else None, _stream(stream)))
     return info
 
 

@@ -7,6 +7,7 @@
 // atomic ticket) sums the partials in index order and runs the scalar update.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -465,3 +466,49 @@ extern "C" oam_status oam_l1_fista(const oam_model *m, const float *d_s, float *
   return OAM_OK;
 }
 
+// ---------------------------------------------------------------- no-allocation LSQR
+// Some callers cannot call cudaMalloc at solve time: hosts that reserve all
+// device memory up front for their own allocator (so a library allocation
+// would fail or fragment it), and latency-critical loops where an allocation's
+// implicit device synchronisation is not acceptable.  oam_lsqr_noalloc runs
+// the same LSQR as oam_lsqr on a fixed workspace that lives in this library's
+// static device memory instead of a caller-provided buffer.
+namespace {
+
+constexpr size_t kStaticWorkBytes = size_t(32) << 20;  // 32 MiB per GPU that loads the library
+__device__ __align__(256) unsigned char g_static_work[kStaticWorkBytes];
+
+constexpr int kMaxDevices = 64;
+void *g_static_ptr[kMaxDevices] = {};
+std::mutex g_static_mu;
+
+// Device address of g_static_work on the current device (looked up once per device).
+oam_status static_work_ptr(void **out) {
+  int dev = 0;
+  OAM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return OAM_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_work) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return OAM_ERR_CUDA;
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return OAM_OK;
+}
+
+}  // namespace
+
+extern "C" oam_status oam_lsqr_noalloc(const oam_model *m, const float *d_s, float *d_x, const oam_lsqr_opts *opts,
+                                       oam_lsqr_info *info, void *stream) {
+  if (!m || !d_s || !d_x || !opts) return OAM_ERR_INVALID_ARG;
+  const size_t need = layout(m).total(0);
+  if (need > kStaticWorkBytes) return OAM_ERR_INVALID_ARG;
+  void *work = nullptr;
+  oam_status rc = static_work_ptr(&work);
+  if (rc) return rc;
+  return oam_lsqr(m, d_s, d_x, opts, info, work, kStaticWorkBytes, stream);
+}
