@@ -513,6 +513,7 @@ oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int 
   p.data = L->d_data;
   p.slot_bytes = L->slot_bytes;
   p.strip_rows = kTileM + 2 * R;
+  p.items_bytes = (int)((sizeof(TcItem) * L->stages * m->W + 127) & ~size_t(127));
   const int strip_bytes = p.strip_rows * 16 * 8;
   p.n_slots = std::min(12, (kSmemLimit - 512 - p.items_bytes - 2 * strip_bytes) / L->slot_bytes);
   if (p.n_slots < 2) return OAM_ERR_UNSUPPORTED;
@@ -520,10 +521,10 @@ oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int 
   p.tmem_cols = L->tmem_cols;
   p.part = m->d_tc_part;
   p.part_stride = (size_t)m->grid.py * m->grid.px;
-  p.items_bytes = (int)((sizeof(TcItem) * L->stages * m->W + 127) & ~size_t(127));
   p.status = m->d_status;
   p.budget = 4000000000LL;  // ~2 s at 2 GHz
   const size_t smem = 512 + (size_t)p.items_bytes + 2 * (size_t)strip_bytes + (size_t)p.n_slots * p.slot_bytes;
+  if (smem > (size_t)kSmemLimit) return OAM_ERR_UNSUPPORTED;
   OAM_CUDA_TRY(cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int n_tiles = (int)(((long long)m->grid.py * wp + kTileM - 1) / kTileM);
   const int parts = m->W;  // one tap row per block
