@@ -9,14 +9,29 @@
 //
 // M = 128 positions (one tensor-memory lane each), N = the slab band of one
 // 16-deep K chunk (time samples for A, depths for A^T), K = (tap, 16-chunk).
-// Positions use a padded flat index q = y*Wp + x with Wp = px + R, so a
-// lateral tap shift a is a shift of the whole 128-row operand by a rows: one
-// staged strip of 128 + 2R rows serves all 2R+1 taps of a row offset b by
-// moving the shared-memory descriptor start 16 bytes per tap.  Padding
-// columns hold zeros, and out-of-grid rows sit in zero padding rows.
+//
+// Mirror folding.  The sensor is axially symmetric and its patch set is
+// mirror-symmetric (Results, axial symmetry), so S[b][a] = S[+-b][+-a] exactly
+// (one stored orbit).  The four mirrored taps therefore share one slab tile,
+// and their operand rows are summed before the product:
+//   F[pos][k] = X[pos + (b, a)] + X[pos + (b, -a)] + X[pos + (-b, a)] + X[pos + (-b, -a)]
+// (duplicates dropped when a or b is 0).  One block handles one 128-position
+// tile and one |b|; it stages the FP32 rows y+b and y-b (TMA, 128-byte
+// swizzle), eight warps build F on CUDA cores and split it into BF16 hi/lo,
+// and one thread issues the MMAs.  This cuts the MMA count by ~4 for a 61x61
+// window.
+//
+// Positions use a padded flat index q = y*Wp + x with Wp = px + R, so a lateral
+// offset a is a shift by a rows of a staged strip of 128 + 2R rows.  Padding
+// columns and the R+1 padding rows above and below hold zeros.
 //
 // Each product uses hi = bf16(v), lo = bf16(v - hi) splits of the slab and of
-// the iterate: D += X_hi S_hi + X_hi S_lo + X_lo S_hi, accumulated in FP32.
+// the folded iterate: D += F_hi S_hi + F_hi S_lo + F_lo S_hi, accumulated in
+// FP32 in tensor memory.  Each block's tensor-memory sums are written as one
+// partial per |b|; k_sum_parts adds them in index order (this bounds how many
+// MMA results any one accumulator takes, which keeps the tensor cores' FP32
+// accumulation within 1e-4 of the FP64 oracle).
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -29,9 +44,12 @@ using namespace oam;
 
 namespace oam {
 
-constexpr int kStageK = 32;        // K elements per staged strip (two 16-deep MMA chunks)
+constexpr int kStageK = 32;        // K elements per stage (two 16-deep MMA chunks)
 constexpr int kTileM = 128;        // positions per block
-constexpr int kThreads = 192;      // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
+constexpr int kFoldWarps = 8;      // warps that build the folded operand (then run the epilogue)
+constexpr int kThreads = 64 + 32 * kFoldWarps;
+constexpr int kFoldSlots = 3;
+constexpr int kFoldBytes = 16384;  // hi + lo: 2 x [4 chunks of 8][128 rows][16 bytes]
 constexpr int kSmemLimit = 227 * 1024;
 
 struct __align__(16) TcItem {
@@ -52,13 +70,14 @@ struct TcLayout {
   int acc_cols = 0;       // accumulator width (multiple of 16)
   int tmem_cols = 0;      // allocated tensor-memory columns (power of two >= 32)
   int out_lo = 0;         // output index of accumulator column 0
-  int in_lo = 0;          // input index of packed chunk 0
-  int chunks8 = 0;        // 8-element chunks in the packed input
+  int in_lo = 0;          // input index of packed element 0
+  int in_elems = 0;       // packed elements per position (32 * stages)
   int slot_bytes = 0;     // shared-memory slot per item
   TcItem *d_items = nullptr;
   uint8_t *d_data = nullptr;
   size_t data_bytes = 0;
   double exec_flops = 0;  // MMA flops of one application (3 products, band and tile padding)
+  CUtensorMap tmap;  // FP32 packed input [qtot][in_elems], box 32 x (128 + 2R), 128-byte swizzle
 };
 
 }  // namespace oam
@@ -66,54 +85,96 @@ struct TcLayout {
 namespace {
 
 struct CorrParams {
-  const uint8_t *in_hi, *in_lo;  // packed input [chunks8][qtot][8 x bf16]
   long long qtot;
-  int wp, px, py, R, W, dir, stages;
+  int wp, px, py, R, W, stages;
   const int *tap_orbit;
   const TcItem *items;  // [n_orb][stages]
   const uint8_t *data;
-  int slot_bytes, n_slots, strip_rows, items_bytes;
+  int slot_bytes, n_slots, strip_rows, strip_bytes, items_bytes;
   int acc_cols, tmem_cols;
-  float *part;            // partial sums [W][py*px][acc_cols], one slice per tap row b
-  size_t part_stride;     // py*px
+  float *part;         // partial sums [R+1][py*px][acc_cols], one slice per |b|
+  size_t part_stride;  // py*px
   int *status;
   long long budget;
 };
 
-__device__ __forceinline__ bool row_skipped(const CorrParams &p, int tile, int b) {
-  const int q0 = tile * kTileM;
-  const int y_first = q0 / p.wp, y_last = (q0 + kTileM - 1) / p.wp;
-  const int off = p.dir == 0 ? b : -b;
-  return (y_last + off < 0) || (y_first + off >= p.py);
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(ptx::smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(ptx::smem_addr(bar))
+      : "memory");
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
-  extern __shared__ __align__(1024) uint8_t smem[];
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Does row offset `off` put any of the tile's rows inside the grid?
+__device__ __forceinline__ bool row_live(const CorrParams &p, int tile, int off) {
+  const int q0 = tile * kTileM;
+  const int y_first = q0 / p.wp, y_last = (q0 + kTileM - 1) / p.wp;
+  return !(y_last + off < 0 || y_first + off >= p.py);
+}
+
+// Add one staged FP32 row (128-byte rows, 128-byte TMA swizzle: 16-byte chunk c
+// of row r sits at chunk c ^ (r & 7)) for the 16 elements of half h.
+__device__ __forceinline__ void add_row(const float *strip, int row, int h, float (&acc)[16]) {
+  const float4 *r4 = reinterpret_cast<const float4 *>(strip + row * 32);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 v = r4[(4 * h + i) ^ (row & 7)];
+    acc[4 * i + 0] += v.x;
+    acc[4 * i + 1] += v.y;
+    acc[4 * i + 2] += v.z;
+    acc[4 * i + 3] += v.w;
+  }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_corr_fold(const __grid_constant__ CUtensorMap tmap, const CorrParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 128-byte-swizzled TMA destinations need 1024-byte alignment
+  uint8_t *smem = smem_raw + ((1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
+  const int NF = kFoldSlots;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
   uint64_t *strip_full = bars, *strip_empty = bars + 2;
   uint64_t *acc_ready = bars + 4, *acc_full = bars + 5;
-  uint64_t *slab_full = bars + 6, *slab_empty = bars + 6 + p.n_slots;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 256);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 260);
-  volatile int *never = reinterpret_cast<volatile int *>(smem + 264);  // stays 0: waits that ignore abort
-  const int L = p.strip_rows;
-  const uint32_t strip_bytes = (uint32_t)L * 16u * 4u * 2u;  // 4 chunks of 8, hi + lo
-  TcItem *sitems = reinterpret_cast<TcItem *>(smem + 512);  // [stages][W] for this block's row
-  uint8_t *strips = smem + 512 + p.items_bytes;
-  uint8_t *slots = strips + 2 * strip_bytes;
+  uint64_t *fold_full = bars + 6, *fold_empty = bars + 6 + NF;
+  uint64_t *slab_full = bars + 6 + 2 * NF, *slab_empty = bars + 6 + 2 * NF + p.n_slots;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 512);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 516);
+  volatile int *never = reinterpret_cast<volatile int *>(smem + 520);  // stays 0: waits that ignore abort
+  TcItem *sitems = reinterpret_cast<TcItem *>(smem + 1024);           // [stages][R+1] for this |b|
+  uint8_t *strips = smem + 1024 + p.items_bytes;                       // [2 slots][2 rows][strip_bytes]
+  uint8_t *folds = strips + 4 * p.strip_bytes;                         // [NF][kFoldBytes]
+  uint8_t *slots = folds + NF * kFoldBytes;                            // [n_slots][slot_bytes]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x;
-  const int b = (int)blockIdx.y - p.R;  // this block's tap row
-  const bool skip_row = row_skipped(p, tile, b);
+  const int b = (int)blockIdx.y;  // |b|: rows y + b and y - b
+  const int R = p.R, NA = R + 1;  // a = 0 .. R
+  const bool live_p = row_live(p, tile, b), live_m = row_live(p, tile, -b);
+  const bool skip = !live_p && !live_m;
+  const int n_rows = b > 0 ? 2 : 1;
+  const int L = p.strip_rows;
 
   if (threadIdx.x == 0) {
-    ptx::mbar_init(&strip_full[0], 1);
-    ptx::mbar_init(&strip_full[1], 1);
-    ptx::mbar_init(&strip_empty[0], 1);
-    ptx::mbar_init(&strip_empty[1], 1);
-    ptx::mbar_init(acc_ready, 4);
+    for (int i = 0; i < 2; ++i) {
+      ptx::mbar_init(&strip_full[i], 1);
+      ptx::mbar_init(&strip_empty[i], kFoldWarps);
+    }
+    ptx::mbar_init(acc_ready, kFoldWarps);
     ptx::mbar_init(acc_full, 1);
+    for (int i = 0; i < NF; ++i) {
+      ptx::mbar_init(&fold_full[i], kFoldWarps);
+      ptx::mbar_init(&fold_empty[i], 1);
+    }
     for (int i = 0; i < p.n_slots; ++i) {
       ptx::mbar_init(&slab_full[i], 1);
       ptx::mbar_init(&slab_empty[i], 1);
@@ -122,11 +183,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
     *never = 0;
     ptx::mbar_fence_init();
   }
-  if (warp == 0 && !skip_row) {
-    const int n = p.stages * p.W;
+  if (warp == 0 && !skip) {
+    const int n = p.stages * NA;
     for (int i = lane; i < n; i += 32) {
-      const int st = i / p.W, ai = i % p.W;
-      sitems[i] = p.items[p.tap_orbit[(b + p.R) * p.W + ai] * p.stages + st];
+      const int st = i / NA, a = i % NA;
+      sitems[i] = p.items[p.tap_orbit[(b + R) * p.W + (a + R)] * p.stages + st];
     }
   }
   if (warp == 1) {
@@ -145,42 +206,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    if (lane == 0) {
+    if (lane == 0 && !skip) {
       int it_strip = 0, it_slab = 0;
       bool ok = true;
-      if (!skip_row) {
-        const long long q_base =
-            (long long)(p.R + 1) * p.wp + (long long)tile * kTileM + (long long)(p.dir == 0 ? b : -b) * p.wp - p.R;
-        for (int st = 0; st < p.stages && ok; ++st) {
-          const int s = it_strip & 1;
-          if (!ptx::mbar_wait(&strip_empty[s], ((it_strip >> 1) & 1) ^ 1, abort_flag, p.budget)) {
-            fail(1);
+      const int q_p = (int)((long long)(R + 1) * p.wp + (long long)tile * kTileM + (long long)b * p.wp - R);
+      const int q_m = (int)((long long)(R + 1) * p.wp + (long long)tile * kTileM - (long long)b * p.wp - R);
+      for (int st = 0; st < p.stages && ok; ++st) {
+        const int s = it_strip & 1;
+        if (!ptx::mbar_wait(&strip_empty[s], ((it_strip >> 1) & 1) ^ 1, abort_flag, p.budget)) {
+          fail(1);
+          ok = false;
+          break;
+        }
+        ptx::mbar_arrive_expect_tx(&strip_full[s], (uint32_t)(n_rows * L * 128));
+        uint8_t *dst = strips + (size_t)s * 2 * p.strip_bytes;
+        tma_load_2d(dst, &tmap, kStageK * st, q_p, &strip_full[s]);
+        if (n_rows == 2) tma_load_2d(dst + p.strip_bytes, &tmap, kStageK * st, q_m, &strip_full[s]);
+        ++it_strip;
+        const TcItem *row_items = sitems + st * NA;
+        for (int a = 0; a < NA; ++a) {
+          const TcItem item = row_items[a];
+          const int slot = it_slab % p.n_slots;
+          if (!ptx::mbar_wait(&slab_empty[slot], ((it_slab / p.n_slots) & 1) ^ 1, abort_flag, p.budget)) {
+            fail(2);
             ok = false;
             break;
           }
-          ptx::mbar_arrive_expect_tx(&strip_full[s], strip_bytes);
-          uint8_t *dst = strips + s * strip_bytes;
-          for (int c = 0; c < 4; ++c) {
-            const long long src = ((long long)(4 * st + c) * p.qtot + q_base) * 16;
-            ptx::bulk_g2s(dst + c * L * 16, p.in_hi + src, L * 16, &strip_full[s]);
-            ptx::bulk_g2s(dst + (4 + c) * L * 16, p.in_lo + src, L * 16, &strip_full[s]);
-          }
-          ++it_strip;
-          const TcItem *row_items = sitems + st * p.W;
-          for (int ai = 0; ai < p.W; ++ai) {
-            const TcItem item = row_items[ai];
-            const int slot = it_slab % p.n_slots;
-            if (!ptx::mbar_wait(&slab_empty[slot], ((it_slab / p.n_slots) & 1) ^ 1, abort_flag, p.budget)) {
-              fail(2);
-              ok = false;
-              break;
-            }
-            ptx::mbar_arrive_expect_tx(&slab_full[slot], item.bytes);
-            if (item.bytes > 0)
-              ptx::bulk_g2s(slots + (size_t)slot * p.slot_bytes, p.data + (size_t)item.off16 * 16, item.bytes,
-                            &slab_full[slot]);
-            ++it_slab;
-          }
+          ptx::mbar_arrive_expect_tx(&slab_full[slot], item.bytes);
+          if (item.bytes > 0)
+            ptx::bulk_g2s(slots + (size_t)slot * p.slot_bytes, p.data + (size_t)item.off16 * 16, item.bytes,
+                          &slab_full[slot]);
+          ++it_slab;
         }
       }
       if (!ok) {
@@ -197,81 +253,147 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const CorrParams p) {
       bool ok = ptx::mbar_wait(acc_ready, 0, abort_flag, p.budget);
       if (!ok) fail(4);
       ptx::tc_fence_after();
-      int it_strip = 0, it_slab = 0;
-      const uint32_t lbo_a = (uint32_t)L * 16u;
-      if (!skip_row) {
-        for (int st = 0; st < p.stages && ok; ++st) {
-          const int s = it_strip & 1;
-          if (!ptx::mbar_wait(&strip_full[s], (it_strip >> 1) & 1, abort_flag, p.budget)) {
+      int it_fold = 0, it_slab = 0;
+      // Descriptor templates (start-address field in 16-byte units; fields never carry).
+      const uint64_t slot_desc = ptx::smem_desc(ptx::smem_addr(slots), 0, 128);
+      const uint64_t fold_desc = ptx::smem_desc(ptx::smem_addr(folds), 2048, 128);  // lbo: 128 rows x 16 B
+      const uint32_t idesc_m128 = ptx::idesc_bf16_f32(kTileM, 0);
+      for (int st = 0; st < p.stages && ok && !skip; ++st) {
+        const TcItem *row_items = sitems + st * NA;
+        for (int a = 0; a < NA; ++a) {
+          const int f = it_fold % NF, slot = it_slab % p.n_slots;
+          if (!ptx::mbar_wait(&fold_full[f], (it_fold / NF) & 1, abort_flag, p.budget)) {
             fail(8);
             ok = false;
             break;
           }
-          const uint32_t a_hi = ptx::smem_addr(strips + s * strip_bytes);
-          const uint32_t a_lo = a_hi + 4u * lbo_a;
-          const TcItem *row_items = sitems + st * p.W;
-          for (int ai = 0; ai < p.W; ++ai) {
-            const TcItem item = row_items[ai];
-            const int slot = it_slab % p.n_slots;
-            if (!ptx::mbar_wait(&slab_full[slot], (it_slab / p.n_slots) & 1, abort_flag, p.budget)) {
-              fail(16);
-              ok = false;
-              break;
-            }
-            ptx::tc_fence_after();
-            // tap a = ai - R: forward reads row m + R + a, adjoint row m + R - a
-            const uint32_t shift = (uint32_t)(p.dir == 0 ? ai : 2 * p.R - ai) * 16u;
-            uint32_t b_addr = ptx::smem_addr(slots + (size_t)slot * p.slot_bytes);
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              const uint32_t N = item.n[c];
-              if (N == 0) continue;
-              const uint32_t idesc = ptx::idesc_bf16_f32(kTileM, N);
-              const uint64_t dah = ptx::smem_desc(a_hi + 2u * c * lbo_a + shift, lbo_a, 128);
-              const uint64_t dal = ptx::smem_desc(a_lo + 2u * c * lbo_a + shift, lbo_a, 128);
-              const uint64_t dbh = ptx::smem_desc(b_addr, N * 16u, 128);
-              const uint64_t dbl = ptx::smem_desc(b_addr + N * 32u, N * 16u, 128);
-              const uint32_t d = tmem + item.col[c];
-              ptx::mma_bf16(d, dah, dbh, idesc, 1);
-              ptx::mma_bf16(d, dah, dbl, idesc, 1);
-              ptx::mma_bf16(d, dal, dbh, idesc, 1);
-              b_addr += N * 64u;
-            }
-            ptx::mma_commit(&slab_empty[slot]);
-            ++it_slab;
+          if (!ptx::mbar_wait(&slab_full[slot], (it_slab / p.n_slots) & 1, abort_flag, p.budget)) {
+            fail(16);
+            ok = false;
+            break;
           }
-          ptx::mma_commit(&strip_empty[s]);
-          ++it_strip;
+          ptx::tc_fence_after();
+          const TcItem item = row_items[a];
+          const uint64_t dA_hi = fold_desc + (uint64_t)((f * kFoldBytes) >> 4);
+          const uint64_t dA_lo = dA_hi + (8192 >> 4);
+          uint64_t dB = slot_desc + (uint64_t)(((uint32_t)slot * (uint32_t)p.slot_bytes) >> 4);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const uint32_t n = item.n[c];
+            if (n == 0) continue;
+            const uint64_t ca = (uint64_t)((2 * c * 2048) >> 4);  // chunk c: k8 blocks 2c, 2c+1
+            const uint64_t dbh = dB + ((uint64_t)n << 16);          // lbo = 16 n bytes
+            const uint64_t dbl = dbh + 2u * n;                      // lo tile 32 n bytes later
+            const uint32_t idesc = idesc_m128 | ((n >> 3) << 17);
+            const uint32_t d = tmem + item.col[c];
+            ptx::mma_bf16(d, dA_hi + ca, dbh, idesc, 1);
+            ptx::mma_bf16(d, dA_hi + ca, dbl, idesc, 1);
+            ptx::mma_bf16(d, dA_lo + ca, dbh, idesc, 1);
+            dB += 4u * n;  // next tile 64 n bytes later
+          }
+          ptx::mma_commit(&slab_empty[slot]);
+          ptx::mma_commit(&fold_empty[f]);
+          ++it_slab;
+          ++it_fold;
         }
       }
       ptx::mma_commit(acc_full);
     }
   } else {
-    // ------------------------------------------------------------ epilogue (warps 2-5)
-    const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
+    // ------------------------------------------------------------ fold warps, then epilogue
+    const int fw = warp - 2;        // 0 .. kFoldWarps-1
+    const int quarter = warp & 3;   // tensor-memory lanes 32*quarter .. +31
     const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-    for (int col = 0; col < p.tmem_cols; col += 32) ptx::tmem_st32_zero(tmem + lane_base + (uint32_t)col);
+    const int half_cols = p.tmem_cols / 2;
+    const int col_begin = fw < 4 ? 0 : half_cols;
+    for (int col = col_begin; col < col_begin + half_cols; col += 32)
+      ptx::tmem_st32_zero(tmem + lane_base + (uint32_t)col);
     ptx::tmem_wait_st();
     ptx::tc_fence_before();
     __syncwarp();
     if (lane == 0) ptx::mbar_arrive(acc_ready);
-    bool ok = ptx::mbar_wait(acc_full, 0, abort_flag, 4 * p.budget);
-    ok = __all_sync(0xffffffffu, ok);
+
+    bool ok = true;
+    if (!skip) {
+      const int ft = threadIdx.x - 64;
+      const int m = ft & 127, h = ft >> 7;  // row, 16-element half of the stage
+      int it_strip = 0, it_fold = 0;
+      for (int st = 0; st < p.stages && ok; ++st) {
+        const int s = it_strip & 1;
+        ok = ptx::mbar_wait(&strip_full[s], (it_strip >> 1) & 1, abort_flag, p.budget);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+          if (lane == 0) fail(32);
+          break;
+        }
+        const float *X1 = reinterpret_cast<const float *>(strips + (size_t)s * 2 * p.strip_bytes);
+        const float *X2 = reinterpret_cast<const float *>(strips + (size_t)s * 2 * p.strip_bytes + p.strip_bytes);
+        for (int a = 0; a < NA; ++a) {
+          const int f = it_fold % NF;
+          ok = ptx::mbar_wait(&fold_empty[f], ((it_fold / NF) & 1) ^ 1, abort_flag, p.budget);
+          ok = __all_sync(0xffffffffu, ok);
+          if (!ok) {
+            if (lane == 0) fail(64);
+            break;
+          }
+          float acc[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[i] = 0.0f;
+          const int rp = m + R + a, rm = m + R - a;
+          add_row(X1, rp, h, acc);
+          if (a > 0) add_row(X1, rm, h, acc);
+          if (b > 0) {
+            add_row(X2, rp, h, acc);
+            if (a > 0) add_row(X2, rm, h, acc);
+          }
+          uint8_t *fo = folds + f * kFoldBytes;
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {  // k8 block 2h + j
+            uint4 hv, lv;
+            float hf[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) hf[e] = __bfloat162float(__float2bfloat16_rn(acc[8 * j + e]));
+            hv.x = pack_bf16x2(hf[0], hf[1]);
+            hv.y = pack_bf16x2(hf[2], hf[3]);
+            hv.z = pack_bf16x2(hf[4], hf[5]);
+            hv.w = pack_bf16x2(hf[6], hf[7]);
+            lv.x = pack_bf16x2(acc[8 * j + 0] - hf[0], acc[8 * j + 1] - hf[1]);
+            lv.y = pack_bf16x2(acc[8 * j + 2] - hf[2], acc[8 * j + 3] - hf[3]);
+            lv.z = pack_bf16x2(acc[8 * j + 4] - hf[4], acc[8 * j + 5] - hf[5]);
+            lv.w = pack_bf16x2(acc[8 * j + 6] - hf[6], acc[8 * j + 7] - hf[7]);
+            const int blk = 2 * h + j;
+            *reinterpret_cast<uint4 *>(fo + blk * 2048 + m * 16) = hv;
+            *reinterpret_cast<uint4 *>(fo + 8192 + blk * 2048 + m * 16) = lv;
+          }
+          fence_proxy_async_smem();  // make the stores visible to the tensor cores
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&fold_full[f]);
+          ++it_fold;
+        }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&strip_empty[s]);
+        ++it_strip;
+      }
+    }
+
+    // epilogue: this warp's lane quarter and column half of the accumulator
+    bool done = ptx::mbar_wait(acc_full, 0, abort_flag, 4 * p.budget);
+    done = __all_sync(0xffffffffu, done && ok);
     ptx::tc_fence_after();
-    const int m = 32 * quarter + lane;
-    const long long qf = (long long)tile * kTileM + m;
+    const int mrow = 32 * quarter + lane;
+    const long long qf = (long long)tile * kTileM + mrow;
     const int y = (int)(qf / p.wp), x = (int)(qf % p.wp);
-    const bool valid = ok && y < p.py && x < p.px;
-    // this part's partial sums: part[blockIdx.y][y*px + x][0 .. acc_cols)
-    float *row = p.part + ((size_t)blockIdx.y * p.part_stride + (size_t)y * p.px + x) * p.acc_cols;
-    if (ok) {
-      for (int col = 0; col < p.acc_cols; col += 32) {
+    const bool valid = done && y < p.py && x < p.px;
+    float *row = p.part + ((size_t)b * p.part_stride + (size_t)y * p.px + x) * p.acc_cols;
+    if (done) {
+      const int c_end = std::min(col_begin + half_cols, p.acc_cols);
+      for (int col = col_begin; col < c_end; col += 32) {
         uint32_t r[32];
         ptx::tmem_ld32(tmem + lane_base + (uint32_t)col, r);
         ptx::tmem_wait_ld();
         if (valid) {
           float4 *dst = reinterpret_cast<float4 *>(row + col);
-          const int nv = min(8, (p.acc_cols - col) >> 2);
+          const int nv = std::min(8, (p.acc_cols - col) >> 2);
 #pragma unroll
           for (int j = 0; j < 8; ++j)
             if (j < nv)
@@ -319,34 +441,33 @@ __global__ void k_pack_tiles(const float *band, const int *band_lo, const int *b
   }
 }
 
-// Iterate: in[py][px][len] (FP32) -> hi/lo [chunks8][qtot][8] bf16, element j of
-// chunk c holding index first + 8c + j of the row of padded position q.
-__global__ void k_pack_input(const float *__restrict__ in, int len, int first, int chunks8, long long qtot, int wp,
-                             int R, int px, int py, uint4 *__restrict__ out_hi, uint4 *__restrict__ out_lo) {
-  const long long total = (long long)chunks8 * qtot;
+// Iterate in[py][px][len] -> out[qtot][elems] (FP32): element e of padded
+// position q is index first + e of the row of (y, x) = (q / wp - R - 1, q % wp),
+// zero outside the grid or the row.
+__global__ void k_pack_input(const float *__restrict__ in, int len, int first, int elems, long long qtot, int wp,
+                             int R, int px, int py, float4 *__restrict__ out) {
+  const int e4n = elems >> 2;
+  const long long total = qtot * e4n;
+  const bool vec = ((len | first) & 3) == 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i / qtot);
-    const long long q = i % qtot;
+    const long long q = i / e4n;
+    const int e = 4 * (int)(i % e4n);
     const int y = (int)(q / wp) - (R + 1), x = (int)(q % wp);
-    float v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = 0.0f;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (y >= 0 && y < py && x < px) {
       const float *src = in + ((size_t)y * px + x) * len;
-      const int e0 = first + 8 * c;
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (e0 + j < len) v[j] = src[e0 + j];
+      const int idx = first + e;
+      if (vec && idx + 3 < len) {
+        v = *reinterpret_cast<const float4 *>(src + idx);
+      } else {
+        if (idx < len) v.x = src[idx];
+        if (idx + 1 < len) v.y = src[idx + 1];
+        if (idx + 2 < len) v.z = src[idx + 2];
+        if (idx + 3 < len) v.w = src[idx + 3];
+      }
     }
-    __align__(16) __nv_bfloat16 h[8], l[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      h[j] = __float2bfloat16_rn(v[j]);
-      l[j] = __float2bfloat16_rn(v[j] - __bfloat162float(h[j]));
-    }
-    out_hi[i] = *reinterpret_cast<uint4 *>(h);
-    out_lo[i] = *reinterpret_cast<uint4 *>(l);
+    out[i] = v;
   }
 }
 
@@ -373,6 +494,33 @@ int pow2_cols(int n) {
   return c;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+oam_status encode_tmap(CUtensorMap *map, float *base, long long qtot, int elems, int rows) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p) {
+      cudaGetLastError();
+      return OAM_ERR_CUDA;
+    }
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)elems, (cuuint64_t)qtot};
+  const cuuint64_t strides[1] = {(cuuint64_t)elems * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kStageK, (cuuint32_t)rows};
+  const cuuint32_t estr[2] = {1, 1};
+  if (fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+      CUDA_SUCCESS)
+    return OAM_ERR_CUDA;
+  return OAM_OK;
+}
+
 // Build one direction's item and tile tables from the band form, then pack.
 oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d_band_hi) {
   const int nz = m->grid.nz, O = m->n_orb;
@@ -389,7 +537,7 @@ oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d
     L->out_lo = 0;
     L->in_lo = t_lo;
   }
-  L->chunks8 = 4 * L->stages;
+  L->in_elems = kStageK * L->stages;
   L->tmem_cols = pow2_cols(L->acc_cols);
   if (L->tmem_cols > 512) return OAM_ERR_UNSUPPORTED;
 
@@ -397,7 +545,6 @@ oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d
   std::vector<TcTile> tiles;
   long long off = 0;
   int max_item = 16;
-  double flops_cols = 0;  // sum over orbits of MMA columns x 16 (per position, per tap)
   for (int o = 0; o < O; ++o) {
     for (int s = 0; s < L->stages; ++s) {
       TcItem it{};
@@ -437,7 +584,6 @@ oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d
         it.n[c] = (uint16_t)n;
         tiles.push_back(TcTile{o, chunk, col, n, off});
         off += 64LL * n;  // hi + lo: 2 x (n rows x 16 elements x 2 bytes)
-        flops_cols += 16.0 * n;
       }
       it.bytes = (uint32_t)(off - item_off);
       max_item = std::max(max_item, (int)it.bytes);
@@ -446,23 +592,22 @@ oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d
   }
   L->slot_bytes = (max_item + 127) & ~127;
   L->data_bytes = (size_t)std::max<long long>(off, 16);
-  // executed MMA flops of one application: 3 products x 2 x M x (16 x N) summed
-  // over the (position tile, tap row) blocks whose row meets the grid
+  // executed MMA flops of one application: 3 products x 2 x M x (16 x N) over the
+  // (position tile, |b|, a >= 0) work items whose rows meet the grid
   {
     std::vector<double> orb_cols(O, 0.0);
     for (const TcTile &t : tiles) orb_cols[t.orbit] += 16.0 * t.n;
     const int wp = m->grid.px + m->R, W = m->W, R = m->R;
     const long long n_tiles = ((long long)m->grid.py * wp + kTileM - 1) / kTileM;
-    std::vector<double> row_cols(W, 0.0);
-    for (int bi = 0; bi < W; ++bi)
-      for (int ai = 0; ai < W; ++ai) row_cols[bi] += orb_cols[m->h_tap_orbit[bi * W + ai]];
+    std::vector<double> row_cols(R + 1, 0.0);
+    for (int b = 0; b <= R; ++b)
+      for (int a = 0; a <= R; ++a) row_cols[b] += orb_cols[m->h_tap_orbit[(b + R) * W + (a + R)]];
     double total = 0;
     for (long long t = 0; t < n_tiles; ++t) {
       const long long yf = t * kTileM / wp, yl = (t * kTileM + kTileM - 1) / wp;
-      for (int bi = 0; bi < W; ++bi) {
-        const int off = dir == 0 ? bi - R : R - bi;
-        if (yl + off < 0 || yf + off >= m->grid.py) continue;
-        total += row_cols[bi];
+      for (int b = 0; b <= R; ++b) {
+        const bool lp = !(yl + b < 0 || yf + b >= m->grid.py), lm = !(yl - b < 0 || yf - b >= m->grid.py);
+        if (lp || lm) total += row_cols[b];
       }
     }
     L->exec_flops = 3.0 * 2.0 * kTileM * total;
@@ -484,38 +629,30 @@ oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d
   return OAM_OK;
 }
 
-oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int in_len, float *out, int out_len,
-                    cudaStream_t st) {
-  if (!m->d_tc_part) return OAM_ERR_UNSUPPORTED;
-  const int R = m->R, wp = m->grid.px + R;
-  const long long qtot = m->tc_qtot;
-  uint8_t *hi = m->d_tc_pack, *lo = m->d_tc_pack + (size_t)L->chunks8 * qtot * 16;
-  {
-    const long long total = (long long)L->chunks8 * qtot;
-    const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * m->sm_count);
-    k_pack_input<<<blocks, 256, 0, st>>>(in, in_len, L->in_lo, L->chunks8, qtot, wp, R, m->grid.px, m->grid.py,
-                                         reinterpret_cast<uint4 *>(hi), reinterpret_cast<uint4 *>(lo));
-    OAM_LAUNCHED();
-  }
+struct Launch {
+  CorrParams p;
+  size_t smem;
+};
+
+oam_status plan_launch(const oam_model *m, const TcLayout *L, Launch *out) {
+  const int R = m->R;
   CorrParams p{};
-  p.in_hi = hi;
-  p.in_lo = lo;
-  p.qtot = qtot;
-  p.wp = wp;
+  p.qtot = m->tc_qtot;
+  p.wp = m->grid.px + R;
   p.px = m->grid.px;
   p.py = m->grid.py;
   p.R = R;
   p.W = m->W;
-  p.dir = L->dir;
   p.stages = L->stages;
   p.tap_orbit = m->d_tap_orbit;
   p.items = L->d_items;
   p.data = L->d_data;
   p.slot_bytes = L->slot_bytes;
   p.strip_rows = kTileM + 2 * R;
-  p.items_bytes = (int)((sizeof(TcItem) * L->stages * m->W + 127) & ~size_t(127));
-  const int strip_bytes = p.strip_rows * 16 * 8;
-  p.n_slots = std::min(12, (kSmemLimit - 512 - p.items_bytes - 2 * strip_bytes) / L->slot_bytes);
+  p.strip_bytes = (p.strip_rows * 128 + 1023) & ~1023;  // 128-byte rows, 1024-byte aligned
+  p.items_bytes = (int)((sizeof(TcItem) * L->stages * (R + 1) + 1023) & ~size_t(1023));
+  const int fixed = 1024 /* alignment slack */ + 1024 + p.items_bytes + 4 * p.strip_bytes + kFoldSlots * kFoldBytes;
+  p.n_slots = std::min(16, (kSmemLimit - fixed) / L->slot_bytes);
   if (p.n_slots < 2) return OAM_ERR_UNSUPPORTED;
   p.acc_cols = L->acc_cols;
   p.tmem_cols = L->tmem_cols;
@@ -523,19 +660,36 @@ oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int 
   p.part_stride = (size_t)m->grid.py * m->grid.px;
   p.status = m->d_status;
   p.budget = 4000000000LL;  // ~2 s at 2 GHz
-  const size_t smem = 512 + (size_t)p.items_bytes + 2 * (size_t)strip_bytes + (size_t)p.n_slots * p.slot_bytes;
-  if (smem > (size_t)kSmemLimit) return OAM_ERR_UNSUPPORTED;
-  OAM_CUDA_TRY(cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int n_tiles = (int)(((long long)m->grid.py * wp + kTileM - 1) / kTileM);
-  const int parts = m->W;  // one tap row per block
+  out->p = p;
+  out->smem = (size_t)fixed + (size_t)p.n_slots * p.slot_bytes;
+  if (out->smem > (size_t)kSmemLimit) return OAM_ERR_UNSUPPORTED;
+  return OAM_OK;
+}
+
+oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int in_len, float *out, int out_len,
+                    cudaStream_t st) {
+  if (!m->d_tc_part || !m->d_tc_pack) return OAM_ERR_UNSUPPORTED;
+  Launch lp;
+  oam_status rc = plan_launch(m, L, &lp);
+  if (rc) return rc;
+  const int R = m->R;
+  {
+    const long long total = m->tc_qtot * (L->in_elems / 4);
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 16LL * m->sm_count);
+    k_pack_input<<<blocks, 256, 0, st>>>(in, in_len, L->in_lo, L->in_elems, m->tc_qtot, m->grid.px + R, R, m->grid.px,
+                                         m->grid.py, reinterpret_cast<float4 *>(m->d_tc_pack));
+    OAM_LAUNCHED();
+  }
+  OAM_CUDA_TRY(cudaFuncSetAttribute(k_corr_fold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lp.smem));
+  const int n_tiles = (int)(((long long)m->grid.py * (m->grid.px + R) + kTileM - 1) / kTileM);
   {
     ProfScope prof(m, st, L->dir == 0);
-    k_corr_tc<<<dim3(n_tiles, parts), kThreads, smem, st>>>(p);
+    k_corr_fold<<<dim3(n_tiles, R + 1), kThreads, lp.smem, st>>>(L->tmap, lp.p);
     OAM_LAUNCHED();
   }
   const size_t npos = (size_t)m->grid.py * m->grid.px;
   const int blocks = (int)std::min<size_t>((npos * out_len + 255) / 256, 16ull * m->sm_count);
-  k_sum_parts<<<blocks, 256, 0, st>>>(m->d_tc_part, parts, npos, L->acc_cols, L->out_lo, out_len, out);
+  k_sum_parts<<<blocks, 256, 0, st>>>(m->d_tc_part, R + 1, npos, L->acc_cols, L->out_lo, out_len, out);
   OAM_LAUNCHED();
   return OAM_OK;
 }
@@ -543,8 +697,7 @@ oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int 
 }  // namespace
 
 oam_status oam::tc_build(oam_model *m, cudaStream_t st) {
-  if (m->grid.px + m->R > (1 << 20)) return OAM_ERR_UNSUPPORTED;
-  if (kTileM + 2 * m->R > 1000) return OAM_ERR_UNSUPPORTED;  // strip rows per chunk
+  if (kTileM + 2 * m->R > 256) return OAM_ERR_UNSUPPORTED;  // strip rows per TMA box
   int *d_band_hi = nullptr;
   const size_t nb = (size_t)m->n_orb * m->grid.nz;
   OAM_CUDA_TRY(cudaMallocAsync((void **)&d_band_hi, sizeof(int) * nb, st));
@@ -557,17 +710,23 @@ oam_status oam::tc_build(oam_model *m, cudaStream_t st) {
   if (rc) return rc;
   const int wp = m->grid.px + m->R;
   m->tc_qtot = (long long)(m->grid.py + 2 * m->R + 2) * wp + 256;
-  const int chunks = std::max(m->tc_fwd->chunks8, m->tc_adj->chunks8);
-  m->tc_pack_bytes = 2ull * chunks * m->tc_qtot * 16;
+  if (m->tc_qtot > 0x7fffffffLL) return OAM_ERR_UNSUPPORTED;
+  const int elems = std::max(m->tc_fwd->in_elems, m->tc_adj->in_elems);
+  m->tc_pack_bytes = (size_t)elems * m->tc_qtot * sizeof(float);
   rc = dev_alloc(m, &m->d_tc_pack, m->tc_pack_bytes);
   if (rc) return rc;
-  // One block per (position tile, tap row): bounds the MMA steps summed into
-  // one tensor-memory accumulator; the rows are added in FP32 in a fixed order.
-  const int parts = m->W;
+  for (TcLayout *L : {m->tc_fwd, m->tc_adj}) {
+    rc = encode_tmap(&L->tmap, reinterpret_cast<float *>(m->d_tc_pack), m->tc_qtot, L->in_elems, kTileM + 2 * m->R);
+    if (rc) return rc;
+    Launch lp;
+    rc = plan_launch(m, L, &lp);
+    if (rc) return rc;
+  }
+  // One partial per (position, |b|): bounds the MMA results summed into one
+  // tensor-memory accumulator; the parts are added in FP32 in a fixed order.
   const int acc = std::max(m->tc_fwd->acc_cols, m->tc_adj->acc_cols);
-  rc = dev_alloc(m, &m->d_tc_part, (size_t)parts * m->grid.py * m->grid.px * acc);
+  rc = dev_alloc(m, &m->d_tc_part, (size_t)(m->R + 1) * m->grid.py * m->grid.px * acc);
   if (rc) return rc;
-  OAM_CUDA_TRY(cudaMemsetAsync(m->d_tc_pack, 0, m->tc_pack_bytes, st));
   return OAM_OK;
 }
 
