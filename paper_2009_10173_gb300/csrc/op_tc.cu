@@ -17,8 +17,9 @@
 //   F[pos][k] = X[pos + (b, a)] + X[pos + (b, -a)] + X[pos + (-b, a)] + X[pos + (-b, -a)]
 // (duplicates dropped when a or b is 0).  One block handles one 128-position
 // tile and one |b|; it stages the FP32 rows y+b and y-b (TMA, 128-byte
-// swizzle), eight warps build F on CUDA cores and split it into BF16 hi/lo,
-// and one thread issues the MMAs.  This cuts the MMA count by ~4 for a 61x61
+// swizzle) and adds them once per stage, eight warps build F from two shifted
+// rows of that sum, split it into BF16 hi/lo in tensor memory, and one thread
+// issues the MMAs with A read from tensor memory.  This cuts the MMA count by ~4 for a 61x61
 // window.
 //
 // Positions use a padded flat index q = y*Wp + x with Wp = px + R, so a lateral
@@ -48,8 +49,8 @@ constexpr int kStageK = 32;        // K elements per stage (two 16-deep MMA chun
 constexpr int kTileM = 128;        // positions per block
 constexpr int kFoldWarps = 8;      // warps that build the folded operand (then run the epilogue)
 constexpr int kThreads = 64 + 32 * kFoldWarps;
-constexpr int kFoldSlots = 3;
-constexpr int kFoldBytes = 16384;  // hi + lo: 2 x [4 chunks of 8][128 rows][16 bytes]
+constexpr int kMaxItems = 8;       // item ring depth (slab tile + folded operand)
+constexpr int kFoldCols = 32;      // tensor-memory columns per folded operand: 2 chunks x (hi, lo) x 8
 constexpr int kSmemLimit = 227 * 1024;
 
 struct __align__(16) TcItem {
@@ -90,8 +91,8 @@ struct CorrParams {
   const int *tap_orbit;
   const TcItem *items;  // [n_orb][stages]
   const uint8_t *data;
-  int slot_bytes, n_slots, strip_rows, strip_bytes, items_bytes;
-  int acc_cols, tmem_cols;
+  int slot_bytes, n_items, strip_rows, strip_bytes, items_bytes;
+  int acc_cols, tmem_cols, fold_col0;
   float *part;         // partial sums [R+1][py*px][acc_cols], one slice per |b|
   size_t part_stride;  // py*px
   int *status;
@@ -131,29 +132,22 @@ __device__ __forceinline__ void add_row(const float *strip, int row, int h, floa
   }
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<const uint32_t *>(&v);
-}
-
 __global__ void __launch_bounds__(kThreads, 1)
     k_corr_fold(const __grid_constant__ CUtensorMap tmap, const CorrParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 128-byte-swizzled TMA destinations need 1024-byte alignment
   uint8_t *smem = smem_raw + ((1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
-  const int NF = kFoldSlots;
+  const int K = p.n_items;  // item ring: slab tile in shared memory + folded operand in tensor memory
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
   uint64_t *strip_full = bars, *strip_empty = bars + 2;
   uint64_t *acc_ready = bars + 4, *acc_full = bars + 5;
-  uint64_t *fold_full = bars + 6, *fold_empty = bars + 6 + NF;
-  uint64_t *slab_full = bars + 6 + 2 * NF, *slab_empty = bars + 6 + 2 * NF + p.n_slots;
+  uint64_t *slab_full = bars + 6, *fold_full = bars + 6 + K, *item_empty = bars + 6 + 2 * K;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 512);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 516);
   volatile int *never = reinterpret_cast<volatile int *>(smem + 520);  // stays 0: waits that ignore abort
   TcItem *sitems = reinterpret_cast<TcItem *>(smem + 1024);           // [stages][R+1] for this |b|
   uint8_t *strips = smem + 1024 + p.items_bytes;                       // [2 slots][2 rows][strip_bytes]
-  uint8_t *folds = strips + 4 * p.strip_bytes;                         // [NF][kFoldBytes]
-  uint8_t *slots = folds + NF * kFoldBytes;                            // [n_slots][slot_bytes]
+  uint8_t *slots = strips + 4 * p.strip_bytes;                         // [K][slot_bytes]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x;
@@ -171,13 +165,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     ptx::mbar_init(acc_ready, kFoldWarps);
     ptx::mbar_init(acc_full, 1);
-    for (int i = 0; i < NF; ++i) {
-      ptx::mbar_init(&fold_full[i], kFoldWarps);
-      ptx::mbar_init(&fold_empty[i], 1);
-    }
-    for (int i = 0; i < p.n_slots; ++i) {
+    for (int i = 0; i < K; ++i) {
       ptx::mbar_init(&slab_full[i], 1);
-      ptx::mbar_init(&slab_empty[i], 1);
+      ptx::mbar_init(&fold_full[i], kFoldWarps);
+      ptx::mbar_init(&item_empty[i], 1);
     }
     *abort_flag = 0;
     *never = 0;
@@ -208,6 +199,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ producer
     if (lane == 0 && !skip) {
       int it_strip = 0, it_slab = 0;
+      int k = 0;
+      uint32_t lap = 0;  // parity of the item ring's current lap
       bool ok = true;
       const int q_p = (int)((long long)(R + 1) * p.wp + (long long)tile * kTileM + (long long)b * p.wp - R);
       const int q_m = (int)((long long)(R + 1) * p.wp + (long long)tile * kTileM - (long long)b * p.wp - R);
@@ -226,23 +219,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         const TcItem *row_items = sitems + st * NA;
         for (int a = 0; a < NA; ++a) {
           const TcItem item = row_items[a];
-          const int slot = it_slab % p.n_slots;
-          if (!ptx::mbar_wait(&slab_empty[slot], ((it_slab / p.n_slots) & 1) ^ 1, abort_flag, p.budget)) {
+          if (!ptx::mbar_wait(&item_empty[k], lap ^ 1, abort_flag, p.budget)) {
             fail(2);
             ok = false;
             break;
           }
-          ptx::mbar_arrive_expect_tx(&slab_full[slot], item.bytes);
+          ptx::mbar_arrive_expect_tx(&slab_full[k], item.bytes);
           if (item.bytes > 0)
-            ptx::bulk_g2s(slots + (size_t)slot * p.slot_bytes, p.data + (size_t)item.off16 * 16, item.bytes,
-                          &slab_full[slot]);
+            ptx::bulk_g2s(slots + (size_t)k * p.slot_bytes, p.data + (size_t)item.off16 * 16, item.bytes,
+                          &slab_full[k]);
           ++it_slab;
+          if (++k == K) {
+            k = 0;
+            lap ^= 1;
+          }
         }
       }
       if (!ok) {
         // let copies already issued land before the block exits
-        for (int i = std::max(0, it_slab - p.n_slots); i < it_slab; ++i)
-          ptx::mbar_wait(&slab_full[i % p.n_slots], (i / p.n_slots) & 1, never, p.budget);
+        for (int i = std::max(0, it_slab - K); i < it_slab; ++i)
+          ptx::mbar_wait(&slab_full[i % K], (i / K) & 1, never, p.budget);
         for (int i = std::max(0, it_strip - 2); i < it_strip; ++i)
           ptx::mbar_wait(&strip_full[i & 1], (i >> 1) & 1, never, p.budget);
       }
@@ -253,48 +249,47 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = ptx::mbar_wait(acc_ready, 0, abort_flag, p.budget);
       if (!ok) fail(4);
       ptx::tc_fence_after();
-      int it_fold = 0, it_slab = 0;
-      // Descriptor templates (start-address field in 16-byte units; fields never carry).
+      int k = 0;
+      uint32_t lap = 0;
+      // B descriptor template (start-address field in 16-byte units; fields never carry)
       const uint64_t slot_desc = ptx::smem_desc(ptx::smem_addr(slots), 0, 128);
-      const uint64_t fold_desc = ptx::smem_desc(ptx::smem_addr(folds), 2048, 128);  // lbo: 128 rows x 16 B
       const uint32_t idesc_m128 = ptx::idesc_bf16_f32(kTileM, 0);
       for (int st = 0; st < p.stages && ok && !skip; ++st) {
         const TcItem *row_items = sitems + st * NA;
         for (int a = 0; a < NA; ++a) {
-          const int f = it_fold % NF, slot = it_slab % p.n_slots;
-          if (!ptx::mbar_wait(&fold_full[f], (it_fold / NF) & 1, abort_flag, p.budget)) {
+          if (!ptx::mbar_wait(&slab_full[k], lap, abort_flag, p.budget)) {
             fail(8);
             ok = false;
             break;
           }
-          if (!ptx::mbar_wait(&slab_full[slot], (it_slab / p.n_slots) & 1, abort_flag, p.budget)) {
+          if (!ptx::mbar_wait(&fold_full[k], lap, abort_flag, p.budget)) {
             fail(16);
             ok = false;
             break;
           }
           ptx::tc_fence_after();
           const TcItem item = row_items[a];
-          const uint64_t dA_hi = fold_desc + (uint64_t)((f * kFoldBytes) >> 4);
-          const uint64_t dA_lo = dA_hi + (8192 >> 4);
-          uint64_t dB = slot_desc + (uint64_t)(((uint32_t)slot * (uint32_t)p.slot_bytes) >> 4);
+          const uint32_t a_base = tmem + (uint32_t)(p.fold_col0 + 32 * k);
+          uint64_t dB = slot_desc + (uint64_t)(((uint32_t)k * (uint32_t)p.slot_bytes) >> 4);
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const uint32_t n = item.n[c];
             if (n == 0) continue;
-            const uint64_t ca = (uint64_t)((2 * c * 2048) >> 4);  // chunk c: k8 blocks 2c, 2c+1
-            const uint64_t dbh = dB + ((uint64_t)n << 16);          // lbo = 16 n bytes
-            const uint64_t dbl = dbh + 2u * n;                      // lo tile 32 n bytes later
+            const uint32_t a_hi = a_base + 16u * c, a_lo = a_hi + 8u;
+            const uint64_t dbh = dB + ((uint64_t)n << 16);  // lbo = 16 n bytes
+            const uint64_t dbl = dbh + 2u * n;              // lo tile 32 n bytes later
             const uint32_t idesc = idesc_m128 | ((n >> 3) << 17);
             const uint32_t d = tmem + item.col[c];
-            ptx::mma_bf16(d, dA_hi + ca, dbh, idesc, 1);
-            ptx::mma_bf16(d, dA_hi + ca, dbl, idesc, 1);
-            ptx::mma_bf16(d, dA_lo + ca, dbh, idesc, 1);
+            ptx::mma_bf16_ta(d, a_hi, dbh, idesc, 1);
+            ptx::mma_bf16_ta(d, a_hi, dbl, idesc, 1);
+            ptx::mma_bf16_ta(d, a_lo, dbh, idesc, 1);
             dB += 4u * n;  // next tile 64 n bytes later
           }
-          ptx::mma_commit(&slab_empty[slot]);
-          ptx::mma_commit(&fold_empty[f]);
-          ++it_slab;
-          ++it_fold;
+          ptx::mma_commit(&item_empty[k]);
+          if (++k == K) {
+            k = 0;
+            lap ^= 1;
+          }
         }
       }
       ptx::mma_commit(acc_full);
@@ -304,10 +299,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int fw = warp - 2;        // 0 .. kFoldWarps-1
     const int quarter = warp & 3;   // tensor-memory lanes 32*quarter .. +31
     const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-    const int half_cols = p.tmem_cols / 2;
-    const int col_begin = fw < 4 ? 0 : half_cols;
-    for (int col = col_begin; col < col_begin + half_cols; col += 32)
-      ptx::tmem_st32_zero(tmem + lane_base + (uint32_t)col);
+    const int nb = (p.acc_cols + 31) / 32;  // 32-column blocks of the accumulator
+    const int blk_begin = fw < 4 ? 0 : nb / 2, blk_end = fw < 4 ? nb / 2 : nb;
+    for (int j = blk_begin; j < blk_end; ++j) ptx::tmem_st32_zero(tmem + lane_base + (uint32_t)(32 * j));
     ptx::tmem_wait_st();
     ptx::tc_fence_before();
     __syncwarp();
@@ -315,9 +309,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     bool ok = true;
     if (!skip) {
-      const int ft = threadIdx.x - 64;
-      const int m = ft & 127, h = ft >> 7;  // row, 16-element half of the stage
-      int it_strip = 0, it_fold = 0;
+      const int m = 32 * quarter + lane;  // row (tensor-memory lane) this thread folds
+      const int h = fw >> 2;              // 16-element half of the stage = MMA chunk
+      int it_strip = 0, k = 0;
+      uint32_t lap = 0;
       for (int st = 0; st < p.stages && ok; ++st) {
         const int s = it_strip & 1;
         ok = ptx::mbar_wait(&strip_full[s], (it_strip >> 1) & 1, abort_flag, p.budget);
@@ -326,11 +321,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (lane == 0) fail(32);
           break;
         }
-        const float *X1 = reinterpret_cast<const float *>(strips + (size_t)s * 2 * p.strip_bytes);
-        const float *X2 = reinterpret_cast<const float *>(strips + (size_t)s * 2 * p.strip_bytes + p.strip_bytes);
+        float *X1 = reinterpret_cast<float *>(strips + (size_t)s * 2 * p.strip_bytes);
+        if (b > 0) {
+          // P = X(y+b) + X(y-b) in place: both strips share the swizzle, so the
+          // sum runs over physical float4s.
+          const float4 *X2 = reinterpret_cast<const float4 *>(strips + (size_t)s * 2 * p.strip_bytes + p.strip_bytes);
+          float4 *P4 = reinterpret_cast<float4 *>(X1);
+          for (int i = threadIdx.x - 64; i < L * 8; i += 32 * kFoldWarps) {
+            float4 u = P4[i];
+            const float4 v = X2[i];
+            u.x += v.x;
+            u.y += v.y;
+            u.z += v.z;
+            u.w += v.w;
+            P4[i] = u;
+          }
+          asm volatile("bar.sync 1, %0;" ::"r"(32 * kFoldWarps) : "memory");  // fold warps only
+        }
         for (int a = 0; a < NA; ++a) {
-          const int f = it_fold % NF;
-          ok = ptx::mbar_wait(&fold_empty[f], ((it_fold / NF) & 1) ^ 1, abort_flag, p.budget);
+          ok = ptx::mbar_wait(&item_empty[k], lap ^ 1, abort_flag, p.budget);
           ok = __all_sync(0xffffffffu, ok);
           if (!ok) {
             if (lane == 0) fail(64);
@@ -339,36 +348,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           float acc[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) acc[i] = 0.0f;
-          const int rp = m + R + a, rm = m + R - a;
-          add_row(X1, rp, h, acc);
-          if (a > 0) add_row(X1, rm, h, acc);
-          if (b > 0) {
-            add_row(X2, rp, h, acc);
-            if (a > 0) add_row(X2, rm, h, acc);
-          }
-          uint8_t *fo = folds + f * kFoldBytes;
+          add_row(X1, m + R + a, h, acc);
+          if (a > 0) add_row(X1, m + R - a, h, acc);
+          uint32_t hv[8], lv[8];
 #pragma unroll
-          for (int j = 0; j < 2; ++j) {  // k8 block 2h + j
-            uint4 hv, lv;
-            float hf[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) hf[e] = __bfloat162float(__float2bfloat16_rn(acc[8 * j + e]));
-            hv.x = pack_bf16x2(hf[0], hf[1]);
-            hv.y = pack_bf16x2(hf[2], hf[3]);
-            hv.z = pack_bf16x2(hf[4], hf[5]);
-            hv.w = pack_bf16x2(hf[6], hf[7]);
-            lv.x = pack_bf16x2(acc[8 * j + 0] - hf[0], acc[8 * j + 1] - hf[1]);
-            lv.y = pack_bf16x2(acc[8 * j + 2] - hf[2], acc[8 * j + 3] - hf[3]);
-            lv.z = pack_bf16x2(acc[8 * j + 4] - hf[4], acc[8 * j + 5] - hf[5]);
-            lv.w = pack_bf16x2(acc[8 * j + 6] - hf[6], acc[8 * j + 7] - hf[7]);
-            const int blk = 2 * h + j;
-            *reinterpret_cast<uint4 *>(fo + blk * 2048 + m * 16) = hv;
-            *reinterpret_cast<uint4 *>(fo + 8192 + blk * 2048 + m * 16) = lv;
+          for (int e = 0; e < 8; ++e) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(acc[2 * e], acc[2 * e + 1]);
+            const float2 hf = __bfloat1622float2(h2);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(acc[2 * e] - hf.x, acc[2 * e + 1] - hf.y);
+            hv[e] = *reinterpret_cast<const uint32_t *>(&h2);
+            lv[e] = *reinterpret_cast<const uint32_t *>(&l2);
           }
-          fence_proxy_async_smem();  // make the stores visible to the tensor cores
+          const uint32_t fa = tmem + lane_base + (uint32_t)(p.fold_col0 + 32 * k + 16 * h);
+          ptx::tmem_st8(fa, hv);
+          ptx::tmem_st8(fa + 8u, lv);
+          ptx::tmem_wait_st();
+          ptx::tc_fence_before();
           __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&fold_full[f]);
-          ++it_fold;
+          if (lane == 0) ptx::mbar_arrive(&fold_full[k]);
+          if (++k == p.n_items) {
+            k = 0;
+            lap ^= 1;
+          }
         }
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&strip_empty[s]);
@@ -386,8 +387,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool valid = done && y < p.py && x < p.px;
     float *row = p.part + ((size_t)b * p.part_stride + (size_t)y * p.px + x) * p.acc_cols;
     if (done) {
-      const int c_end = std::min(col_begin + half_cols, p.acc_cols);
-      for (int col = col_begin; col < c_end; col += 32) {
+      for (int j = blk_begin; j < blk_end; ++j) {
+        const int col = 32 * j;
         uint32_t r[32];
         ptx::tmem_ld32(tmem + lane_base + (uint32_t)col, r);
         ptx::tmem_wait_ld();
@@ -395,10 +396,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           float4 *dst = reinterpret_cast<float4 *>(row + col);
           const int nv = std::min(8, (p.acc_cols - col) >> 2);
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (j < nv)
-              dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                   __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          for (int q = 0; q < 8; ++q)
+            if (q < nv)
+              dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                   __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
         }
       }
     }
@@ -651,17 +652,20 @@ oam_status plan_launch(const oam_model *m, const TcLayout *L, Launch *out) {
   p.strip_rows = kTileM + 2 * R;
   p.strip_bytes = (p.strip_rows * 128 + 1023) & ~1023;  // 128-byte rows, 1024-byte aligned
   p.items_bytes = (int)((sizeof(TcItem) * L->stages * (R + 1) + 1023) & ~size_t(1023));
-  const int fixed = 1024 /* alignment slack */ + 1024 + p.items_bytes + 4 * p.strip_bytes + kFoldSlots * kFoldBytes;
-  p.n_slots = std::min(16, (kSmemLimit - fixed) / L->slot_bytes);
-  if (p.n_slots < 2) return OAM_ERR_UNSUPPORTED;
+  const int fixed = 1024 /* alignment slack */ + 1024 + p.items_bytes + 4 * p.strip_bytes;
+  p.fold_col0 = (L->acc_cols + 31) & ~31;
+  const int tmem_items = (512 - p.fold_col0) / kFoldCols;
+  p.n_items = std::min(kMaxItems, std::min(tmem_items, (kSmemLimit - fixed) / L->slot_bytes));
+  if (p.n_items < 2) return OAM_ERR_UNSUPPORTED;
   p.acc_cols = L->acc_cols;
-  p.tmem_cols = L->tmem_cols;
+  p.tmem_cols = 32;
+  while (p.tmem_cols < p.fold_col0 + kFoldCols * p.n_items) p.tmem_cols <<= 1;
   p.part = m->d_tc_part;
   p.part_stride = (size_t)m->grid.py * m->grid.px;
   p.status = m->d_status;
   p.budget = 4000000000LL;  // ~2 s at 2 GHz
   out->p = p;
-  out->smem = (size_t)fixed + (size_t)p.n_slots * p.slot_bytes;
+  out->smem = (size_t)fixed + (size_t)p.n_items * p.slot_bytes;
   if (out->smem > (size_t)kSmemLimit) return OAM_ERR_UNSUPPORTED;
   return OAM_OK;
 }
