@@ -197,6 +197,75 @@ oam_status oam_lsqr_noalloc(const oam_model *model, const float *d_s, float *d_x
 /* Workspace bytes for solver 0 = LSQR, 1 = FISTA. */
 oam_status oam_solver_work_bytes(const oam_model *model, int32_t solver, size_t *bytes);
 
+/* ------------------------------------------------------------- autotuning */
+/* Pick the tensor-core kernels' item-ring depth for this model's shapes by
+ * timing each candidate (CUDA events on `stream`, `reps` runs each after one
+ * warm-up); the choice is kept in the model.  Allocates and frees a scratch
+ * volume and signal buffer; synchronises `stream`.  No-op for
+ * OAM_PREC_FP32.  The paper has no counterpart (tuning of this implementation). */
+oam_status oam_model_autotune(oam_model *model, int32_t reps, void *stream, int32_t *ring_forward,
+                              int32_t *ring_adjoint);
+
+/* --------------------------------------------------------------- batching */
+/* Many uneven reconstructions in one CUDA-graph launch (the paper reconstructs
+ * one volume at a time; this is a serving feature).  Each job is LSQR (MB-L2)
+ * and/or FISTA (MB-L1) on its own model, signals, images and workspace (at
+ * least the larger of oam_solver_work_bytes(model, 0/1)); the jobs run on
+ * separate branches of one graph, so their kernels overlap on the GPU.  The
+ * graph is recorded on the first oam_batch_run after any oam_batch_set_job
+ * and replayed afterwards.  Buffers must stay valid until the run completes. */
+typedef struct oam_batch oam_batch;
+oam_status oam_batch_create(int32_t n_jobs, oam_batch **out);
+/* d_x_l2 / d_x_l1 may be NULL when the matching iteration count is 0. */
+oam_status oam_batch_set_job(oam_batch *batch, int32_t job, const oam_model *model, const float *d_s,
+                             float *d_x_l2, float *d_x_l1, const oam_lsqr_opts *lsqr, const oam_fista_opts *fista,
+                             void *d_work, size_t work_bytes);
+/* Launch every job on `stream` (asynchronous; synchronise the stream for results). */
+oam_status oam_batch_run(oam_batch *batch, void *stream);
+oam_status oam_batch_free(oam_batch *batch);
+
+/* ---------------------------------------------------------------- serving */
+/* A continuous-batching request server (no counterpart in the paper).  A host
+ * thread admits queued requests first-in first-out while a slot (CUDA stream)
+ * is free and the device-memory reservation stays within hbm_budget_bytes
+ * (a conservative per-request estimate: model, signals, two images,
+ * workspace); each admitted request builds its model, copies its host signals
+ * in, runs LSQR then FISTA, and copies both images out on its slot's stream,
+ * so requests on different slots overlap on the GPU.  Finished requests
+ * release their memory and slot to the next queued request.  Results do not
+ * depend on what else runs (all kernels are deterministic). */
+typedef struct oam_server oam_server;
+typedef struct {
+  size_t hbm_budget_bytes;
+  int32_t max_slots;
+  int32_t precision;                       /* oam_precision */
+  int32_t lsqr_iters, fista_iters, power_iters;
+  double lambda_rel;                       /* FISTA lambda = lambda_rel * max|A^T s| */
+} oam_server_opts;
+typedef struct {
+  int32_t state;     /* 0 queued, 1 running, 2 done, 3 failed */
+  int32_t error;     /* oam_status of a failed request */
+  double latency_s;  /* submit to completion (done or failed), else -1 */
+} oam_request_info;
+typedef struct {
+  int32_t queued, running, peak_running;
+  size_t reserved_bytes, peak_reserved_bytes;
+} oam_server_stats_t;
+/* Device bytes the server reserves for one request of this grid before
+ * admitting it (an upper bound of what the request allocates). */
+oam_status oam_request_footprint(int32_t precision, const oam_grid *grid, size_t *bytes);
+oam_status oam_server_create(const oam_server_opts *opts, oam_server **out);
+/* h_s: host signals (py*px*nt floats), h_x_l2 / h_x_l1: host images
+ * (py*px*nz floats, may be NULL); all must stay valid until the request ends. */
+oam_status oam_server_submit(oam_server *server, const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
+                             const float *h_s, float *h_x_l2, float *h_x_l1, int64_t *request_id);
+oam_status oam_server_poll(oam_server *server, int64_t request_id, oam_request_info *info);
+/* Block until the request ends or timeout_s passes (OAM_ERR_TIMEOUT). */
+oam_status oam_server_wait(oam_server *server, int64_t request_id, double timeout_s);
+oam_status oam_server_stats(oam_server *server, oam_server_stats_t *stats);
+/* Finish queued and running requests, then release the server. */
+oam_status oam_server_stop(oam_server *server);
+
 /* ---------------------------------------------------------------- timing */
 /* Device time of the operator kernels, measured with CUDA events recorded on
  * the caller's stream around the main kernel of every forward / adjoint

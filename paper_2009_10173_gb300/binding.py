@@ -18,7 +18,10 @@ OAM_PREC_FP32, OAM_PREC_BF16X3 = 0, 1
 
 EXPORTED = ("oam_build_model", "oam_model_free", "oam_model_get_info", "oam_model_slab_column", "oam_forward",
             "oam_adjoint", "oam_lsqr", "oam_l1_fista", "oam_solver_work_bytes", "oam_status_string",
-            "oam_version", "oam_profile_enable", "oam_profile_read", "oam_launch_count", "oam_lsqr_noalloc")
+            "oam_version", "oam_profile_enable", "oam_profile_read", "oam_launch_count", "oam_lsqr_noalloc",
+            "oam_model_autotune", "oam_batch_create", "oam_batch_set_job", "oam_batch_run", "oam_batch_free",
+            "oam_server_create", "oam_server_submit", "oam_server_poll", "oam_server_wait", "oam_server_stats",
+            "oam_server_stop", "oam_request_footprint")
 
 
 class OamSensor(ctypes.Structure):
@@ -69,6 +72,21 @@ class OamProfile(ctypes.Structure):
                 ("forward_ms", ctypes.c_double), ("adjoint_ms", ctypes.c_double)]
 
 
+class OamServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("lsqr_iters", ctypes.c_int32), ("fista_iters", ctypes.c_int32), ("power_iters", ctypes.c_int32),
+                ("lambda_rel", ctypes.c_double)]
+
+
+class OamRequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("error", ctypes.c_int32), ("latency_s", ctypes.c_double)]
+
+
+class OamServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int32), ("running", ctypes.c_int32), ("peak_running", ctypes.c_int32),
+                ("reserved_bytes", ctypes.c_size_t), ("peak_reserved_bytes", ctypes.c_size_t)]
+
+
 class OamError(RuntimeError):
     def __init__(self, fn, code):
         super().__init__(f"{fn} failed: {status_string(code)} ({code})")
@@ -103,6 +121,18 @@ def lib():
         L.oam_profile_enable.argtypes = [vp, i32]
         L.oam_profile_read.argtypes = [vp, P(OamProfile)]
         L.oam_launch_count.restype = ctypes.c_int64
+        L.oam_model_autotune.argtypes = [vp, i32, vp, P(i32), P(i32)]
+        L.oam_batch_create.argtypes = [i32, P(vp)]
+        L.oam_batch_set_job.argtypes = [vp, i32, vp, vp, vp, vp, P(OamLsqrOpts), P(OamFistaOpts), vp, sz]
+        L.oam_batch_run.argtypes = [vp, vp]
+        L.oam_batch_free.argtypes = [vp]
+        L.oam_server_create.argtypes = [P(OamServerOpts), P(vp)]
+        L.oam_server_submit.argtypes = [vp, P(OamSensor), P(OamGrid), P(OamEir), vp, vp, vp, P(ctypes.c_int64)]
+        L.oam_server_poll.argtypes = [vp, ctypes.c_int64, P(OamRequestInfo)]
+        L.oam_server_wait.argtypes = [vp, ctypes.c_int64, ctypes.c_double]
+        L.oam_server_stats.argtypes = [vp, P(OamServerStats)]
+        L.oam_server_stop.argtypes = [vp]
+        L.oam_request_footprint.argtypes = [i32, P(OamGrid), P(sz)]
         for f in EXPORTED:
             if f not in ("oam_status_string", "oam_version", "oam_launch_count"):
                 getattr(L, f).restype = ctypes.c_int
@@ -219,3 +249,71 @@ def oam_profile_read(model):
 
 def oam_launch_count():
     return lib().oam_launch_count()
+
+
+def oam_model_autotune(model, reps=3, stream=None):
+    f, a = ctypes.c_int32(), ctypes.c_int32()
+    _check("oam_model_autotune", lib().oam_model_autotune(model, int(reps), _stream(stream), ctypes.byref(f),
+                                                          ctypes.byref(a)))
+    return f.value, a.value
+
+
+def oam_batch_create(n_jobs):
+    h = ctypes.c_void_p()
+    _check("oam_batch_create", lib().oam_batch_create(int(n_jobs), ctypes.byref(h)))
+    return h
+
+
+def oam_batch_set_job(batch, job, model, s, x_l2, x_l1, lsqr_opts, fista_opts, work):
+    _check("oam_batch_set_job", lib().oam_batch_set_job(
+        batch, int(job), model, _ptr(s), _ptr(x_l2), _ptr(x_l1), ctypes.byref(lsqr_opts) if lsqr_opts else None,
+        ctypes.byref(fista_opts) if fista_opts else None, _ptr(work), work.numel() * work.element_size()))
+
+
+def oam_batch_run(batch, stream=None):
+    _check("oam_batch_run", lib().oam_batch_run(batch, _stream(stream)))
+
+
+def oam_batch_free(batch):
+    _check("oam_batch_free", lib().oam_batch_free(batch))
+
+
+def oam_server_create(opts):
+    h = ctypes.c_void_p()
+    _check("oam_server_create", lib().oam_server_create(ctypes.byref(opts), ctypes.byref(h)))
+    return h
+
+
+def oam_server_submit(server, sensor, grid, eir, h_s, h_x_l2=None, h_x_l1=None):
+    """h_* are host (CPU, preferably pinned) float32 tensors that must outlive the request."""
+    rid = ctypes.c_int64()
+    _check("oam_server_submit", lib().oam_server_submit(server, ctypes.byref(sensor), ctypes.byref(grid),
+                                                        ctypes.byref(eir), _ptr(h_s), _ptr(h_x_l2), _ptr(h_x_l1),
+                                                        ctypes.byref(rid)))
+    return rid.value
+
+
+def oam_server_poll(server, rid):
+    info = OamRequestInfo()
+    _check("oam_server_poll", lib().oam_server_poll(server, ctypes.c_int64(rid), ctypes.byref(info)))
+    return info
+
+
+def oam_server_wait(server, rid, timeout_s):
+    return lib().oam_server_wait(server, ctypes.c_int64(rid), ctypes.c_double(timeout_s))
+
+
+def oam_server_stats(server):
+    st = OamServerStats()
+    _check("oam_server_stats", lib().oam_server_stats(server, ctypes.byref(st)))
+    return st
+
+
+def oam_server_stop(server):
+    _check("oam_server_stop", lib().oam_server_stop(server))
+
+
+def oam_request_footprint(precision, grid):
+    n = ctypes.c_size_t()
+    _check("oam_request_footprint", lib().oam_request_footprint(int(precision), ctypes.byref(grid), ctypes.byref(n)))
+    return n.value

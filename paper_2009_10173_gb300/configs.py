@@ -43,3 +43,43 @@ BATCH_DEPTH = (128, 192, 256, 384)
 BATCH_NT = (512, 768, 1024)
 BATCH_FOCAL = (3e-3, 6e-3)
 BATCH_APERTURE = (2e-3, 4e-3)
+
+
+def batch_job(seed, base=None, nt_choice=None):
+    """One reconstruction of the batched workload: a scan grid, depth count and
+    sample count drawn from the batch sets, and a seeded sensor (focal length
+    U[3, 6] mm, aperture U[2, 4] mm); other parameters as the 200x200x300
+    workload, volume centred on the focus, 30 LSQR + 50 FISTA iterations."""
+    import numpy as np
+    base = VOLUME_200 if base is None else base
+    rng = np.random.Generator(np.random.PCG64(seed))
+    scan = int(rng.choice(BATCH_SCAN))
+    nz = int(rng.choice(BATCH_DEPTH))
+    nt = int(rng.choice(BATCH_NT)) if nt_choice is None else int(nt_choice)
+    focal = float(rng.uniform(*BATCH_FOCAL))
+    aperture = float(rng.uniform(*BATCH_APERTURE))
+    return scaled(base, px=scan, py=scan, nz=nz, nt=nt, focal_m=focal, aperture_m=aperture,
+                  z0_rel_m=-(nz / 2) * base["dz_m"], lsqr_iters=30, fista_iters=50, power_iters=20,
+                  lambda_rel=1e-3, seed=seed)
+
+
+def batch_workload(n=16, seed0=1000):
+    """The batched workload: jobs with seeds seed0 .. seed0 + n - 1."""
+    return [batch_job(seed0 + i) for i in range(n)]
+
+
+def next_nt(cfg):
+    """The next larger sample count of the batch set (used when the arrival
+    window check fails), or None."""
+    larger = [n for n in BATCH_NT if n > cfg["nt"]]
+    return scaled(cfg, nt=larger[0]) if larger else None
+
+
+def served_request(seed, p_large=0.05):
+    """A request of the served workload: sizes as the batched workload, with
+    probability p_large a 200x200x300 volume instead."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if rng.uniform() < p_large:
+        return scaled(VOLUME_200, lsqr_iters=30, fista_iters=50, power_iters=20, lambda_rel=1e-3, seed=seed)
+    return batch_job(seed + 7919)

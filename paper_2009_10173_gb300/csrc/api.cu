@@ -99,14 +99,14 @@ void plan_orbits(oam_model *m) {
     for (int a = -R; a <= R; ++a) m->h_tap_orbit[(b + R) * W + (a + R)] = id[std::abs(b) * (R + 1) + std::abs(a)];
 }
 
-void free_model(oam_model *m) {
+void free_model(oam_model *m, cudaStream_t st) {
   if (!m) return;
-  tc_free(m);
+  tc_free(m, st);
   for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
   void *ptrs[] = {m->d_status, m->d_tap_orbit, m->d_patch, m->d_band_lo, m->d_band, m->d_fwd_krange, m->d_fwd_off,
                   m->d_fwd, m->d_adj_nrange, m->d_adj_off, m->d_adj};
   for (void *p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, st);
   delete m;
 }
 
@@ -145,6 +145,8 @@ oam_status oam::upload_patches(oam_model *m, cudaStream_t st) {
 }
 
 std::atomic<long long> oam::g_launches{0};
+
+void oam::model_release(oam_model *m, cudaStream_t st) { free_model(m, st); }
 
 oam::ProfScope::ProfScope(const oam_model *m_, cudaStream_t s, bool f) : m(m_), st(s), fwd(f) {
   oam_model::Prof &p = m->prof;
@@ -243,6 +245,7 @@ oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const
   m->cut = eir->trunc_sigma * m->sigma_s;
   plan_orbits(m);
   cudaStream_t st = as_stream(stream);
+  m->alloc_stream = st;
   rc = dev_alloc(m, &m->d_status, 1);
   if (!rc && cudaMemsetAsync(m->d_status, 0, sizeof(int), st) != cudaSuccess) rc = OAM_ERR_CUDA;
   if (!rc) rc = upload_patches(m, st);
@@ -252,7 +255,8 @@ oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const
   if (rc) {
     cudaStreamSynchronize(st);
     cudaGetLastError();
-    free_model(m);
+    free_model(m, st);
+    cudaStreamSynchronize(st);
     return rc;
   }
   *out = m;
@@ -262,7 +266,8 @@ oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const
 oam_status oam_model_free(oam_model *model) {
   if (!model) return OAM_OK;
   cudaDeviceSynchronize();
-  free_model(model);
+  free_model(model, nullptr);
+  cudaStreamSynchronize(nullptr);
   return OAM_OK;
 }
 

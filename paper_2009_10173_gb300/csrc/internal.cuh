@@ -82,6 +82,7 @@ struct oam_model {
   float *d_tc_part = nullptr;  // per-part partial sums of the tensor-core operators
 
   int *d_status = nullptr;  // device error word (bounded waits that ran out)
+  cudaStream_t alloc_stream = nullptr;  // stream of the stream-ordered allocations (the build stream)
 
   // operator timing (oam_profile_enable / oam_profile_read)
   struct Prof {
@@ -140,10 +141,14 @@ oam_status adjoint_fp32(const oam_model *m, const float *s, float *H, cudaStream
 
 // op_tc.cu
 oam_status tc_build(oam_model *m, cudaStream_t st);
-void tc_free(oam_model *m);
+void tc_free(oam_model *m, cudaStream_t st);
 oam_status forward_tc(const oam_model *m, const float *H, float *s, cudaStream_t st);
 oam_status adjoint_tc(const oam_model *m, const float *s, float *H, cudaStream_t st);
 double tc_exec_flops(const oam_model *m, int dir);
+oam_status tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_fwd, int *best_adj);
+
+// free every device buffer of a model with cudaFreeAsync on `st`, then the model
+void model_release(oam_model *m, cudaStream_t st);
 
 // dispatch on the model's precision
 oam_status apply_forward(const oam_model *m, const float *H, float *s, cudaStream_t st);
@@ -156,10 +161,12 @@ inline size_t sig_elems(const oam_model *m) {
   return (size_t)m->grid.py * m->grid.px * m->grid.nt;
 }
 
+// Model memory comes from the stream-ordered allocator on the build stream, so
+// releasing a model never forces a device-wide synchronisation.
 template <typename T>
 oam_status dev_alloc(oam_model *m, T **p, size_t count) {
   if (count == 0) count = 1;
-  if (cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
+  if (cudaMallocAsync((void **)p, count * sizeof(T), m->alloc_stream) != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
     return OAM_ERR_OOM;

@@ -74,6 +74,7 @@ struct TcLayout {
   int in_lo = 0;          // input index of packed element 0
   int in_elems = 0;       // packed elements per position (32 * stages)
   int slot_bytes = 0;     // shared-memory slot per item
+  int ring_pref = 0;      // item-ring depth chosen by oam_model_autotune (0 = deepest that fits)
   TcItem *d_items = nullptr;
   uint8_t *d_data = nullptr;
   size_t data_bytes = 0;
@@ -656,6 +657,7 @@ oam_status plan_launch(const oam_model *m, const TcLayout *L, Launch *out) {
   p.fold_col0 = (L->acc_cols + 31) & ~31;
   const int tmem_items = (512 - p.fold_col0) / kFoldCols;
   p.n_items = std::min(kMaxItems, std::min(tmem_items, (kSmemLimit - fixed) / L->slot_bytes));
+  if (L->ring_pref >= 2) p.n_items = std::min(p.n_items, L->ring_pref);
   if (p.n_items < 2) return OAM_ERR_UNSUPPORTED;
   p.acc_cols = L->acc_cols;
   p.tmem_cols = 32;
@@ -734,17 +736,17 @@ oam_status oam::tc_build(oam_model *m, cudaStream_t st) {
   return OAM_OK;
 }
 
-void oam::tc_free(oam_model *m) {
+void oam::tc_free(oam_model *m, cudaStream_t st) {
   for (TcLayout *L : {m->tc_fwd, m->tc_adj}) {
     if (!L) continue;
-    if (L->d_items) cudaFree(L->d_items);
-    if (L->d_data) cudaFree(L->d_data);
+    if (L->d_items) cudaFreeAsync(L->d_items, st);
+    if (L->d_data) cudaFreeAsync(L->d_data, st);
     delete L;
   }
   m->tc_fwd = m->tc_adj = nullptr;
-  if (m->d_tc_pack) cudaFree(m->d_tc_pack);
+  if (m->d_tc_pack) cudaFreeAsync(m->d_tc_pack, st);
   m->d_tc_pack = nullptr;
-  if (m->d_tc_part) cudaFree(m->d_tc_part);
+  if (m->d_tc_part) cudaFreeAsync(m->d_tc_part, st);
   m->d_tc_part = nullptr;
 }
 
@@ -759,4 +761,54 @@ oam_status oam::forward_tc(const oam_model *m, const float *H, float *s, cudaStr
 
 oam_status oam::adjoint_tc(const oam_model *m, const float *s, float *H, cudaStream_t st) {
   return run_corr(m, m->tc_adj, s, m->grid.nt, H, m->grid.nz, st);
+}
+
+// ---------------------------------------------------------------- autotuner
+// Ring depth per direction: time each candidate depth on the model's own
+// shapes (CUDA events on `st`) and keep the fastest.
+oam_status oam::tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_fwd, int *best_adj) {
+  if (!m->tc_fwd) return OAM_ERR_UNSUPPORTED;
+  const size_t nv = vol_elems(m), ns = sig_elems(m);
+  float *buf = nullptr;
+  if (cudaMalloc((void **)&buf, (nv + ns) * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return OAM_ERR_OOM;
+  }
+  oam_status rc = OAM_OK;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaMemsetAsync(buf, 0, (nv + ns) * sizeof(float), st);
+  for (int dir = 0; dir < 2 && !rc; ++dir) {
+    TcLayout *L = dir == 0 ? m->tc_fwd : m->tc_adj;
+    L->ring_pref = 0;
+    Launch lp;
+    if ((rc = plan_launch(m, L, &lp))) break;
+    const int deepest = lp.p.n_items;
+    float best_ms = 1e30f;
+    int best = deepest;
+    for (int depth = 2; depth <= deepest; depth += (depth < 4 ? 1 : 2)) {
+      L->ring_pref = depth;
+      for (int r = 0; r <= reps && !rc; ++r) {  // first run warms up
+        if (r == 1) cudaEventRecord(e0, st);
+        rc = dir == 0 ? run_corr(m, L, buf, m->grid.nz, buf + nv, m->grid.nt, st)
+                      : run_corr(m, L, buf + nv, m->grid.nt, buf, m->grid.nz, st);
+      }
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = OAM_ERR_CUDA;
+      if (rc) break;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = depth;
+      }
+    }
+    L->ring_pref = best;
+    (dir == 0 ? *best_fwd : *best_adj) = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  return rc;
 }

@@ -1,0 +1,476 @@
+// Runtime around the operators and solvers: the ring-depth autotuner entry
+// point, batched reconstructions in one CUDA graph, and a continuous-batching
+// request server.  None of this is in the paper, which reconstructs one volume
+// at a time; it serves many uneven reconstructions on one GPU.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace oam;
+
+// ---------------------------------------------------------------- autotune
+extern "C" oam_status oam_model_autotune(oam_model *m, int32_t reps, void *stream, int32_t *ring_forward,
+                                         int32_t *ring_adjoint) {
+  if (!m || reps < 1) return OAM_ERR_INVALID_ARG;
+  if (m->precision != OAM_PREC_BF16X3) return OAM_OK;  // nothing to tune on the FP32 path
+  int f = 0, a = 0;
+  oam_status rc = tc_autotune(m, reps, as_stream(stream), &f, &a);
+  if (rc) return rc;
+  if (ring_forward) *ring_forward = f;
+  if (ring_adjoint) *ring_adjoint = a;
+  return OAM_OK;
+}
+
+// ---------------------------------------------------------------- batch
+struct oam_batch {
+  struct Job {
+    const oam_model *model = nullptr;
+    const float *s = nullptr;
+    float *x_l2 = nullptr, *x_l1 = nullptr;
+    oam_lsqr_opts lsqr{};
+    oam_fista_opts fista{};
+    void *work = nullptr;
+    size_t work_bytes = 0;
+    bool set = false;
+  };
+  std::vector<Job> jobs;
+  cudaStream_t origin = nullptr;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool dirty = true;
+};
+
+namespace {
+
+void batch_release_graph(oam_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+void batch_destroy(oam_batch *b) {
+  batch_release_graph(b);
+  for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+}
+
+// Record every job (LSQR, then FISTA) on its own branch of one graph.
+oam_status batch_capture(oam_batch *b) {
+  batch_release_graph(b);
+  OAM_CUDA_TRY(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed));
+  oam_status rc = OAM_OK;
+  if (cudaEventRecord(b->fork, b->origin) != cudaSuccess) rc = OAM_ERR_CUDA;
+  for (size_t j = 0; j < b->jobs.size() && !rc; ++j) {
+    const oam_batch::Job &J = b->jobs[j];
+    cudaStream_t st = b->streams[j];
+    if (cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess) {
+      rc = OAM_ERR_CUDA;
+      break;
+    }
+    if (J.lsqr.iters > 0) rc = oam_lsqr(J.model, J.s, J.x_l2, &J.lsqr, nullptr, J.work, J.work_bytes, st);
+    if (!rc && J.fista.iters > 0) rc = oam_l1_fista(J.model, J.s, J.x_l1, &J.fista, nullptr, J.work, J.work_bytes, st);
+    if (!rc && cudaEventRecord(b->joins[j], st) != cudaSuccess) rc = OAM_ERR_CUDA;
+    if (!rc && cudaStreamWaitEvent(b->origin, b->joins[j], 0) != cudaSuccess) rc = OAM_ERR_CUDA;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t end = cudaStreamEndCapture(b->origin, &g);
+  if (rc || end != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc ? rc : OAM_ERR_CUDA;
+  }
+  b->graph = g;
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    batch_release_graph(b);
+    return OAM_ERR_CUDA;
+  }
+  b->dirty = false;
+  return OAM_OK;
+}
+
+}  // namespace
+
+extern "C" oam_status oam_batch_create(int32_t n_jobs, oam_batch **out) {
+  if (!out || n_jobs < 1 || n_jobs > 4096) return OAM_ERR_INVALID_ARG;
+  *out = nullptr;
+  oam_batch *b = new (std::nothrow) oam_batch();
+  if (!b) return OAM_ERR_OOM;
+  b->jobs.resize(n_jobs);
+  bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int j = 0; j < n_jobs && ok; ++j) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) b->streams.push_back(s);
+    ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) b->joins.push_back(e);
+  }
+  if (!ok) {
+    cudaGetLastError();
+    batch_destroy(b);
+    return OAM_ERR_CUDA;
+  }
+  *out = b;
+  return OAM_OK;
+}
+
+extern "C" oam_status oam_batch_set_job(oam_batch *b, int32_t j, const oam_model *model, const float *d_s,
+                                        float *d_x_l2, float *d_x_l1, const oam_lsqr_opts *lsqr,
+                                        const oam_fista_opts *fista, void *d_work, size_t work_bytes) {
+  if (!b || j < 0 || j >= (int)b->jobs.size() || !model || !d_s || !d_work) return OAM_ERR_INVALID_ARG;
+  if ((!lsqr || lsqr->iters <= 0) && (!fista || fista->iters <= 0)) return OAM_ERR_INVALID_ARG;
+  size_t need = 0, n1 = 0;
+  oam_solver_work_bytes(model, 0, &need);
+  oam_solver_work_bytes(model, 1, &n1);
+  need = std::max(need, n1);
+  if (work_bytes < need) return OAM_ERR_INVALID_ARG;
+  oam_batch::Job &J = b->jobs[j];
+  J.model = model;
+  J.s = d_s;
+  J.x_l2 = d_x_l2;
+  J.x_l1 = d_x_l1;
+  J.lsqr = lsqr ? *lsqr : oam_lsqr_opts{};
+  J.fista = fista ? *fista : oam_fista_opts{};
+  if (J.lsqr.iters > 0 && !d_x_l2) return OAM_ERR_INVALID_ARG;
+  if (J.fista.iters > 0 && !d_x_l1) return OAM_ERR_INVALID_ARG;
+  J.work = d_work;
+  J.work_bytes = work_bytes;
+  J.set = true;
+  b->dirty = true;
+  return OAM_OK;
+}
+
+extern "C" oam_status oam_batch_run(oam_batch *b, void *stream) {
+  if (!b) return OAM_ERR_INVALID_ARG;
+  for (const auto &J : b->jobs)
+    if (!J.set) return OAM_ERR_INVALID_ARG;
+  if (b->dirty) {
+    oam_status rc = batch_capture(b);
+    if (rc) return rc;
+  }
+  OAM_CUDA_TRY(cudaGraphLaunch(b->exec, as_stream(stream)));
+  count_launch(1);
+  return OAM_OK;
+}
+
+extern "C" oam_status oam_batch_free(oam_batch *b) {
+  if (!b) return OAM_OK;
+  cudaDeviceSynchronize();
+  batch_destroy(b);
+  return OAM_OK;
+}
+
+// ---------------------------------------------------------------- server
+// Requests carry host signals and host image buffers.  A host thread admits
+// queued requests while a slot (stream) is free and the device-memory budget
+// holds their footprint, builds each request's model and buffers, and
+// enqueues copy-in, LSQR, FISTA and copy-out on the slot's stream; requests on
+// different slots overlap on the GPU.  Finished slots free their memory and
+// take the next request (continuous batching).  Completion is detected with
+// event queries, never with unbounded waits.
+struct oam_server {
+  struct Req {
+    int64_t id = 0;
+    oam_sensor sensor{};
+    oam_grid grid{};
+    oam_eir eir{};
+    const float *h_s = nullptr;
+    float *h_x2 = nullptr, *h_x1 = nullptr;
+    int32_t state = 0;  // 0 queued, 1 running, 2 done, 3 failed
+    oam_status error = OAM_OK;
+    size_t reserved = 0;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    // device resources while running
+    oam_model *model = nullptr;
+    float *d_s = nullptr, *d_x2 = nullptr, *d_x1 = nullptr;
+    void *d_work = nullptr;
+    int slot = -1;
+    cudaEvent_t done_ev = nullptr;
+  };
+  oam_server_opts opts{};
+  int device = 0;
+  std::vector<cudaStream_t> streams;
+  std::vector<bool> slot_busy;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<int64_t> queue;
+  std::map<int64_t, Req> reqs;
+  int64_t next_id = 1;
+  size_t reserved = 0, peak_reserved = 0;
+  int running = 0, peak_running = 0;
+  bool stop = false;
+  std::thread worker;
+};
+
+namespace {
+
+size_t vol_bytes(const oam_grid &g) { return (size_t)g.px * g.py * g.nz * sizeof(float); }
+size_t sig_bytes(const oam_grid &g) { return (size_t)g.px * g.py * g.nt * sizeof(float); }
+
+// Device-memory reservation for a request before its model exists: signals,
+// two images, solver workspace, and an upper bound of the model (band form,
+// FP32 layouts, tensor-core tiles and per-|b| partial sums).
+size_t footprint_estimate(const oam_server_opts &o, const oam_grid &g) {
+  const size_t R = (g.win - 1) / 2;
+  const size_t orbits = (R + 1) * (R + 1);
+  const size_t band = 512;  // samples per (orbit, depth) upper bound
+  size_t model = orbits * g.nz * band * 4 * 3;  // band form + two FP32 layouts
+  if (o.precision == OAM_PREC_BF16X3) {
+    model += orbits * g.nz * band * 2 * 2 * 2;                      // BF16 hi/lo tiles, both directions
+    model += (R + 1) * (size_t)g.px * g.py * 512 * sizeof(float);   // per-|b| partial sums
+    model += (size_t)(g.py + 2 * R + 2) * (g.px + R) * 512 * sizeof(float);  // staged input
+  }
+  const size_t work = 256 * 1024 + 2 * sig_bytes(g) + 3 * vol_bytes(g);
+  return model + sig_bytes(g) + 2 * vol_bytes(g) + work;
+}
+
+void release(oam_server *S, oam_server::Req &r) {
+  // the request's stream is idle (its completion event fired): free on it
+  cudaStream_t st = r.slot >= 0 ? S->streams[r.slot] : nullptr;
+  if (r.model) model_release(r.model, st);
+  if (r.d_s) cudaFreeAsync(r.d_s, st);
+  if (r.d_x2) cudaFreeAsync(r.d_x2, st);
+  if (r.d_x1) cudaFreeAsync(r.d_x1, st);
+  if (r.d_work) cudaFreeAsync(r.d_work, st);
+  if (r.done_ev) cudaEventDestroy(r.done_ev);
+  r.model = nullptr;
+  r.d_s = r.d_x2 = r.d_x1 = nullptr;
+  r.d_work = nullptr;
+  r.done_ev = nullptr;
+  if (r.slot >= 0) S->slot_busy[r.slot] = false;
+  r.slot = -1;
+  S->reserved -= r.reserved;
+  r.reserved = 0;
+  S->running -= 1;
+}
+
+// Build and enqueue one admitted request (server thread, lock not held).
+oam_status launch(oam_server *S, oam_server::Req &r) {
+  cudaStream_t st = S->streams[r.slot];
+  oam_status rc = oam_build_model(&r.sensor, &r.grid, &r.eir, (oam_precision)S->opts.precision, st, &r.model);
+  if (rc) return rc;
+  size_t w0 = 0, w1 = 0;
+  oam_solver_work_bytes(r.model, 0, &w0);
+  oam_solver_work_bytes(r.model, 1, &w1);
+  const size_t wb = std::max(w0, w1);
+  if (cudaMallocAsync((void **)&r.d_s, sig_bytes(r.grid), st) != cudaSuccess ||
+      cudaMallocAsync((void **)&r.d_x2, vol_bytes(r.grid), st) != cudaSuccess ||
+      cudaMallocAsync((void **)&r.d_x1, vol_bytes(r.grid), st) != cudaSuccess ||
+      cudaMallocAsync(&r.d_work, wb, st) != cudaSuccess) {
+    cudaGetLastError();
+    return OAM_ERR_OOM;
+  }
+  OAM_CUDA_TRY(cudaEventCreateWithFlags(&r.done_ev, cudaEventDisableTiming));
+  OAM_CUDA_TRY(cudaMemcpyAsync(r.d_s, r.h_s, sig_bytes(r.grid), cudaMemcpyHostToDevice, st));
+  oam_lsqr_opts lo{S->opts.lsqr_iters, 0.0};
+  oam_fista_opts fo{};
+  fo.iters = S->opts.fista_iters;
+  fo.power_iters = S->opts.power_iters;
+  fo.nonneg = 1;
+  fo.lambda = -1.0;
+  fo.lambda_rel = S->opts.lambda_rel;
+  fo.L = 0.0;
+  if (lo.iters > 0 && (rc = oam_lsqr(r.model, r.d_s, r.d_x2, &lo, nullptr, r.d_work, wb, st))) return rc;
+  if (fo.iters > 0 && (rc = oam_l1_fista(r.model, r.d_s, r.d_x1, &fo, nullptr, r.d_work, wb, st))) return rc;
+  if (r.h_x2 && lo.iters > 0)
+    OAM_CUDA_TRY(cudaMemcpyAsync(r.h_x2, r.d_x2, vol_bytes(r.grid), cudaMemcpyDeviceToHost, st));
+  if (r.h_x1 && fo.iters > 0)
+    OAM_CUDA_TRY(cudaMemcpyAsync(r.h_x1, r.d_x1, vol_bytes(r.grid), cudaMemcpyDeviceToHost, st));
+  OAM_CUDA_TRY(cudaEventRecord(r.done_ev, st));
+  return OAM_OK;
+}
+
+void server_loop(oam_server *S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (true) {
+    // 1. retire finished requests
+    for (auto &kv : S->reqs) {
+      oam_server::Req &r = kv.second;
+      if (r.state != 1) continue;
+      const cudaError_t q = cudaEventQuery(r.done_ev);
+      if (q == cudaErrorNotReady) continue;
+      r.state = q == cudaSuccess ? 2 : 3;
+      if (q != cudaSuccess) {
+        r.error = OAM_ERR_CUDA;
+        cudaGetLastError();
+      }
+      r.t_done = std::chrono::steady_clock::now();
+      release(S, r);
+      S->cv.notify_all();
+    }
+    // 2. admit queued requests (first in, first out) while a slot and memory are free
+    while (!S->queue.empty()) {
+      oam_server::Req &r = S->reqs[S->queue.front()];
+      const size_t need = footprint_estimate(S->opts, r.grid);
+      int slot = -1;
+      for (int i = 0; i < (int)S->slot_busy.size(); ++i)
+        if (!S->slot_busy[i]) {
+          slot = i;
+          break;
+        }
+      if (slot < 0) break;
+      if (need > S->opts.hbm_budget_bytes) {  // can never fit
+        S->queue.pop_front();
+        r.state = 3;
+        r.error = OAM_ERR_OOM;
+        r.t_done = std::chrono::steady_clock::now();
+        S->cv.notify_all();
+        continue;
+      }
+      if (S->reserved + need > S->opts.hbm_budget_bytes) break;
+      S->queue.pop_front();
+      r.slot = slot;
+      S->slot_busy[slot] = true;
+      r.reserved = need;
+      S->reserved += need;
+      S->peak_reserved = std::max(S->peak_reserved, S->reserved);
+      S->running += 1;
+      S->peak_running = std::max(S->peak_running, S->running);
+      r.state = 1;
+      lk.unlock();
+      const oam_status rc = launch(S, r);
+      lk.lock();
+      if (rc) {
+        cudaStreamSynchronize(S->streams[slot]);
+        cudaGetLastError();
+        r.state = 3;
+        r.error = rc;
+        r.t_done = std::chrono::steady_clock::now();
+        release(S, r);
+        S->cv.notify_all();
+      }
+    }
+    if (S->stop && S->queue.empty() && S->running == 0) break;
+    S->cv.wait_for(lk, std::chrono::microseconds(200));
+  }
+}
+
+}  // namespace
+
+extern "C" oam_status oam_request_footprint(int32_t precision, const oam_grid *grid, size_t *bytes) {
+  if (!grid || !bytes || grid->win < 1 || grid->px < 1 || grid->py < 1 || grid->nz < 1 || grid->nt < 1)
+    return OAM_ERR_INVALID_ARG;
+  if (precision != OAM_PREC_FP32 && precision != OAM_PREC_BF16X3) return OAM_ERR_INVALID_ARG;
+  oam_server_opts o{};
+  o.precision = precision;
+  *bytes = footprint_estimate(o, *grid);
+  return OAM_OK;
+}
+
+extern "C" oam_status oam_server_create(const oam_server_opts *opts, oam_server **out) {
+  if (!opts || !out || opts->max_slots < 1 || opts->max_slots > 256 || opts->hbm_budget_bytes == 0 ||
+      opts->lsqr_iters < 0 || opts->fista_iters < 0 || opts->power_iters < 1 ||
+      (opts->precision != OAM_PREC_FP32 && opts->precision != OAM_PREC_BF16X3))
+    return OAM_ERR_INVALID_ARG;
+  *out = nullptr;
+  oam_server *S = new (std::nothrow) oam_server();
+  if (!S) return OAM_ERR_OOM;
+  S->opts = *opts;
+  if (cudaGetDevice(&S->device) != cudaSuccess) {
+    delete S;
+    return OAM_ERR_CUDA;
+  }
+  for (int i = 0; i < opts->max_slots; ++i) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      for (cudaStream_t t : S->streams) cudaStreamDestroy(t);
+      delete S;
+      return OAM_ERR_CUDA;
+    }
+    S->streams.push_back(s);
+  }
+  S->slot_busy.assign(opts->max_slots, false);
+  S->worker = std::thread(server_loop, S);
+  *out = S;
+  return OAM_OK;
+}
+
+extern "C" oam_status oam_server_submit(oam_server *S, const oam_sensor *sensor, const oam_grid *grid,
+                                        const oam_eir *eir, const float *h_s, float *h_x_l2, float *h_x_l1,
+                                        int64_t *request_id) {
+  if (!S || !sensor || !grid || !eir || !h_s || !request_id) return OAM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->stop) return OAM_ERR_BUSY;
+  oam_server::Req r;
+  r.id = S->next_id++;
+  r.sensor = *sensor;
+  r.grid = *grid;
+  r.eir = *eir;
+  r.h_s = h_s;
+  r.h_x2 = h_x_l2;
+  r.h_x1 = h_x_l1;
+  r.t_submit = std::chrono::steady_clock::now();
+  S->reqs[r.id] = r;
+  S->queue.push_back(r.id);
+  *request_id = r.id;
+  S->cv.notify_all();
+  return OAM_OK;
+}
+
+extern "C" oam_status oam_server_poll(oam_server *S, int64_t id, oam_request_info *info) {
+  if (!S || !info) return OAM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return OAM_ERR_INVALID_ARG;
+  const oam_server::Req &r = it->second;
+  info->state = r.state;
+  info->error = r.error;
+  info->latency_s = (r.state >= 2) ? std::chrono::duration<double>(r.t_done - r.t_submit).count() : -1.0;
+  return OAM_OK;
+}
+
+extern "C" oam_status oam_server_wait(oam_server *S, int64_t id, double timeout_s) {
+  if (!S || !(timeout_s >= 0)) return OAM_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return OAM_ERR_INVALID_ARG;
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+  while (it->second.state < 2) {
+    if (S->cv.wait_until(lk, deadline) == std::cv_status::timeout && it->second.state < 2) return OAM_ERR_TIMEOUT;
+  }
+  return it->second.state == 2 ? OAM_OK : it->second.error;
+}
+
+extern "C" oam_status oam_server_stats(oam_server *S, oam_server_stats_t *st) {
+  if (!S || !st) return OAM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  st->queued = (int32_t)S->queue.size();
+  st->running = S->running;
+  st->peak_running = S->peak_running;
+  st->reserved_bytes = S->reserved;
+  st->peak_reserved_bytes = S->peak_reserved;
+  return OAM_OK;
+}
+
+extern "C" oam_status oam_server_stop(oam_server *S) {
+  if (!S) return OAM_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->cv.notify_all();
+  }
+  if (S->worker.joinable()) S->worker.join();
+  for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
+  delete S;
+  return OAM_OK;
+}

@@ -1,0 +1,107 @@
+"""Served reconstructions: Poisson-arriving requests over the C request server.
+
+    python -m paper_2009_10173_gb300.serve --rates 2 20 --requests 60
+
+For each arrival rate, requests (sizes as the batched workload, with an
+occasional 200x200x300 volume) are submitted at exponential inter-arrival
+times to one oam_server with a 150 GB device-memory budget; the server admits
+them as slots and memory free up, and their work overlaps on the GPU.  Prints
+one JSON line per rate: offered and achieved load, volumes/s, p50/p99 latency.
+Signals come from a pool of prepared instances (vessel phantom, 20 dB noise),
+prepared before the clock starts.  Marshalling only: all arithmetic runs in
+liboam.so.
+"""
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import binding as B
+from . import configs, inputs
+from .batch import build_model
+
+
+class Instance:
+    """A prepared request: configuration, pinned host signals and image buffers."""
+
+    def __init__(self, cfg, precision):
+        cfg, m = build_model(cfg, precision)
+        H = inputs.phantom(cfg, cfg.get("seed", 0), kind="vessels", count=10)
+        clean = m.forward(torch.from_numpy(H.astype(np.float32)).cuda()).cpu().numpy()
+        m.close()
+        noisy = inputs.add_noise(clean, 20.0, cfg.get("seed", 0) + 10 ** 6).astype(np.float32)
+        self.cfg = cfg
+        self.structs = B.structs_from_config(cfg)
+        self.h_s = torch.from_numpy(noisy).pin_memory()
+        self.vol_shape = (cfg["py"], cfg["px"], cfg["nz"])
+
+    def new_outputs(self):
+        return (torch.empty(self.vol_shape, dtype=torch.float32).pin_memory(),
+                torch.empty(self.vol_shape, dtype=torch.float32).pin_memory())
+
+
+def make_server(budget_bytes=150 * 10 ** 9, slots=8, precision=B.OAM_PREC_BF16X3, lsqr_iters=30, fista_iters=50,
+                power_iters=20, lambda_rel=1e-3):
+    opts = B.OamServerOpts(int(budget_bytes), int(slots), int(precision), int(lsqr_iters), int(fista_iters),
+                           int(power_iters), float(lambda_rel))
+    return B.oam_server_create(opts)
+
+
+def run_rate(server, pool, rate, n_requests, seed, timeout_s=3600.0):
+    """Submit n_requests at Poisson arrival times (rate per second), wait for all."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, n_requests)
+    picks = rng.integers(0, len(pool), n_requests)
+    keep = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for i in range(n_requests):
+        t_next += gaps[i]
+        delay = t_next - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        inst = pool[picks[i]]
+        x2, x1 = inst.new_outputs()
+        s, g, e = inst.structs
+        rid = B.oam_server_submit(server, s, g, e, inst.h_s, x2, x1)
+        keep.append((rid, inst, x2, x1))
+    lat, failed = [], 0
+    for rid, inst, x2, x1 in keep:
+        rc = B.oam_server_wait(server, rid, timeout_s)
+        info = B.oam_server_poll(server, rid)
+        if rc != B.OAM_OK or info.state != 2:
+            failed += 1
+        else:
+            lat.append(info.latency_s)
+    makespan = time.perf_counter() - t0
+    stats = B.oam_server_stats(server)
+    return {"rate_offered_per_s": rate, "requests": n_requests, "completed": len(lat), "failed": failed,
+            "makespan_s": makespan, "volumes_per_s": len(lat) / makespan,
+            "p50_latency_s": float(np.percentile(lat, 50)) if lat else None,
+            "p99_latency_s": float(np.percentile(lat, 99)) if lat else None,
+            "peak_running": stats.peak_running, "peak_reserved_gb": stats.peak_reserved_bytes / 1e9}, keep
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--rates", type=float, nargs="+", default=[2.0, 20.0])
+    p.add_argument("--requests", type=int, default=60)
+    p.add_argument("--pool", type=int, default=12)
+    p.add_argument("--slots", type=int, default=8)
+    p.add_argument("--budget-gb", type=float, default=150.0)
+    a = p.parse_args()
+    pool = [Instance(configs.served_request(2000 + j), B.OAM_PREC_BF16X3) for j in range(a.pool)]
+    for k, rate in enumerate(a.rates):
+        server = make_server(a.budget_gb * 1e9, a.slots)
+        res, _ = run_rate(server, pool, rate, a.requests, seed=3000 + k)
+        B.oam_server_stop(server)
+        res.update({"workload": "served: Poisson arrivals, sizes as the batched workload plus occasional "
+                                "200x200x300 volumes, 30 LSQR + 50 FISTA each",
+                    "slots": a.slots, "budget_gb": a.budget_gb, "pool_instances": a.pool})
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+"""Batched and served reconstructions on the GPU (through the C ABI).
+
+* A batch of uneven jobs in one CUDA-graph launch gives exactly the images of
+  each job run on its own (the kernels are deterministic), and one small job
+  agrees with the FP64 oracle's LSQR and FISTA.
+* The request server returns, for every request in a mix of concurrent
+  requests, exactly the images of the same request served alone; it respects
+  its device-memory budget, reports invalid requests as failed without
+  disturbing the others, and its bounded waits time out.
+* The ring-depth autotuner keeps results unchanged.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import solvers
+from paper_2009_10173_gb300 import binding as B
+from paper_2009_10173_gb300 import configs, inputs
+from paper_2009_10173_gb300.batch import Batch
+from paper_2009_10173_gb300.model import Model
+
+pytestmark = pytest.mark.gpu
+
+BASE = configs.scaled(configs.TINY_32, n_patches=400)
+JOBS = [
+    configs.scaled(BASE, px=24, py=20, nz=32, nt=192, win=11, lsqr_iters=6, fista_iters=5, power_iters=4,
+                   lambda_rel=1e-3, seed=11),
+    configs.scaled(BASE, px=40, py=33, nz=48, nt=192, win=9, focal_m=3.5e-3, aperture_m=2.5e-3, lsqr_iters=6,
+                   fista_iters=5, power_iters=4, lambda_rel=1e-3, seed=12),
+    configs.scaled(BASE, px=17, py=29, nz=40, nt=256, win=13, focal_m=5e-3, aperture_m=3.4e-3, lsqr_iters=6,
+                   fista_iters=5, power_iters=4, lambda_rel=1e-3, seed=13),
+]
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def signals_for(cfg, m):
+    H = inputs.phantom(cfg, cfg["seed"], count=4)
+    clean = m.forward(torch.from_numpy(H.astype(np.float32)).cuda()).cpu().numpy()
+    return torch.from_numpy(inputs.add_noise(clean, 20.0, cfg["seed"] + 10 ** 6).astype(np.float32)).cuda()
+
+
+def standalone(cfg, m, s):
+    x2, _ = m.lsqr(s, cfg["lsqr_iters"])
+    x1, _ = m.fista(s, cfg["fista_iters"], power_iters=cfg["power_iters"], lambda_rel=cfg["lambda_rel"])
+    torch.cuda.synchronize()
+    return x2.cpu().numpy(), x1.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", [B.OAM_PREC_FP32, B.OAM_PREC_BF16X3])
+def test_batch_graph_equals_standalone_runs(prec):
+    cfgs, sigs = [], []
+    for cfg in JOBS:
+        m = Model(cfg, precision=prec)
+        cfgs.append(dict(cfg, _model=m))
+        sigs.append(signals_for(cfg, m))
+    ref = [standalone(c, c["_model"], s) for c, s in zip(cfgs, sigs)]
+    batch = Batch(cfgs, sigs, autotune=(prec == B.OAM_PREC_BF16X3))
+    for _ in range(2):  # record, then replay the same graph
+        batch.run()
+        torch.cuda.synchronize()
+        for j, (x2, x1) in zip(batch.jobs, ref):
+            assert np.array_equal(j["x2"].cpu().numpy(), x2)
+            assert np.array_equal(j["x1"].cpu().numpy(), x1)
+    batch.close()
+
+
+def test_batch_job_matches_oracle():
+    cfg = dict(JOBS[0])
+    S = oracle.slab(cfg)
+    H = inputs.phantom(cfg, cfg["seed"], count=4)
+    s64 = inputs.add_noise(oracle.forward(S, H), 20.0, cfg["seed"] + 10 ** 6)
+    s32 = s64.astype(np.float32)
+    m = Model(cfg, precision=B.OAM_PREC_BF16X3)
+    batch = Batch([dict(cfg, _model=m)], [torch.from_numpy(s32).cuda()], autotune=False)
+    batch.run()
+    torch.cuda.synchronize()
+    A, AT = (lambda v: oracle.forward(S, v)), (lambda v: oracle.adjoint(S, v))
+    x2_ref, _ = solvers.lsqr(A, AT, s32.astype(np.float64), cfg["lsqr_iters"])
+    x1_ref, _ = solvers.mb_l1(A, AT, s32.astype(np.float64), cfg["fista_iters"], cfg["power_iters"],
+                              np.ones(m.vol_shape), lambda_rel=cfg["lambda_rel"], nonneg=True)
+    assert rel(batch.jobs[0]["x2"].cpu().numpy(), x2_ref) < 1e-3
+    assert rel(batch.jobs[0]["x1"].cpu().numpy(), x1_ref) < 1e-3
+    batch.close()
+
+
+def test_autotune_keeps_results():
+    cfg = JOBS[1]
+    m = Model(cfg, precision=B.OAM_PREC_BF16X3)
+    H = torch.from_numpy(inputs.gaussian(m.vol_shape, 5).astype(np.float32)).cuda()
+    before = m.forward(H).cpu().numpy()
+    f, a = B.oam_model_autotune(m.handle, 2)
+    assert f >= 2 and a >= 2
+    after = m.forward(H).cpu().numpy()
+    assert np.array_equal(before, after)
+    m.close()
+
+
+def _request(cfg):
+    m = Model(cfg, precision=B.OAM_PREC_BF16X3)
+    s = signals_for(cfg, m).cpu().pin_memory()
+    m.close()
+    return cfg, s
+
+
+def _serve(server, reqs):
+    outs = []
+    for cfg, s in reqs:
+        x2 = torch.empty((cfg["py"], cfg["px"], cfg["nz"]), dtype=torch.float32).pin_memory()
+        x1 = torch.empty_like(x2).pin_memory()
+        sn, g, e = B.structs_from_config(cfg)
+        rid = B.oam_server_submit(server, sn, g, e, s, x2, x1)
+        outs.append((rid, x2, x1))
+    for rid, _, _ in outs:
+        assert B.oam_server_wait(server, rid, 120.0) == B.OAM_OK
+    return outs
+
+
+def _server(budget=8 << 30, slots=3, iters=(6, 5, 4)):
+    opts = B.OamServerOpts(budget, slots, B.OAM_PREC_BF16X3, iters[0], iters[1], iters[2], 1e-3)
+    return B.oam_server_create(opts)
+
+
+def test_server_results_same_alone_and_in_the_mix():
+    reqs = [_request(c) for c in JOBS] + [_request(configs.scaled(JOBS[0], seed=21))]
+    alone = []
+    for r in reqs:
+        srv = _server(slots=1)
+        (rid, x2, x1), = _serve(srv, [r])
+        B.oam_server_stop(srv)
+        alone.append((x2.numpy().copy(), x1.numpy().copy()))
+    srv = _server(slots=3)
+    mixed = _serve(srv, reqs)
+    st = B.oam_server_stats(srv)
+    B.oam_server_stop(srv)
+    assert st.peak_running >= 2  # requests were on the GPU together
+    for (rid, x2, x1), (a2, a1) in zip(mixed, alone):
+        assert np.array_equal(x2.numpy(), a2)
+        assert np.array_equal(x1.numpy(), a1)
+
+
+def test_server_budget_failure_and_timeout():
+    reqs = [_request(JOBS[1]), _request(JOBS[2])]
+    # a budget that fits one request's reservation at a time
+    srv = _server(budget=1, slots=2)
+    sn, g, e = B.structs_from_config(JOBS[1])
+    x2 = torch.empty((JOBS[1]["py"], JOBS[1]["px"], JOBS[1]["nz"])).pin_memory()
+    rid = B.oam_server_submit(srv, sn, g, e, reqs[0][1], x2, None)
+    assert B.oam_server_wait(srv, rid, 60.0) == B.OAM_ERR_OOM  # can never fit the budget
+    B.oam_server_stop(srv)
+
+    need = max(B.oam_request_footprint(B.OAM_PREC_BF16X3, B.structs_from_config(c)[1]) for c, _ in reqs)
+    srv = _server(budget=int(need * 1.5), slots=2, iters=(40, 30, 10))
+    outs, bufs = [], []  # host outputs must outlive their requests
+    for cfg, s in reqs:
+        sn, g, e = B.structs_from_config(cfg)
+        bufs.append(torch.empty((cfg["py"], cfg["px"], cfg["nz"])).pin_memory())
+        outs.append(B.oam_server_submit(srv, sn, g, e, s, bufs[-1], None))
+    # the second request waits for memory: a short wait on it times out
+    assert B.oam_server_wait(srv, outs[1], 0.0) == B.OAM_ERR_TIMEOUT
+    # an invalid request fails without disturbing the others
+    bad = configs.scaled(JOBS[1], win=10)
+    sn, g, e = B.structs_from_config(bad)
+    rid_bad = B.oam_server_submit(srv, sn, g, e, reqs[0][1], None, None)
+    for rid in outs:
+        assert B.oam_server_wait(srv, rid, 120.0) == B.OAM_OK
+    assert B.oam_server_wait(srv, rid_bad, 60.0) == B.OAM_ERR_INVALID_ARG
+    st = B.oam_server_stats(srv)
+    B.oam_server_stop(srv)
+    assert st.peak_running == 1
+    assert st.peak_reserved_bytes <= int(need * 1.5)
