@@ -30,6 +30,11 @@ LSQR_ITERS, FISTA_ITERS, POWER_ITERS, LAMBDA_REL = 50, 100, 20, 1e-3
 # operator applications per step: LSQR 1 + 2*50; FISTA 2*20 power + 1 lambda + 2*100
 OPS_PER_STEP = (1 + 2 * LSQR_ITERS) + (2 * POWER_ITERS + 1 + 2 * FISTA_ITERS)
 FP32_LANES_PER_SM = 128
+# DRAM bytes per launch of the tensor-core operator kernel (k_corr_fold) on this
+# workload: dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of the
+# same kernel on a 96x96-position case of this workload (438.7 MB for 2945 blocks),
+# scaled by blocks processed (11160 / 2945).  Set to None when the kernel changes.
+TC_TRAFFIC_BYTES = 438.7e6 * 11160 / 2945
 
 
 def parse():
@@ -250,7 +255,8 @@ def run_ours(args, rank, world):
                  B.OAM_PREC_BF16X3: "split-BF16 (hi*hi+hi*lo+lo*hi) tcgen05 operators, FP32 accumulate"}[prec]
 
     # synthetic input for this rank: vessel tree + microspheres, clean signals by A, 20 dB noise
-    seed = 1 + rank
+    from paper_2009_10173_gb300 import replicas
+    seed = replicas.replica_seed(1, rank)
     H = inputs.phantom(cfg, seed, kind="vessels", count=50)
     m0 = make_model(B.OAM_PREC_FP32)
     clean = m0.forward(torch.from_numpy(H.astype(np.float32)).cuda()).cpu().numpy()
@@ -324,9 +330,7 @@ def run_ours(args, rank, world):
     e2e_ms = e0.elapsed_time(e1)
 
     if dist:
-        t = torch.tensor([elapsed_ms, e2e_ms], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        elapsed_ms, e2e_ms = t.tolist()
+        elapsed_ms, e2e_ms = replicas.max_over_ranks([elapsed_ms, e2e_ms], device="cuda")
     if rank != 0:
         return
 
@@ -352,8 +356,10 @@ def run_ours(args, rank, world):
                 "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:g} MHz"}
     else:
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "tensor", "kernel": f"{dom} (tcgen05 split-BF16)", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+        roof = {"bound": "tensor", "kernel": f"{dom} (tcgen05 split-BF16, mirror-folded)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": TC_TRAFFIC_BYTES,
+                "executed_tflops": (info.exec_flops_adjoint if dom == "adjoint" else info.exec_flops_forward) /
+                                   (dom_ms * 1e-3) / 1e12,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
     line = {"metric": METRIC, "value": value, "unit": "volumes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
