@@ -17,10 +17,11 @@
 //   F[pos][k] = X[pos + (b, a)] + X[pos + (b, -a)] + X[pos + (-b, a)] + X[pos + (-b, -a)]
 // (duplicates dropped when a or b is 0).  One block handles one 128-position
 // tile and one |b|; it stages the FP32 rows y+b and y-b (TMA, 128-byte
-// swizzle) and adds them once per stage, eight warps build F from two shifted
-// rows of that sum, split it into BF16 hi/lo in tensor memory, and one thread
-// issues the MMAs with A read from tensor memory.  This cuts the MMA count by ~4 for a 61x61
-// window.
+// swizzle) and adds them once per stage, sixteen warps build F from two shifted
+// rows of that sum (8 of the stage's 32 K elements each), split it into BF16
+// hi/lo in tensor memory, and one warp walks the items while an elected lane
+// issues the MMAs with A read from tensor memory.  This cuts the MMA count by
+// ~4 for a 61x61 window.
 //
 // Positions use a padded flat index q = y*Wp + x with Wp = px + R, so a lateral
 // offset a is a shift by a rows of a staged strip of 128 + 2R rows.  Padding
@@ -47,7 +48,7 @@ namespace oam {
 
 constexpr int kStageK = 32;        // K elements per stage (two 16-deep MMA chunks)
 constexpr int kTileM = 128;        // positions per block
-constexpr int kFoldWarps = 8;      // warps that build the folded operand (then run the epilogue)
+constexpr int kFoldWarps = 16;     // warps that build the folded operand (then run the epilogue)
 constexpr int kThreads = 64 + 32 * kFoldWarps;
 constexpr int kMaxItems = 8;       // item ring depth (slab tile + folded operand)
 constexpr int kFoldCols = 32;      // tensor-memory columns per folded operand: 2 chunks x (hi, lo) x 8
@@ -120,12 +121,12 @@ __device__ __forceinline__ bool row_live(const CorrParams &p, int tile, int off)
 }
 
 // Add one staged FP32 row (128-byte rows, 128-byte TMA swizzle: 16-byte chunk c
-// of row r sits at chunk c ^ (r & 7)) for the 16 elements of half h.
-__device__ __forceinline__ void add_row(const float *strip, int row, int h, float (&acc)[16]) {
+// of row r sits at chunk c ^ (r & 7)) for the 8 elements of quarter q.
+__device__ __forceinline__ void add_row(const float *strip, int row, int q, float (&acc)[8]) {
   const float4 *r4 = reinterpret_cast<const float4 *>(strip + row * 32);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float4 v = r4[(4 * h + i) ^ (row & 7)];
+  for (int i = 0; i < 2; ++i) {
+    const float4 v = r4[(2 * q + i) ^ (row & 7)];
     acc[4 * i + 0] += v.x;
     acc[4 * i + 1] += v.y;
     acc[4 * i + 2] += v.z;
@@ -246,62 +247,65 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      bool ok = ptx::mbar_wait(acc_ready, 0, abort_flag, p.budget);
-      if (!ok) fail(4);
-      ptx::tc_fence_after();
-      int k = 0;
-      uint32_t lap = 0;
-      // B descriptor template (start-address field in 16-byte units; fields never carry)
-      const uint64_t slot_desc = ptx::smem_desc(ptx::smem_addr(slots), 0, 128);
-      const uint32_t idesc_m128 = ptx::idesc_bf16_f32(kTileM, 0);
-      for (int st = 0; st < p.stages && ok && !skip; ++st) {
-        const TcItem *row_items = sitems + st * NA;
-        for (int a = 0; a < NA; ++a) {
-          if (!ptx::mbar_wait(&slab_full[k], lap, abort_flag, p.budget)) {
-            fail(8);
-            ok = false;
-            break;
-          }
-          if (!ptx::mbar_wait(&fold_full[k], lap, abort_flag, p.budget)) {
-            fail(16);
-            ok = false;
-            break;
-          }
-          ptx::tc_fence_after();
-          const TcItem item = row_items[a];
-          const uint32_t a_base = tmem + (uint32_t)(p.fold_col0 + 32 * k);
-          uint64_t dB = slot_desc + (uint64_t)(((uint32_t)k * (uint32_t)p.slot_bytes) >> 4);
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const uint32_t n = item.n[c];
-            if (n == 0) continue;
-            const uint32_t a_hi = a_base + 16u * c, a_lo = a_hi + 8u;
-            const uint64_t dbh = dB + ((uint64_t)n << 16);  // lbo = 16 n bytes
-            const uint64_t dbl = dbh + 2u * n;              // lo tile 32 n bytes later
-            const uint32_t idesc = idesc_m128 | ((n >> 3) << 17);
-            const uint32_t d = tmem + item.col[c];
-            ptx::mma_bf16_ta(d, a_hi, dbh, idesc, 1);
-            ptx::mma_bf16_ta(d, a_hi, dbl, idesc, 1);
-            ptx::mma_bf16_ta(d, a_lo, dbh, idesc, 1);
-            dB += 4u * n;  // next tile 64 n bytes later
-          }
+    // The whole warp walks the item ring, so every MMA operand is computed
+    // warp-uniformly; one elected lane issues the MMAs and commits.  (A loop
+    // run by a single lane issues at about half the rate.)
+    bool ok = __all_sync(0xffffffffu, ptx::mbar_wait(acc_ready, 0, abort_flag, p.budget));
+    if (!ok && lane == 0) fail(4);
+    ptx::tc_fence_after();
+    const bool leader = ptx::elect_one();
+    int k = 0;
+    uint32_t lap = 0;
+    // B descriptor template (start-address field in 16-byte units; fields never carry)
+    const uint64_t slot_desc = ptx::smem_desc(ptx::smem_addr(slots), 0, 128);
+    const uint32_t idesc_m128 = ptx::idesc_bf16_f32(kTileM, 0);
+    for (int st = 0; st < p.stages && ok && !skip; ++st) {
+      const TcItem *row_items = sitems + st * NA;
+      for (int a = 0; a < NA; ++a) {
+        bool w = ptx::mbar_wait(&slab_full[k], lap, abort_flag, p.budget);
+        if (w) w = ptx::mbar_wait(&fold_full[k], lap, abort_flag, p.budget);
+        if (!__all_sync(0xffffffffu, w)) {
+          if (lane == 0) fail(8);
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const TcItem item = row_items[a];
+        const uint32_t a_base = tmem + (uint32_t)(p.fold_col0 + 32 * k);
+        const uint64_t dB = slot_desc + (uint64_t)(((uint32_t)k * (uint32_t)p.slot_bytes) >> 4);
+        const uint32_t n0 = item.n[0], n1 = item.n[1];
+        const uint64_t b0h = dB + ((uint64_t)n0 << 16), b0l = b0h + 2u * n0;  // lbo = 16 n bytes; lo 32 n bytes on
+        const uint64_t dB1 = dB + 4u * n0;                                   // second tile 64 n0 bytes later
+        const uint64_t b1h = dB1 + ((uint64_t)n1 << 16), b1l = b1h + 2u * n1;
+        const uint32_t i0 = idesc_m128 | ((n0 >> 3) << 17), i1 = idesc_m128 | ((n1 >> 3) << 17);
+        const uint32_t d0 = tmem + item.col[0], d1 = tmem + item.col[1];
+        if (leader) {
+          // the two chunks accumulate into different columns: interleave them
+          if (n0) ptx::mma_bf16_ta(d0, a_base, b0h, i0, 1);
+          if (n1) ptx::mma_bf16_ta(d1, a_base + 16u, b1h, i1, 1);
+          if (n0) ptx::mma_bf16_ta(d0, a_base + 8u, b0h, i0, 1);
+          if (n1) ptx::mma_bf16_ta(d1, a_base + 24u, b1h, i1, 1);
+          if (n0) ptx::mma_bf16_ta(d0, a_base, b0l, i0, 1);
+          if (n1) ptx::mma_bf16_ta(d1, a_base + 16u, b1l, i1, 1);
           ptx::mma_commit(&item_empty[k]);
-          if (++k == K) {
-            k = 0;
-            lap ^= 1;
-          }
+        }
+        __syncwarp();
+        if (++k == K) {
+          k = 0;
+          lap ^= 1;
         }
       }
-      ptx::mma_commit(acc_full);
     }
+    if (leader) ptx::mma_commit(acc_full);
+    __syncwarp();
   } else {
     // ------------------------------------------------------------ fold warps, then epilogue
     const int fw = warp - 2;        // 0 .. kFoldWarps-1
     const int quarter = warp & 3;   // tensor-memory lanes 32*quarter .. +31
+    const int kq = fw >> 2;         // 8-deep quarter of the 32-deep stage this warp folds
     const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
     const int nb = (p.acc_cols + 31) / 32;  // 32-column blocks of the accumulator
-    const int blk_begin = fw < 4 ? 0 : nb / 2, blk_end = fw < 4 ? nb / 2 : nb;
+    const int blk_begin = kq * nb / 4, blk_end = (kq + 1) * nb / 4;
     for (int j = blk_begin; j < blk_end; ++j) ptx::tmem_st32_zero(tmem + lane_base + (uint32_t)(32 * j));
     ptx::tmem_wait_st();
     ptx::tc_fence_before();
@@ -311,7 +315,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     if (!skip) {
       const int m = 32 * quarter + lane;  // row (tensor-memory lane) this thread folds
-      const int h = fw >> 2;              // 16-element half of the stage = MMA chunk
+      // elements 8 kq .. 8 kq + 7 of the stage: MMA chunk kq / 2, half kq % 2 of its 16 K
+      const uint32_t fold_off = (uint32_t)(16 * (kq >> 1) + 4 * (kq & 1));
       int it_strip = 0, k = 0;
       uint32_t lap = 0;
       for (int st = 0; st < p.stages && ok; ++st) {
@@ -346,23 +351,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) fail(64);
             break;
           }
-          float acc[16];
+          float acc[8];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) acc[i] = 0.0f;
-          add_row(X1, m + R + a, h, acc);
-          if (a > 0) add_row(X1, m + R - a, h, acc);
-          uint32_t hv[8], lv[8];
+          for (int i = 0; i < 8; ++i) acc[i] = 0.0f;
+          add_row(X1, m + R + a, kq, acc);
+          if (a > 0) add_row(X1, m + R - a, kq, acc);
+          uint32_t hv[4], lv[4];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
+          for (int e = 0; e < 4; ++e) {
             const __nv_bfloat162 h2 = __floats2bfloat162_rn(acc[2 * e], acc[2 * e + 1]);
             const float2 hf = __bfloat1622float2(h2);
             const __nv_bfloat162 l2 = __floats2bfloat162_rn(acc[2 * e] - hf.x, acc[2 * e + 1] - hf.y);
             hv[e] = *reinterpret_cast<const uint32_t *>(&h2);
             lv[e] = *reinterpret_cast<const uint32_t *>(&l2);
           }
-          const uint32_t fa = tmem + lane_base + (uint32_t)(p.fold_col0 + 32 * k + 16 * h);
-          ptx::tmem_st8(fa, hv);
-          ptx::tmem_st8(fa + 8u, lv);
+          const uint32_t fa = tmem + lane_base + (uint32_t)(p.fold_col0 + 32 * k) + fold_off;
+          ptx::tmem_st4(fa, hv);
+          ptx::tmem_st4(fa + 8u, lv);
           ptx::tmem_wait_st();
           ptx::tc_fence_before();
           __syncwarp();
