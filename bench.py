@@ -32,9 +32,9 @@ OPS_PER_STEP = (1 + 2 * LSQR_ITERS) + (2 * POWER_ITERS + 1 + 2 * FISTA_ITERS)
 FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the tensor-core operator kernel (k_corr_fold) on this
 # workload: dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of the
-# same kernel on a 96x96-position case of this workload (438.7 MB for 2945 blocks),
+# same kernel on a 96x96-position case of this workload (441.3 MB for 2945 blocks),
 # scaled by blocks processed (11160 / 2945).  Set to None when the kernel changes.
-TC_TRAFFIC_BYTES = 438.7e6 * 11160 / 2945
+TC_TRAFFIC_BYTES = 441.3e6 * 11160 / 2945
 
 
 def parse():

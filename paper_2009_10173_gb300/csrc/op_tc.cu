@@ -109,10 +109,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
       : "memory");
 }
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 // Does row offset `off` put any of the tile's rows inside the grid?
 __device__ __forceinline__ bool row_live(const CorrParams &p, int tile, int off) {
   const int q0 = tile * kTileM;
@@ -120,8 +116,21 @@ __device__ __forceinline__ bool row_live(const CorrParams &p, int tile, int off)
   return !(y_last + off < 0 || y_first + off >= p.py);
 }
 
-// Add one staged FP32 row (128-byte rows, 128-byte TMA swizzle: 16-byte chunk c
-// of row r sits at chunk c ^ (r & 7)) for the 8 elements of quarter q.
+// Staged FP32 rows are 128 bytes with the TMA's 128-byte swizzle: 16-byte
+// chunk c of row r sits at chunk c ^ (r & 7).  Read the 8 elements of quarter q.
+__device__ __forceinline__ void load_row(const float *strip, int row, int q, float (&v)[8]) {
+  const float4 *r4 = reinterpret_cast<const float4 *>(strip + row * 32);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float4 u = r4[(2 * q + i) ^ (row & 7)];
+    v[4 * i + 0] = u.x;
+    v[4 * i + 1] = u.y;
+    v[4 * i + 2] = u.z;
+    v[4 * i + 3] = u.w;
+  }
+}
+
+// Add the 8 elements of quarter q of a staged row.
 __device__ __forceinline__ void add_row(const float *strip, int row, int q, float (&acc)[8]) {
   const float4 *r4 = reinterpret_cast<const float4 *>(strip + row * 32);
 #pragma unroll
@@ -176,9 +185,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     *never = 0;
     ptx::mbar_fence_init();
   }
-  if (warp == 0 && !skip) {
+  if (!skip) {  // this |b|'s item table, loaded by every thread in one pass
     const int n = p.stages * NA;
-    for (int i = lane; i < n; i += 32) {
+    for (int i = threadIdx.x; i < n; i += kThreads) {
       const int st = i / NA, a = i % NA;
       sitems[i] = p.items[p.tap_orbit[(b + R) * p.W + (a + R)] * p.stages + st];
     }
@@ -352,9 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           float acc[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) acc[i] = 0.0f;
-          add_row(X1, m + R + a, kq, acc);
+          load_row(X1, m + R + a, kq, acc);
           if (a > 0) add_row(X1, m + R - a, kq, acc);
           uint32_t hv[4], lv[4];
 #pragma unroll
