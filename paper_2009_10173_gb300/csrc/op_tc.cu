@@ -116,30 +116,65 @@ __device__ __forceinline__ bool row_live(const CorrParams &p, int tile, int off)
   return !(y_last + off < 0 || y_first + off >= p.py);
 }
 
+// Packed FP32 pairs (two lanes of one 64-bit register) and their arithmetic.
+__device__ __forceinline__ uint64_t add_f32x2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t sub_f32x2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t pack_f32x2(float x, float y) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ void unpack_f32x2(uint64_t v, float &x, float &y) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+}
+
 // Staged FP32 rows are 128 bytes with the TMA's 128-byte swizzle: 16-byte
-// chunk c of row r sits at chunk c ^ (r & 7).  Read the 8 elements of quarter q.
-__device__ __forceinline__ void load_row(const float *strip, int row, int q, float (&v)[8]) {
-  const float4 *r4 = reinterpret_cast<const float4 *>(strip + row * 32);
+// chunk c of row r sits at chunk c ^ (r & 7).  Read the 8 elements of
+// quarter q as four FP32 pairs.
+__device__ __forceinline__ void load_row(const float *strip, int row, int q, uint64_t (&v)[4]) {
+  const ulonglong2 *r2 = reinterpret_cast<const ulonglong2 *>(strip + row * 32);
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const float4 u = r4[(2 * q + i) ^ (row & 7)];
-    v[4 * i + 0] = u.x;
-    v[4 * i + 1] = u.y;
-    v[4 * i + 2] = u.z;
-    v[4 * i + 3] = u.w;
+    const ulonglong2 u = r2[(2 * q + i) ^ (row & 7)];
+    v[2 * i] = u.x;
+    v[2 * i + 1] = u.y;
   }
 }
 
 // Add the 8 elements of quarter q of a staged row.
-__device__ __forceinline__ void add_row(const float *strip, int row, int q, float (&acc)[8]) {
-  const float4 *r4 = reinterpret_cast<const float4 *>(strip + row * 32);
+__device__ __forceinline__ void add_row(const float *strip, int row, int q, uint64_t (&v)[4]) {
+  const ulonglong2 *r2 = reinterpret_cast<const ulonglong2 *>(strip + row * 32);
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const float4 v = r4[(2 * q + i) ^ (row & 7)];
-    acc[4 * i + 0] += v.x;
-    acc[4 * i + 1] += v.y;
-    acc[4 * i + 2] += v.z;
-    acc[4 * i + 3] += v.w;
+    const ulonglong2 u = r2[(2 * q + i) ^ (row & 7)];
+    v[2 * i] = add_f32x2(v[2 * i], u.x);
+    v[2 * i + 1] = add_f32x2(v[2 * i + 1], u.y);
+  }
+}
+
+// Split four FP32 pairs into BF16 pairs hi = bf16(v) and lo = bf16(v - hi),
+// both rounded to nearest even; element 2e in the low half of word e.
+__device__ __forceinline__ void split_bf16(const uint64_t (&v)[4], uint32_t (&hv)[4], uint32_t (&lv)[4]) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float x, y;
+    unpack_f32x2(v[e], x, y);
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(x, y);
+    const uint32_t hb = *reinterpret_cast<const uint32_t *>(&h2);
+    const uint64_t lo = sub_f32x2(v[e], pack_f32x2(__uint_as_float(hb << 16), __uint_as_float(hb & 0xffff0000u)));
+    float lx, ly;
+    unpack_f32x2(lo, lx, ly);
+    const __nv_bfloat162 l2 = __floats2bfloat162_rn(lx, ly);
+    hv[e] = hb;
+    lv[e] = *reinterpret_cast<const uint32_t *>(&l2);
   }
 }
 
@@ -353,35 +388,53 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           asm volatile("bar.sync 1, %0;" ::"r"(32 * kFoldWarps) : "memory");  // fold warps only
         }
-        for (int a = 0; a < NA; ++a) {
+        // two items (a, a + 1) per pass: one wait, fence and barrier step for both
+        for (int a = 0; a < NA; a += 2) {
+          const bool two = a + 1 < NA;
+          const bool wrap = k + 1 == p.n_items;
+          const int k1 = wrap ? 0 : k + 1;
+          const uint32_t lap1 = wrap ? lap ^ 1 : lap;
           ok = ptx::mbar_wait(&item_empty[k], lap ^ 1, abort_flag, p.budget);
+          if (ok && two) ok = ptx::mbar_wait(&item_empty[k1], lap1 ^ 1, abort_flag, p.budget);
           ok = __all_sync(0xffffffffu, ok);
           if (!ok) {
             if (lane == 0) fail(64);
             break;
           }
-          float acc[8];
-          load_row(X1, m + R + a, kq, acc);
-          if (a > 0) add_row(X1, m + R - a, kq, acc);
-          uint32_t hv[4], lv[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn(acc[2 * e], acc[2 * e + 1]);
-            const float2 hf = __bfloat1622float2(h2);
-            const __nv_bfloat162 l2 = __floats2bfloat162_rn(acc[2 * e] - hf.x, acc[2 * e + 1] - hf.y);
-            hv[e] = *reinterpret_cast<const uint32_t *>(&h2);
-            lv[e] = *reinterpret_cast<const uint32_t *>(&l2);
+          uint32_t hv0[4], lv0[4], hv1[4], lv1[4];
+          {
+            uint64_t f0[4], f1[4];
+            load_row(X1, m + R + a, kq, f0);
+            if (a > 0) add_row(X1, m + R - a, kq, f0);
+            if (two) {
+              load_row(X1, m + R + a + 1, kq, f1);
+              add_row(X1, m + R - a - 1, kq, f1);
+            }
+            split_bf16(f0, hv0, lv0);
+            if (two) split_bf16(f1, hv1, lv1);
           }
-          const uint32_t fa = tmem + lane_base + (uint32_t)(p.fold_col0 + 32 * k) + fold_off;
-          ptx::tmem_st4(fa, hv);
-          ptx::tmem_st4(fa + 8u, lv);
+          const uint32_t fa0 = tmem + lane_base + (uint32_t)(p.fold_col0 + 32 * k) + fold_off;
+          ptx::tmem_st4(fa0, hv0);
+          ptx::tmem_st4(fa0 + 8u, lv0);
+          if (two) {
+            const uint32_t fa1 = tmem + lane_base + (uint32_t)(p.fold_col0 + 32 * k1) + fold_off;
+            ptx::tmem_st4(fa1, hv1);
+            ptx::tmem_st4(fa1 + 8u, lv1);
+          }
           ptx::tmem_wait_st();
           ptx::tc_fence_before();
           __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&fold_full[k]);
-          if (++k == p.n_items) {
-            k = 0;
-            lap ^= 1;
+          if (lane == 0) {
+            ptx::mbar_arrive(&fold_full[k]);
+            if (two) ptx::mbar_arrive(&fold_full[k1]);
+          }
+          if (two) {
+            const bool wrap1 = k1 + 1 == p.n_items;
+            k = wrap1 ? 0 : k1 + 1;
+            lap = wrap1 ? lap1 ^ 1 : lap1;
+          } else {
+            k = k1;
+            lap = lap1;
           }
         }
         __syncwarp();
