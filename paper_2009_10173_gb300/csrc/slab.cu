@@ -4,7 +4,8 @@
 // Distances use the cancellation-free form d - F = (2F r.n + |r|^2) / (d + F)
 // in FP64, so the arrival sample fs*(d/c - t0) = (fs/c)(d - F) + fs(F/c - t0)
 // keeps full precision; the EIR derivative is evaluated in FP32 at
-// tau = n - D_j (|tau| <= trunc_sigma * sigma_s) and summed in FP64.
+// tau = n - D_j (|tau| <= trunc_sigma * sigma_s), tau being the FP32 rounding
+// of the exact offset, and summed over patches with a compensated FP32 sum.
 #include <algorithm>
 #include <cmath>
 
@@ -62,43 +63,56 @@ __global__ void k_delta_range(Geo g, const Patch *__restrict__ patch, int M, con
 constexpr int kPatchChunk = 512;
 
 // Band values: thread i of block (o, k) owns sample lo + i (+ blockDim.x ...).
-// Patches are visited in index order, so every entry is a fixed-order sum.
+// Each patch's arrival d (samples, FP64) is split into an integer part and an
+// FP32 fraction, so tau = (n - floor d) - frac(d) is the FP32 rounding of the
+// exact offset; the EIR derivative is evaluated in FP32 and the patch sum is a
+// compensated (Kahan) FP32 sum.  Patches are visited in index order, so every
+// entry is a fixed-order sum.
 __global__ void k_slab_values(Geo g, const Patch *__restrict__ patch, int M, const int *orb_b,
                               const int *orb_a, int nz, const int *band_lo, const int *band_hi,
                               int band_w, float *band) {
   const int o = blockIdx.x, k = blockIdx.y;
   const int b = orb_b[o], a = orb_a[o];
   const int lo = band_lo[o * nz + k], hi = band_hi[o * nz + k];
-  __shared__ double sD[kPatchChunk];
+  __shared__ float sI[kPatchChunk];  // floor(d), exact
+  __shared__ float sF[kPatchChunk];  // d - floor(d) in [0, 1)
   __shared__ float sW[kPatchChunk];
   const int per = (band_w + blockDim.x - 1) / blockDim.x;  // samples per thread (<= 4)
-  double acc[4] = {0, 0, 0, 0};
+  const float cut = (float)g.cut;
+  float sum[4] = {0, 0, 0, 0}, comp[4] = {0, 0, 0, 0};
   for (int j0 = 0; j0 < M; j0 += kPatchChunk) {
     const int cnt = min(kPatchChunk, M - j0);
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       Patch p = patch[j0 + j];
       double dd = delta_dist(g, b, a, k, p);
-      sD[j] = __dadd_rn(__dmul_rn(g.ks, dd), g.G);
+      const double d = __dadd_rn(__dmul_rn(g.ks, dd), g.G);
+      const double di = floor(d);
+      sI[j] = (float)di;
+      sF[j] = (float)(d - di);
       sW[j] = (float)(p.w / ((g.F + dd) * 1e3));  // mm^2 / mm
     }
     __syncthreads();
     for (int r = 0; r < per; ++r) {
       const int n = lo + threadIdx.x + r * blockDim.x;
       if (n >= hi) break;
-      double s = acc[r];
+      const float nf = (float)n;
+      float s = sum[r], c = comp[r];
       for (int j = 0; j < cnt; ++j) {
-        double t = (double)n - sD[j];
-        if (fabs(t) <= g.cut) {
-          float tau = (float)t;
+        const float tau = (nf - sI[j]) - sF[j];
+        if (fabsf(tau) <= cut) {
           float sn, cs;
           sincosf(g.omega * tau, &sn, &cs);
-          float env = expf(-tau * tau * g.inv2s2);
-          float v = -env * (tau * g.invs2 * cs + g.omega * sn);
-          s += (double)(sW[j] * v);
+          const float env = expf(-tau * tau * g.inv2s2);
+          const float v = -env * (tau * g.invs2 * cs + g.omega * sn);
+          const float y = sW[j] * v - c;
+          const float t = s + y;
+          c = (t - s) - y;
+          s = t;
         }
       }
-      acc[r] = s;
+      sum[r] = s;
+      comp[r] = c;
     }
   }
   float *row = band + ((size_t)o * nz + k) * band_w;
@@ -106,7 +120,7 @@ __global__ void k_slab_values(Geo g, const Patch *__restrict__ patch, int M, con
     const int i = threadIdx.x + r * blockDim.x;
     if (i >= band_w) break;
     const int n = lo + i;
-    row[i] = (n < hi) ? (float)acc[r] : 0.0f;
+    row[i] = (n < hi) ? sum[r] - comp[r] : 0.0f;
   }
 }
 
