@@ -10,6 +10,10 @@ benchmark's CPU-baseline leg import this package; the product path
 * ``forward`` / ``adjoint``: A and its transpose as lateral correlations of
   the slab with the volume (Methods, Efficient reconstruction based on
   scanning symmetries).
+* ``forward_fft`` / ``adjoint_fft``: the same operators restated exactly
+  through the 2-D correlation theorem over the zero-padded scan grid, with a
+  project-written radix-2 FFT (``fft``); ``slab_dft`` is the transform of one
+  slab slice.
 * ``oracle.solvers``: LSQR for Eq. 5 with Eq. 6 (MB-L2) and FISTA for Eq. 5
   with Eq. 7 (MB-L1), written from the published algorithms the paper names.
 """
@@ -56,9 +60,14 @@ def lib():
         L.orc_forward.argtypes = [dp, i32, i32, i32, i32, i32, dp, dp]
         L.orc_adjoint.argtypes = [dp, i32, i32, i32, i32, i32, dp, dp]
         L.orc_forward_at.argtypes = [dp, i32, i32, i32, i32, dp, i32, ip, ip, ip, dp]
+        L.orc_fft.argtypes = [dp, dp, i32, i32]
+        L.orc_slab_dft.argtypes = [dp, i32, i32, i32, i32, i32, i32, dp, dp]
+        L.orc_forward_fft.argtypes = [dp, i32, i32, i32, i32, i32, i32, dp, dp]
+        L.orc_adjoint_fft.argtypes = [dp, i32, i32, i32, i32, i32, i32, dp, dp]
         for f in ("orc_patch_count_rings", "orc_patches", "orc_distance_range", "orc_t0",
                   "orc_slab_column", "orc_slab", "orc_slab_time_slice", "orc_forward",
-                  "orc_adjoint", "orc_forward_at"):
+                  "orc_adjoint", "orc_forward_at", "orc_fft", "orc_slab_dft", "orc_forward_fft",
+                  "orc_adjoint_fft"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -191,3 +200,55 @@ def forward_at(slices, H, ys, xs, which):
     out = np.zeros(len(ys))
     _check(lib().orc_forward_at(slices, win, nz, py, px, H, len(ys), ys, xs, which, out))
     return out
+
+
+def fft_size(py, px, win):
+    """Smallest power of two P with P >= max(py, px) + R: no circular wrap of
+    the zero-padded correlation reaches the output window."""
+    need = max(py, px) + (win - 1) // 2
+    P = 1
+    while P < need:
+        P *= 2
+    return P
+
+
+def fft(x, inverse=False):
+    """Unscaled radix-2 DFT of a complex vector (length a power of two):
+    X[f] = sum_j x[j] exp(-+2 pi i j f / n), sign + for ``inverse``."""
+    x = np.asarray(x, np.complex128)
+    re, im = np.ascontiguousarray(x.real), np.ascontiguousarray(x.imag)
+    _check(lib().orc_fft(re, im, len(x), 1 if inverse else -1))
+    return re + 1j * im
+
+
+def slab_dft(S, k, n, P):
+    """2-D DFT of the slab slice S[:, :, k, n] placed at (b mod P, a mod P)."""
+    S = np.ascontiguousarray(S, np.float64)
+    win, _, nz, nt = S.shape
+    re, im = np.zeros((P, P)), np.zeros((P, P))
+    _check(lib().orc_slab_dft(S, win, nz, nt, k, n, P, re, im))
+    return re + 1j * im
+
+
+def forward_fft(S, H, P=None):
+    """A H through the lateral correlation theorem (exact restatement)."""
+    S = np.ascontiguousarray(S, np.float64)
+    H = np.ascontiguousarray(H, np.float64)
+    win, _, nz, nt = S.shape
+    py, px, _ = H.shape
+    P = fft_size(py, px, win) if P is None else P
+    s = np.zeros((py, px, nt))
+    _check(lib().orc_forward_fft(S, win, nz, nt, py, px, P, H, s))
+    return s
+
+
+def adjoint_fft(S, s, P=None):
+    """A^T s through the lateral correlation theorem (exact restatement)."""
+    S = np.ascontiguousarray(S, np.float64)
+    s = np.ascontiguousarray(s, np.float64)
+    win, _, nz, nt = S.shape
+    py, px, _ = s.shape
+    P = fft_size(py, px, win) if P is None else P
+    H = np.zeros((py, px, nz))
+    _check(lib().orc_adjoint_fft(S, win, nz, nt, py, px, P, s, H))
+    return H

@@ -374,3 +374,169 @@ int orc_forward_at(const double *slices, int win, int nz, int py, int px, const 
   }
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Exact lateral-FFT restatement of A and A^T.                              */
+/* Both operators are 2-D correlations over the scan grid, so with the      */
+/* volume and the signals zero-padded to P x P (P >= max(py, px) + R, so    */
+/* that no circular wrap reaches the output window) the correlation theorem */
+/* gives, per depth k and sample n,                                         */
+/*   A:    s^_n(v,u)  = sum_k conj(S^_{k,n}(v,u)) H^_k(v,u)                 */
+/*   A^T:  H^_k(v,u)  = sum_n      S^_{k,n}(v,u)  s^_n(v,u)                 */
+/* where X^ is the 2-D DFT over (y, x) (textbook Cooley-Tukey radix-2 below) */
+/* and S_{k,n} holds S[b][a][k][n] at (b mod P, a mod P).                   */
+/* ------------------------------------------------------------------------ */
+
+static int is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+/* In-place radix-2 decimation-in-time FFT of n complex values spaced by
+ * `stride`: X[f] = sum_j x[j] exp(sign * 2 pi i j f / n), unscaled. */
+static void fft1(double *re, double *im, int n, int stride, int sign) {
+  for (int i = 1, j = 0; i < n; ++i) { /* bit-reversal permutation */
+    int bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) {
+      double t = re[(size_t)i * stride]; re[(size_t)i * stride] = re[(size_t)j * stride]; re[(size_t)j * stride] = t;
+      t = im[(size_t)i * stride]; im[(size_t)i * stride] = im[(size_t)j * stride]; im[(size_t)j * stride] = t;
+    }
+  }
+  for (int len = 2; len <= n; len <<= 1) {
+    const int half = len >> 1;
+    for (int q = 0; q < half; ++q) {
+      const double ang = sign * 2.0 * M_PI * (double)q / (double)len;
+      const double wr = cos(ang), wi = sin(ang);
+      for (int s0 = 0; s0 < n; s0 += len) {
+        const size_t i0 = (size_t)(s0 + q) * stride, i1 = (size_t)(s0 + q + half) * stride;
+        const double xr = re[i1] * wr - im[i1] * wi, xi = re[i1] * wi + im[i1] * wr;
+        re[i1] = re[i0] - xr; im[i1] = im[i0] - xi;
+        re[i0] += xr; im[i0] += xi;
+      }
+    }
+  }
+}
+
+/* 2-D transform of a P x P row-major array (rows then columns). */
+static void fft2(double *re, double *im, int P, int sign) {
+  for (int r = 0; r < P; ++r) fft1(re + (size_t)r * P, im + (size_t)r * P, P, 1, sign);
+  for (int c = 0; c < P; ++c) fft1(re + c, im + c, P, P, sign);
+}
+
+/* Exposed for the tests: one 1-D transform of n values (n a power of two). */
+int orc_fft(double *re, double *im, int n, int sign) {
+  if (!is_pow2(n) || (sign != 1 && sign != -1)) return ORC_EINVAL;
+  fft1(re, im, n, 1, sign);
+  return ORC_OK;
+}
+
+/* The 2-D DFT of one slab slice S[.][.][k][n] placed at (b mod P, a mod P). */
+int orc_slab_dft(const double *S, int win, int nz, int nt, int k, int n, int P, double *re, double *im) {
+  const int R = (win - 1) / 2;
+  if (!is_pow2(P) || P < win) return ORC_EINVAL;
+  memset(re, 0, sizeof(double) * P * P);
+  memset(im, 0, sizeof(double) * P * P);
+  for (int b = -R; b <= R; ++b)
+    for (int a = -R; a <= R; ++a)
+      re[(size_t)((b + P) % P) * P + (a + P) % P] = S[(((size_t)(b + R) * win + (a + R)) * nz + k) * nt + n];
+  fft2(re, im, P, -1);
+  return ORC_OK;
+}
+
+static int fft_pad_ok(int P, int R, int py, int px) {
+  return is_pow2(P) && P >= py + R && P >= px + R;
+}
+
+/* Does any tap of slab column (k, n) differ from zero? */
+static int slice_nonzero(const double *S, int win, int nz, int nt, int k, int n) {
+  for (int t = 0; t < win * win; ++t)
+    if (S[((size_t)t * nz + k) * nt + n] != 0.0) return 1;
+  return 0;
+}
+
+int orc_forward_fft(const double *S, int win, int nz, int nt, int py, int px, int P, const double *H, double *s) {
+  const int R = (win - 1) / 2;
+  const size_t PP = (size_t)P * P;
+  if (!fft_pad_ok(P, R, py, px)) return ORC_EINVAL;
+  double *Hr = calloc(PP * nz, sizeof(double)), *Hi = calloc(PP * nz, sizeof(double));
+  if (!Hr || !Hi) { free(Hr); free(Hi); return ORC_ENOMEM; }
+  for (int k = 0; k < nz; ++k) {
+    for (int y = 0; y < py; ++y)
+      for (int x = 0; x < px; ++x) Hr[k * PP + (size_t)y * P + x] = H[((size_t)y * px + x) * nz + k];
+    fft2(Hr + k * PP, Hi + k * PP, P, -1);
+  }
+  int rc = ORC_OK;
+#pragma omp parallel
+  {
+    double *sr = malloc(sizeof(double) * PP), *si = malloc(sizeof(double) * PP);
+    double *tr = malloc(sizeof(double) * PP), *ti = malloc(sizeof(double) * PP);
+    if (!sr || !si || !tr || !ti) {
+#pragma omp atomic write
+      rc = ORC_ENOMEM;
+    } else {
+#pragma omp for schedule(dynamic)
+      for (int n = 0; n < nt; ++n) {
+        memset(sr, 0, sizeof(double) * PP);
+        memset(si, 0, sizeof(double) * PP);
+        for (int k = 0; k < nz; ++k) {
+          if (!slice_nonzero(S, win, nz, nt, k, n)) continue;
+          orc_slab_dft(S, win, nz, nt, k, n, P, tr, ti);
+          const double *hr = Hr + k * PP, *hi = Hi + k * PP;
+          for (size_t f = 0; f < PP; ++f) { /* conj(S^) * H^ */
+            sr[f] += tr[f] * hr[f] + ti[f] * hi[f];
+            si[f] += tr[f] * hi[f] - ti[f] * hr[f];
+          }
+        }
+        fft2(sr, si, P, +1);
+        for (int y = 0; y < py; ++y)
+          for (int x = 0; x < px; ++x) s[((size_t)y * px + x) * nt + n] = sr[(size_t)y * P + x] / (double)PP;
+      }
+    }
+    free(sr); free(si); free(tr); free(ti);
+  }
+  free(Hr); free(Hi);
+  return rc;
+}
+
+int orc_adjoint_fft(const double *S, int win, int nz, int nt, int py, int px, int P, const double *s, double *H) {
+  const int R = (win - 1) / 2;
+  const size_t PP = (size_t)P * P;
+  if (!fft_pad_ok(P, R, py, px)) return ORC_EINVAL;
+  double *Sr = calloc(PP * nt, sizeof(double)), *Si = calloc(PP * nt, sizeof(double));
+  if (!Sr || !Si) { free(Sr); free(Si); return ORC_ENOMEM; }
+  for (int n = 0; n < nt; ++n) {
+    for (int y = 0; y < py; ++y)
+      for (int x = 0; x < px; ++x) Sr[n * PP + (size_t)y * P + x] = s[((size_t)y * px + x) * nt + n];
+    fft2(Sr + n * PP, Si + n * PP, P, -1);
+  }
+  int rc = ORC_OK;
+#pragma omp parallel
+  {
+    double *hr = malloc(sizeof(double) * PP), *hi = malloc(sizeof(double) * PP);
+    double *tr = malloc(sizeof(double) * PP), *ti = malloc(sizeof(double) * PP);
+    if (!hr || !hi || !tr || !ti) {
+#pragma omp atomic write
+      rc = ORC_ENOMEM;
+    } else {
+#pragma omp for schedule(dynamic)
+      for (int k = 0; k < nz; ++k) {
+        memset(hr, 0, sizeof(double) * PP);
+        memset(hi, 0, sizeof(double) * PP);
+        for (int n = 0; n < nt; ++n) {
+          if (!slice_nonzero(S, win, nz, nt, k, n)) continue;
+          orc_slab_dft(S, win, nz, nt, k, n, P, tr, ti);
+          const double *xr = Sr + n * PP, *xi = Si + n * PP;
+          for (size_t f = 0; f < PP; ++f) { /* S^ * s^ */
+            hr[f] += tr[f] * xr[f] - ti[f] * xi[f];
+            hi[f] += tr[f] * xi[f] + ti[f] * xr[f];
+          }
+        }
+        fft2(hr, hi, P, +1);
+        for (int y = 0; y < py; ++y)
+          for (int x = 0; x < px; ++x) H[((size_t)y * px + x) * nz + k] = hr[(size_t)y * P + x] / (double)PP;
+      }
+    }
+    free(hr); free(hi); free(tr); free(ti);
+  }
+  free(Sr); free(Si);
+  return rc;
+}
