@@ -60,8 +60,15 @@ typedef enum {
 
 typedef enum {
   OAM_PREC_FP32 = 0,  /* plain FP32 slab and FP32 CUDA-core operators */
-  OAM_PREC_BF16X3 = 1 /* split-BF16 (hi+lo) slab and iterate on tcgen05 tensor cores,
-                         FP32 accumulation in tensor memory: hi*hi + hi*lo + lo*hi */
+  OAM_PREC_BF16X3 = 1, /* split-BF16 (hi+lo) slab and iterate on tcgen05 tensor cores,
+                          FP32 accumulation in tensor memory: hi*hi + hi*lo + lo*hi */
+  OAM_PREC_FFT = 2     /* FP32 lateral-FFT form of the same operators: both are 2-D
+                          correlations over the scan grid (Methods, Efficient
+                          reconstruction based on scanning symmetries), restated
+                          exactly by the correlation theorem on a zero-padded
+                          P x P grid (P a power of two >= max(py, px) + R, at most
+                          2048), with the slab's real lateral spectrum stored once
+                          per frequency orbit */
 } oam_precision;
 
 /* Spherically focused sensor (AR-OAM set-up): focal length F, aperture
@@ -98,9 +105,12 @@ typedef struct {
   int64_t nnz;         /* nonzero slab entries over all win*win*nz columns */
   double flops_per_op; /* algorithmic flops of one forward (= one adjoint): 2*px*py*nnz_in_grid */
   size_t device_bytes; /* device memory owned by the model */
-  double exec_flops_forward, exec_flops_adjoint; /* tensor-core flops issued per application
-                                                    (3 BF16 products, band and tile padding);
-                                                    0 for OAM_PREC_FP32 */
+  double exec_flops_forward, exec_flops_adjoint; /* flops issued per application: tensor-core
+                                                    flops (3 BF16 products, band and tile padding)
+                                                    for OAM_PREC_BF16X3, banded spectral products
+                                                    and FFTs for OAM_PREC_FFT; 0 for OAM_PREC_FP32 */
+  double op_bytes;     /* OAM_PREC_FFT: device bytes read + written per application (the
+                          spectral slab dominates); 0 otherwise */
 } oam_model_info;
 
 /* Build the model slab on the device (Methods: Forward modeling, Eqs. 1-4;

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "liboam.so")
 
 OAM_OK, OAM_ERR_INVALID_ARG, OAM_ERR_WINDOW, OAM_ERR_OOM, OAM_ERR_CUDA = 0, 1, 2, 3, 4
 OAM_ERR_DEVICE, OAM_ERR_TIMEOUT, OAM_ERR_BUSY, OAM_ERR_UNSUPPORTED = 5, 6, 7, 8
-OAM_PREC_FP32, OAM_PREC_BF16X3 = 0, 1
+OAM_PREC_FP32, OAM_PREC_BF16X3, OAM_PREC_FFT = 0, 1, 2
 
 EXPORTED = ("oam_build_model", "oam_model_free", "oam_model_get_info", "oam_model_slab_column", "oam_forward",
             "oam_adjoint", "oam_lsqr", "oam_l1_fista", "oam_solver_work_bytes", "oam_status_string",
@@ -44,7 +44,8 @@ class OamModelInfo(ctypes.Structure):
     _fields_ = [("t0_s", ctypes.c_double), ("n_lo", ctypes.c_int32), ("n_hi", ctypes.c_int32),
                 ("n_orbits", ctypes.c_int32), ("precision", ctypes.c_int32), ("nnz", ctypes.c_int64),
                 ("flops_per_op", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("exec_flops_forward", ctypes.c_double), ("exec_flops_adjoint", ctypes.c_double)]
+                ("exec_flops_forward", ctypes.c_double), ("exec_flops_adjoint", ctypes.c_double),
+                ("op_bytes", ctypes.c_double)]
 
 
 class OamLsqrOpts(ctypes.Structure):

@@ -102,6 +102,7 @@ void plan_orbits(oam_model *m) {
 void free_model(oam_model *m, cudaStream_t st) {
   if (!m) return;
   tc_free(m, st);
+  fft_free(m, st);
   for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
   void *ptrs[] = {m->d_status, m->d_tap_orbit, m->d_patch, m->d_band_lo, m->d_band, m->d_fwd_krange, m->d_fwd_off,
                   m->d_fwd, m->d_adj_nrange, m->d_adj_off, m->d_adj};
@@ -222,7 +223,8 @@ oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const
   *out = nullptr;
   oam_status rc = check_params(sensor, grid, eir);
   if (rc) return rc;
-  if (precision != OAM_PREC_FP32 && precision != OAM_PREC_BF16X3) return OAM_ERR_INVALID_ARG;
+  if (precision != OAM_PREC_FP32 && precision != OAM_PREC_BF16X3 && precision != OAM_PREC_FFT)
+    return OAM_ERR_INVALID_ARG;
   int dev = 0, major = 0, minor = 0, sms = 0;
   OAM_CUDA_TRY(cudaGetDevice(&dev));
   OAM_CUDA_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
@@ -251,6 +253,7 @@ oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const
   if (!rc) rc = upload_patches(m, st);
   if (!rc) rc = build_slab(m, st);
   if (!rc && precision == OAM_PREC_BF16X3) rc = tc_build(m, st);
+  if (!rc && precision == OAM_PREC_FFT) rc = fft_build(m, st);
   if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = OAM_ERR_CUDA;
   if (rc) {
     cudaStreamSynchronize(st);
@@ -281,8 +284,9 @@ oam_status oam_model_get_info(const oam_model *m, oam_model_info *info) {
   info->nnz = m->nnz;
   info->flops_per_op = m->flops;
   info->device_bytes = m->bytes;
-  info->exec_flops_forward = tc_exec_flops(m, 0);
-  info->exec_flops_adjoint = tc_exec_flops(m, 1);
+  info->exec_flops_forward = m->precision == OAM_PREC_FFT ? fft_flops(m) : tc_exec_flops(m, 0);
+  info->exec_flops_adjoint = m->precision == OAM_PREC_FFT ? fft_flops(m) : tc_exec_flops(m, 1);
+  info->op_bytes = fft_bytes(m);
   return OAM_OK;
 }
 
@@ -309,10 +313,12 @@ oam_status oam_adjoint(const oam_model *m, const float *d_s, float *d_H, void *s
 
 oam_status oam::apply_forward(const oam_model *m, const float *H, float *s, cudaStream_t st) {
   if (m->precision == OAM_PREC_BF16X3) return forward_tc(m, H, s, st);
+  if (m->precision == OAM_PREC_FFT) return forward_fft(m, H, s, st);
   return forward_fp32(m, H, s, st);
 }
 
 oam_status oam::apply_adjoint(const oam_model *m, const float *s, float *H, cudaStream_t st) {
   if (m->precision == OAM_PREC_BF16X3) return adjoint_tc(m, s, H, st);
+  if (m->precision == OAM_PREC_FFT) return adjoint_fft(m, s, H, st);
   return adjoint_fp32(m, s, H, st);
 }

@@ -33,6 +33,8 @@ struct __align__(32) Patch {
 
 // Tensor-core operator layout of one direction (forward or adjoint); defined in op_tc.cu.
 struct TcLayout;
+// Lateral-FFT form of the operators (OAM_PREC_FFT); defined in op_fft.cu.
+struct FftLayout;
 
 }  // namespace oam
 
@@ -80,6 +82,8 @@ struct oam_model {
   size_t tc_pack_bytes = 0;
   long long tc_qtot = 0;
   float *d_tc_part = nullptr;  // per-part partial sums of the tensor-core operators
+
+  oam::FftLayout *fft = nullptr;  // lateral-FFT form (OAM_PREC_FFT)
 
   int *d_status = nullptr;  // device error word (bounded waits that ran out)
   cudaStream_t alloc_stream = nullptr;  // stream of the stream-ordered allocations (the build stream)
@@ -146,6 +150,14 @@ oam_status forward_tc(const oam_model *m, const float *H, float *s, cudaStream_t
 oam_status adjoint_tc(const oam_model *m, const float *s, float *H, cudaStream_t st);
 double tc_exec_flops(const oam_model *m, int dir);
 oam_status tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_fwd, int *best_adj);
+
+// op_fft.cu
+oam_status fft_build(oam_model *m, cudaStream_t st);
+void fft_free(oam_model *m, cudaStream_t st);
+oam_status forward_fft(const oam_model *m, const float *H, float *s, cudaStream_t st);
+oam_status adjoint_fft(const oam_model *m, const float *s, float *H, cudaStream_t st);
+double fft_flops(const oam_model *m);
+double fft_bytes(const oam_model *m);
 
 // free every device buffer of a model with cudaFreeAsync on `st`, then the model
 void model_release(oam_model *m, cudaStream_t st);

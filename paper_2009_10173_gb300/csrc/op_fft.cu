@@ -1,0 +1,554 @@
+// Lateral-FFT form of the forward and adjoint operators (FP32).
+//
+// A and A^T are 2-D correlations of the single-position slab with the volume
+// over the scan grid (Methods, Efficient reconstruction based on scanning
+// symmetries: the model is the same for every scanning position).  With the
+// volume and the signals zero-padded to P x P, P a power of two with
+// P >= max(py, px) + R, no circular wrap reaches the output window, and the
+// correlation theorem restates both operators exactly per lateral frequency
+// (v, u):
+//   A:    s^(v,u,n) = sum_k S^(v,u,k,n) H^(v,u,k)
+//   A^T:  H^(v,u,k) = sum_n S^(v,u,k,n) s^(v,u,n)
+// The slab is mirror-symmetric in both lateral offsets (the patch set is;
+// Results, axial symmetry), so its lateral DFT
+//   S^(v,u,k,n) = sum_{b,a} S[b][a][k][n] cos(2 pi v b / P) cos(2 pi u a / P)
+// is real and even in v and in u (and symmetric in (v, u) when dx = dy), and
+// conj(S^) = S^.  Ŝ is therefore stored once per frequency orbit
+// {(+-v, +-u)} (and (u, v)), each orbit row holding, for every depth k, the
+// union band of samples [klo_k, klo_k + klen_k) over all lateral offsets.
+//
+// One application is five launches: FFT along x of real rows (half spectrum
+// u in [0, P/2]), FFT along y, the per-orbit banded real matrix times up to
+// four complex frequency vectors, inverse FFT along y, inverse FFT along x
+// back to real rows (Hermitian extension) with zero fill outside the band.
+// FFTs are radix-2 in shared memory with twiddles from sincospi; every sum
+// runs in a fixed order, so results are deterministic.
+#include <algorithm>
+#include <set>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace oam;
+
+namespace oam {
+
+struct FftLayout {
+  int P = 0, lgP = 0, Q = 0;  // transform size, its log2, half-spectrum columns P/2 + 1
+  int KC = 0;                 // channels per FFT block
+  bool d4 = false;            // S^(v,u) = S^(u,v)
+  int n_rep = 0;              // frequency orbits
+  int NS = 0;                 // support length n_hi - n_lo
+  int C = 0;                  // max(nz, NS): channels of the work buffers
+  long long row_len = 0;      // sum_k klen_k: entries of one orbit row of S^
+  int *d_klo = nullptr, *d_klen = nullptr;  // [nz] union band per depth (absolute samples)
+  long long *d_koff = nullptr;              // [nz] offset of depth k in an orbit row
+  int4 *d_members = nullptr;                // [n_rep] half-spectrum indices u*P + v (-1 unused)
+  float *d_shat = nullptr;                  // [n_rep][row_len]
+  float2 *d_w1 = nullptr, *d_w2 = nullptr;  // [Q][P][C] work buffers
+  double flops = 0;                         // flops of one application (matrix part + FFTs)
+  double bytes = 0;                         // device bytes read + written per application
+};
+
+}  // namespace oam
+
+namespace {
+
+constexpr int kFftThreads = 256;
+constexpr int kApplyThreads = 256;
+constexpr int kBuildThreads = 128;
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Twiddles w_j = exp(-2 pi i j / P), j < P/2, into shared memory.
+__device__ __forceinline__ void load_twiddles(float2 *tw, int P) {
+  for (int j = threadIdx.x; j < (P >> 1); j += blockDim.x) {
+    float s, c;
+    sincospif(-2.0f * (float)j / (float)P, &s, &c);
+    tw[j] = make_float2(c, s);
+  }
+}
+
+// In-place radix-2 decimation-in-time transforms of KC interleaved lines of
+// P complex values (a[i * KC + c], loaded in bit-reversed order), sign -1
+// (forward) or +1 (inverse, unscaled).
+__device__ void fft_lines(float2 *a, const float2 *tw, int P, int KC, bool inverse) {
+  __syncthreads();
+  const int nb = (P >> 1) * KC;
+  for (int half = 1, step = P >> 1; half < P; half <<= 1, step >>= 1) {
+    for (int id = threadIdx.x; id < nb; id += blockDim.x) {
+      const int c = id % KC, t = id / KC;
+      const int q = t & (half - 1);
+      const int i0 = 2 * t - q, i1 = i0 + half;
+      float2 w = tw[q * step];
+      if (inverse) w.y = -w.y;
+      const float2 x0 = a[i0 * KC + c], y = cmul(a[i1 * KC + c], w);
+      a[i0 * KC + c] = make_float2(x0.x + y.x, x0.y + y.y);
+      a[i1 * KC + c] = make_float2(x0.x - y.x, x0.y - y.y);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int bitrev(int x, int lg) { return (int)(__brev((unsigned)x) >> (32 - lg)); }
+
+// Real rows -> half spectrum along x.  X[py][px][Ctot] (channels c0 .. c0+C-1
+// used), Y[Q][py][C] complex.  Block (y, channel block).
+__global__ void __launch_bounds__(kFftThreads) k_fft_rows_r2c(const float *__restrict__ X, int py, int px, int Ctot,
+                                                              int c0, int C, int P, int lgP, int KC, int Q,
+                                                              float2 *__restrict__ Y) {
+  extern __shared__ float2 sm[];
+  float2 *tw = sm, *a = sm + (P >> 1);
+  const int y = blockIdx.x, cb = blockIdx.y * KC;
+  load_twiddles(tw, P);
+  for (int i = threadIdx.x; i < P * KC; i += blockDim.x) {
+    const int x = i / KC, c = i % KC;
+    float v = 0.0f;
+    if (x < px && cb + c < C) v = X[((size_t)y * px + x) * Ctot + c0 + cb + c];
+    a[bitrev(x, lgP) * KC + c] = make_float2(v, 0.0f);
+  }
+  fft_lines(a, tw, P, KC, false);
+  for (int i = threadIdx.x; i < Q * KC; i += blockDim.x) {
+    const int u = i / KC, c = i % KC;
+    if (cb + c < C) Y[((size_t)u * py + y) * C + cb + c] = a[u * KC + c];
+  }
+}
+
+// Complex transform along the row index of Z[Q][nin][C] -> W[Q][nout][C]
+// (rows >= nin read as zero, rows >= nout dropped).  Block (u, channel block).
+__global__ void __launch_bounds__(kFftThreads) k_fft_cols(const float2 *__restrict__ Z, int nin, int nout, int C, int P,
+                                                          int lgP, int KC, int inverse, float2 *__restrict__ W) {
+  extern __shared__ float2 sm[];
+  float2 *tw = sm, *a = sm + (P >> 1);
+  const int u = blockIdx.x, cb = blockIdx.y * KC;
+  load_twiddles(tw, P);
+  for (int i = threadIdx.x; i < P * KC; i += blockDim.x) {
+    const int r = i / KC, c = i % KC;
+    float2 v = make_float2(0.0f, 0.0f);
+    if (r < nin && cb + c < C) v = Z[((size_t)u * nin + r) * C + cb + c];
+    a[bitrev(r, lgP) * KC + c] = v;
+  }
+  fft_lines(a, tw, P, KC, inverse != 0);
+  for (int i = threadIdx.x; i < nout * KC; i += blockDim.x) {
+    const int r = i / KC, c = i % KC;
+    if (cb + c < C) W[((size_t)u * nout + r) * C + cb + c] = a[r * KC + c];
+  }
+}
+
+// Half spectrum along x -> real rows, scaled by 1/P^2.  Z[Q][py][C] holds
+// channels c0 .. c0+C-1 of the output X[py][px][Ctot]; every other output
+// channel is written as zero.  Block (y, output channel block).
+__global__ void __launch_bounds__(kFftThreads) k_fft_rows_c2r(const float2 *__restrict__ Z, int py, int px, int Ctot,
+                                                              int c0, int C, int P, int lgP, int KC, int Q,
+                                                              float scale, float *__restrict__ X) {
+  extern __shared__ float2 sm[];
+  float2 *tw = sm, *a = sm + (P >> 1);
+  const int y = blockIdx.x, ob = blockIdx.y * KC;
+  if (ob >= c0 + C || ob + KC <= c0) {  // block entirely outside the band: zeros
+    for (int i = threadIdx.x; i < px * KC; i += blockDim.x) {
+      const int x = i / KC, c = i % KC;
+      if (ob + c < Ctot) X[((size_t)y * px + x) * Ctot + ob + c] = 0.0f;
+    }
+    return;
+  }
+  load_twiddles(tw, P);
+  for (int i = threadIdx.x; i < P * KC; i += blockDim.x) {
+    const int f = i / KC, c = i % KC;
+    const int zc = ob + c - c0;
+    float2 v = make_float2(0.0f, 0.0f);
+    if (zc >= 0 && zc < C) {
+      if (f < Q) {
+        v = Z[((size_t)f * py + y) * C + zc];
+      } else {  // Hermitian extension: Z(P - f) conjugated
+        const float2 w = Z[((size_t)(P - f) * py + y) * C + zc];
+        v = make_float2(w.x, -w.y);
+      }
+    }
+    a[bitrev(f, lgP) * KC + c] = v;
+  }
+  fft_lines(a, tw, P, KC, true);
+  for (int i = threadIdx.x; i < px * KC; i += blockDim.x) {
+    const int x = i / KC, c = i % KC;
+    const int oc = ob + c, zc = oc - c0;
+    if (oc < Ctot) X[((size_t)y * px + x) * Ctot + oc] = (zc >= 0 && zc < C) ? a[x * KC + c].x * scale : 0.0f;
+  }
+}
+
+// Forward, per frequency orbit r: s^_f[j] = sum_k S^_r[k][n - klo_k] H^_f[k]
+// for the orbit's member frequencies f, n = n_lo + j.  Block per orbit.
+__global__ void __launch_bounds__(kApplyThreads) k_fft_apply_fwd(const float *__restrict__ shat, long long row_len,
+                                                                 const int4 *__restrict__ members,
+                                                                 const int *__restrict__ klo,
+                                                                 const int *__restrict__ klen,
+                                                                 const long long *__restrict__ koff, int nz,
+                                                                 int n_lo, int NS, const float2 *__restrict__ Hh,
+                                                                 float2 *__restrict__ sh) {
+  extern __shared__ float2 smf[];
+  float2 *Hs = smf;                                     // [4][nz]
+  int *s_lo = reinterpret_cast<int *>(Hs + 4 * nz);      // [nz]
+  int *s_len = s_lo + nz;                                // [nz]
+  long long *s_off = reinterpret_cast<long long *>(s_len + nz);  // [nz], 8-byte aligned (8 nz bytes above)
+  const int r = blockIdx.x;
+  const int4 mem = members[r];
+  const int f[4] = {mem.x, mem.y, mem.z, mem.w};
+  for (int i = threadIdx.x; i < 4 * nz; i += blockDim.x) {
+    const int mm = i / nz, k = i % nz;
+    Hs[i] = f[mm] >= 0 ? Hh[(size_t)f[mm] * nz + k] : make_float2(0.0f, 0.0f);
+  }
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    s_lo[k] = klo[k];
+    s_len[k] = klen[k];
+    s_off[k] = koff[k];
+  }
+  __syncthreads();
+  const float *row = shat + (size_t)r * row_len;
+  for (int j = threadIdx.x; j < NS; j += blockDim.x) {
+    const int n = n_lo + j;
+    float2 acc[4];
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm) acc[mm] = make_float2(0.0f, 0.0f);
+    for (int k = 0; k < nz; ++k) {
+      const int d = n - s_lo[k];
+      if (d < 0 || d >= s_len[k]) continue;
+      const float sv = row[s_off[k] + d];
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) {
+        const float2 h = Hs[mm * nz + k];
+        acc[mm].x = fmaf(sv, h.x, acc[mm].x);
+        acc[mm].y = fmaf(sv, h.y, acc[mm].y);
+      }
+    }
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm)
+      if (f[mm] >= 0) sh[(size_t)f[mm] * NS + j] = acc[mm];
+  }
+}
+
+// Adjoint, per frequency orbit r: H^_f[k] = sum_{n in band k} S^_r[k][n - klo_k] s^_f[n - n_lo].
+// One warp per depth, lanes over the band, fixed-order butterfly reduction.
+__global__ void __launch_bounds__(kApplyThreads) k_fft_apply_adj(const float *__restrict__ shat, long long row_len,
+                                                                 const int4 *__restrict__ members,
+                                                                 const int *__restrict__ klo,
+                                                                 const int *__restrict__ klen,
+                                                                 const long long *__restrict__ koff, int nz,
+                                                                 int n_lo, int NS, const float2 *__restrict__ sh,
+                                                                 float2 *__restrict__ Hh) {
+  extern __shared__ float2 sma[];
+  float2 *Ss = sma;  // [4][NS]
+  const int r = blockIdx.x;
+  const int4 mem = members[r];
+  const int f[4] = {mem.x, mem.y, mem.z, mem.w};
+  for (int i = threadIdx.x; i < 4 * NS; i += blockDim.x) {
+    const int mm = i / NS, j = i % NS;
+    Ss[i] = f[mm] >= 0 ? sh[(size_t)f[mm] * NS + j] : make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();
+  const float *row = shat + (size_t)r * row_len;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = warp; k < nz; k += nw) {
+    const int lo = klo[k] - n_lo, len = klen[k];
+    const float *rk = row + koff[k];
+    float acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+    for (int d = lane; d < len; d += 32) {
+      const float sv = rk[d];
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) {
+        const float2 x = Ss[mm * NS + lo + d];
+        acc[2 * mm] = fmaf(sv, x.x, acc[2 * mm]);
+        acc[2 * mm + 1] = fmaf(sv, x.y, acc[2 * mm + 1]);
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+    if (lane == 0) {
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm)
+        if (f[mm] >= 0) Hh[(size_t)f[mm] * nz + k] = make_float2(acc[2 * mm], acc[2 * mm + 1]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- S^ build
+// Pass 1: T[b'][u][e] = sum_{a'=0..R} w_a' cos(2 pi u a' / P) S[b'][a'][k_e][n_e]
+// for every row entry e = (k_e, n_e); w_0 = 1, w_{>0} = 2 (the +-a' pair).
+// Block (entry block, b').
+__global__ void __launch_bounds__(kBuildThreads) k_shat_pass1(const float *__restrict__ band,
+                                                              const int *__restrict__ band_lo,
+                                                              const int *__restrict__ band_hi, int band_w,
+                                                              const int *__restrict__ tap_orbit, int R, int W,
+                                                              int nz, const int2 *__restrict__ entry_kn,
+                                                              long long row_len, int P, int Q,
+                                                              float *__restrict__ T) {
+  extern __shared__ float smb[];
+  float *cosT = smb;           // [P]
+  float *sv = smb + P;         // [R+1][blockDim]: weighted slab values of this thread's entry
+  for (int m = threadIdx.x; m < P; m += blockDim.x) cosT[m] = cospif(2.0f * (float)m / (float)P);
+  __syncthreads();
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bp = blockIdx.y;
+  if (e >= row_len) return;
+  const int2 kn = entry_kn[e];
+  const int ts = blockDim.x, tid = threadIdx.x;
+  for (int ap = 0; ap <= R; ++ap) {
+    const int o = tap_orbit[(bp + R) * W + (ap + R)];
+    const int lo = band_lo[o * nz + kn.x], hi = band_hi[o * nz + kn.x];
+    float v = 0.0f;
+    if (kn.y >= lo && kn.y < hi) v = band[((size_t)o * nz + kn.x) * band_w + (kn.y - lo)];
+    sv[ap * ts + tid] = ap == 0 ? v : 2.0f * v;
+  }
+  for (int u = 0; u < Q; ++u) {
+    float acc = 0.0f;
+    for (int ap = 0; ap <= R; ++ap) acc = fmaf(cosT[(u * ap) & (P - 1)], sv[ap * ts + tid], acc);
+    T[((size_t)bp * Q + u) * row_len + e] = acc;
+  }
+}
+
+// Pass 2: S^[r][e] = sum_{b'=0..R} w_b' cos(2 pi v0 b' / P) T[b'][u0][e] for
+// every orbit r = (v0, u0) with this u0.  Block (entry block, u0).
+__global__ void __launch_bounds__(kBuildThreads) k_shat_pass2(const float *__restrict__ T, long long row_len, int R,
+                                                              int P, int Q, const int *__restrict__ rep_of,
+                                                              float *__restrict__ shat) {
+  extern __shared__ float smb[];
+  float *cosT = smb;    // [P]
+  float *tv = smb + P;  // [R+1][blockDim]
+  for (int m = threadIdx.x; m < P; m += blockDim.x) cosT[m] = cospif(2.0f * (float)m / (float)P);
+  __syncthreads();
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int u0 = blockIdx.y;
+  if (e >= row_len) return;
+  const int ts = blockDim.x, tid = threadIdx.x;
+  for (int bp = 0; bp <= R; ++bp) {
+    const float t = T[((size_t)bp * Q + u0) * row_len + e];
+    tv[bp * ts + tid] = bp == 0 ? t : 2.0f * t;
+  }
+  for (int v0 = 0; v0 < Q; ++v0) {
+    const int r = rep_of[v0 * Q + u0];
+    if (r < 0) continue;
+    float acc = 0.0f;
+    for (int bp = 0; bp <= R; ++bp) acc = fmaf(cosT[(v0 * bp) & (P - 1)], tv[bp * ts + tid], acc);
+    shat[(size_t)r * row_len + e] = acc;
+  }
+}
+
+size_t fft_smem(int P, int KC) { return sizeof(float2) * ((size_t)(P >> 1) + (size_t)P * KC); }
+
+}  // namespace
+
+oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
+  const int R = m->R, W = m->W, nz = m->grid.nz;
+  const int need = std::max(m->grid.py, m->grid.px) + R;
+  int P = 2, lgP = 1;
+  while (P < need) {
+    P <<= 1;
+    ++lgP;
+  }
+  if (P > 2048) return OAM_ERR_UNSUPPORTED;
+  FftLayout *L = new (std::nothrow) FftLayout();
+  if (!L) return OAM_ERR_OOM;
+  m->fft = L;
+  L->P = P;
+  L->lgP = lgP;
+  L->Q = P / 2 + 1;
+  L->KC = std::max(2, std::min(16, 4096 / P));
+  const int Q = L->Q;
+  // D4 when the tap -> orbit map is symmetric under b <-> a
+  L->d4 = true;
+  for (int b = -R; b <= R && L->d4; ++b)
+    for (int a = -R; a <= R; ++a)
+      if (m->h_tap_orbit[(b + R) * W + (a + R)] != m->h_tap_orbit[(a + R) * W + (b + R)]) {
+        L->d4 = false;
+        break;
+      }
+  // union band per depth over all orbits
+  std::vector<int> klo(nz, 0), klen(nz, 0);
+  std::vector<long long> koff(nz, 0);
+  long long row = 0;
+  for (int k = 0; k < nz; ++k) {
+    int lo = 1 << 30, hi = -1;
+    for (int o = 0; o < m->n_orb; ++o) {
+      const int bl = m->h_band_lo[(size_t)o * nz + k], bh = m->h_band_hi[(size_t)o * nz + k];
+      if (bh > bl) {
+        lo = std::min(lo, bl);
+        hi = std::max(hi, bh);
+      }
+    }
+    if (hi <= lo) lo = hi = m->n_lo;
+    klo[k] = lo;
+    klen[k] = hi - lo;
+    koff[k] = row;
+    row += hi - lo;
+  }
+  L->row_len = std::max<long long>(row, 1);
+  L->NS = std::max(1, m->n_hi - m->n_lo);
+  L->C = std::max(nz, L->NS);
+  std::vector<int2> entry_kn((size_t)L->row_len, make_int2(0, 0));
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < klen[k]; ++j) entry_kn[(size_t)koff[k] + j] = make_int2(k, klo[k] + j);
+  // frequency orbits and their members in the half spectrum (index u*P + v)
+  std::vector<int> rep_of((size_t)Q * Q, -1);
+  std::vector<int4> members;
+  long long covered = 0;
+  for (int u0 = 0; u0 < Q; ++u0)
+    for (int v0 = 0; v0 < (L->d4 ? u0 + 1 : Q); ++v0) {
+      std::set<int> fs;
+      for (int v : {v0, (P - v0) % P}) fs.insert(u0 * P + v);
+      if (L->d4)
+        for (int v : {u0, (P - u0) % P}) fs.insert(v0 * P + v);
+      int4 mm = make_int4(-1, -1, -1, -1);
+      int *slot = &mm.x;
+      int i = 0;
+      for (int f : fs) slot[i++] = f;
+      covered += i;
+      rep_of[(size_t)v0 * Q + u0] = (int)members.size();
+      members.push_back(mm);
+    }
+  if (covered != (long long)Q * P) return OAM_ERR_DEVICE;  // orbit plan must cover the half spectrum once
+  L->n_rep = (int)members.size();
+
+  oam_status rc;
+  if ((rc = dev_alloc(m, &L->d_klo, nz)) || (rc = dev_alloc(m, &L->d_klen, nz)) ||
+      (rc = dev_alloc(m, &L->d_koff, nz)) || (rc = dev_alloc(m, &L->d_members, members.size())) ||
+      (rc = dev_alloc(m, &L->d_shat, (size_t)L->n_rep * L->row_len)) ||
+      (rc = dev_alloc(m, &L->d_w1, (size_t)Q * P * L->C)) || (rc = dev_alloc(m, &L->d_w2, (size_t)Q * P * L->C)))
+    return rc;
+  OAM_CUDA_TRY(cudaMemcpyAsync(L->d_klo, klo.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, st));
+  OAM_CUDA_TRY(cudaMemcpyAsync(L->d_klen, klen.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, st));
+  OAM_CUDA_TRY(cudaMemcpyAsync(L->d_koff, koff.data(), sizeof(long long) * nz, cudaMemcpyHostToDevice, st));
+  OAM_CUDA_TRY(cudaMemcpyAsync(L->d_members, members.data(), sizeof(int4) * members.size(), cudaMemcpyHostToDevice,
+                               st));
+  // build S^ (temporaries: entry table, band_hi, rep table, T)
+  int2 *d_entry = nullptr;
+  int *d_band_hi = nullptr, *d_rep_of = nullptr;
+  float *d_T = nullptr;
+  const size_t nb = (size_t)m->n_orb * nz;
+  if (cudaMallocAsync((void **)&d_entry, sizeof(int2) * entry_kn.size(), st) != cudaSuccess ||
+      cudaMallocAsync((void **)&d_band_hi, sizeof(int) * nb, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&d_rep_of, sizeof(int) * rep_of.size(), st) != cudaSuccess ||
+      cudaMallocAsync((void **)&d_T, sizeof(float) * (size_t)(R + 1) * Q * L->row_len, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (d_entry) cudaFreeAsync(d_entry, st);
+    if (d_band_hi) cudaFreeAsync(d_band_hi, st);
+    if (d_rep_of) cudaFreeAsync(d_rep_of, st);
+    if (d_T) cudaFreeAsync(d_T, st);
+    return OAM_ERR_OOM;
+  }
+  cudaMemcpyAsync(d_entry, entry_kn.data(), sizeof(int2) * entry_kn.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_band_hi, m->h_band_hi.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_rep_of, rep_of.data(), sizeof(int) * rep_of.size(), cudaMemcpyHostToDevice, st);
+  const unsigned eblocks = (unsigned)((L->row_len + kBuildThreads - 1) / kBuildThreads);
+  const size_t sb = sizeof(float) * ((size_t)P + (size_t)(R + 1) * kBuildThreads);
+  if (sb > 48 * 1024) {
+    OAM_CUDA_TRY(cudaFuncSetAttribute(k_shat_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+    OAM_CUDA_TRY(cudaFuncSetAttribute(k_shat_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+  }
+  k_shat_pass1<<<dim3(eblocks, R + 1), kBuildThreads, sb, st>>>(
+      m->d_band, m->d_band_lo, d_band_hi, m->band_w, m->d_tap_orbit, R, W, nz, d_entry, L->row_len, P, Q, d_T);
+  OAM_LAUNCHED();
+  k_shat_pass2<<<dim3(eblocks, Q), kBuildThreads, sb, st>>>(d_T, L->row_len, R, P, Q, d_rep_of,
+                                                                            L->d_shat);
+  OAM_LAUNCHED();
+  OAM_CUDA_TRY(cudaStreamSynchronize(st));  // host tables above go out of scope
+  cudaFreeAsync(d_entry, st);
+  cudaFreeAsync(d_band_hi, st);
+  cudaFreeAsync(d_rep_of, st);
+  cudaFreeAsync(d_T, st);
+  // cost of one application: the banded matrix over all member frequencies
+  // (real x complex: 4 flops per entry) and 5 N log2 N per complex transform
+  const double half = (double)Q * P;
+  const double fft_lines = (double)m->grid.py * m->grid.nz + half / P * m->grid.nz + half / P * L->NS +
+                           (double)m->grid.py * L->NS;
+  L->flops = 4.0 * half * (double)L->row_len + 5.0 * P * lgP * fft_lines;
+  const double c8 = sizeof(float2);
+  L->bytes = 4.0 * (double)L->n_rep * L->row_len +                              // S^
+             4.0 * vol_elems(m) + 4.0 * (double)m->grid.py * m->grid.px * m->grid.nt +  // input, output
+             c8 * Q * m->grid.py * (nz + L->NS) * 2 +                            // row-transform buffers
+             c8 * half * (nz + L->NS) * 2;                                       // column-transform buffers
+  return OAM_OK;
+}
+
+void oam::fft_free(oam_model *m, cudaStream_t st) {
+  FftLayout *L = m->fft;
+  if (!L) return;
+  for (void *p : {(void *)L->d_klo, (void *)L->d_klen, (void *)L->d_koff, (void *)L->d_members, (void *)L->d_shat,
+                  (void *)L->d_w1, (void *)L->d_w2})
+    if (p) cudaFreeAsync(p, st);
+  delete L;
+  m->fft = nullptr;
+}
+
+double oam::fft_flops(const oam_model *m) { return m->fft ? m->fft->flops : 0.0; }
+double oam::fft_bytes(const oam_model *m) { return m->fft ? m->fft->bytes : 0.0; }
+
+namespace {
+
+oam_status set_smem(const void *fn, size_t bytes) {
+  if (bytes > 48 * 1024)
+    OAM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return OAM_OK;
+}
+
+}  // namespace
+
+oam_status oam::forward_fft(const oam_model *m, const float *H, float *s, cudaStream_t st) {
+  const FftLayout *L = m->fft;
+  if (!L) return OAM_ERR_UNSUPPORTED;
+  const int P = L->P, Q = L->Q, KC = L->KC, nz = m->grid.nz, py = m->grid.py, px = m->grid.px;
+  const size_t sm = fft_smem(P, KC);
+  oam_status rc;
+  if ((rc = set_smem((const void *)k_fft_rows_r2c, sm)) || (rc = set_smem((const void *)k_fft_cols, sm)) ||
+      (rc = set_smem((const void *)k_fft_rows_c2r, sm)))
+    return rc;
+  ProfScope prof(m, st, true);
+  const unsigned cbz = (unsigned)((nz + KC - 1) / KC), cbs = (unsigned)((L->NS + KC - 1) / KC);
+  k_fft_rows_r2c<<<dim3(py, cbz), kFftThreads, sm, st>>>(H, py, px, nz, 0, nz, P, L->lgP, KC, Q, L->d_w2);
+  OAM_LAUNCHED();
+  k_fft_cols<<<dim3(Q, cbz), kFftThreads, sm, st>>>(L->d_w2, py, P, nz, P, L->lgP, KC, 0, L->d_w1);
+  OAM_LAUNCHED();
+  const size_t sa = sizeof(float2) * 4 * nz + sizeof(int) * 2 * nz + sizeof(long long) * nz;
+  if ((rc = set_smem((const void *)k_fft_apply_fwd, sa))) return rc;
+  k_fft_apply_fwd<<<L->n_rep, kApplyThreads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
+                                                       L->d_koff, nz, m->n_lo, L->NS, L->d_w1, L->d_w2);
+  OAM_LAUNCHED();
+  k_fft_cols<<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, P, py, L->NS, P, L->lgP, KC, 1, L->d_w1);
+  OAM_LAUNCHED();
+  const unsigned cbt = (unsigned)((m->grid.nt + KC - 1) / KC);
+  k_fft_rows_c2r<<<dim3(py, cbt), kFftThreads, sm, st>>>(L->d_w1, py, px, m->grid.nt, m->n_lo, L->NS, P, L->lgP, KC,
+                                                         Q, 1.0f / ((float)P * (float)P), s);
+  OAM_LAUNCHED();
+  return OAM_OK;
+}
+
+oam_status oam::adjoint_fft(const oam_model *m, const float *s, float *H, cudaStream_t st) {
+  const FftLayout *L = m->fft;
+  if (!L) return OAM_ERR_UNSUPPORTED;
+  const int P = L->P, Q = L->Q, KC = L->KC, nz = m->grid.nz, py = m->grid.py, px = m->grid.px;
+  const size_t sm = fft_smem(P, KC);
+  oam_status rc;
+  if ((rc = set_smem((const void *)k_fft_rows_r2c, sm)) || (rc = set_smem((const void *)k_fft_cols, sm)) ||
+      (rc = set_smem((const void *)k_fft_rows_c2r, sm)))
+    return rc;
+  ProfScope prof(m, st, false);
+  const unsigned cbz = (unsigned)((nz + KC - 1) / KC), cbs = (unsigned)((L->NS + KC - 1) / KC);
+  k_fft_rows_r2c<<<dim3(py, cbs), kFftThreads, sm, st>>>(s, py, px, m->grid.nt, m->n_lo, L->NS, P, L->lgP, KC, Q,
+                                                         L->d_w2);
+  OAM_LAUNCHED();
+  k_fft_cols<<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, py, P, L->NS, P, L->lgP, KC, 0, L->d_w1);
+  OAM_LAUNCHED();
+  const size_t sa = sizeof(float2) * 4 * L->NS;
+  if ((rc = set_smem((const void *)k_fft_apply_adj, sa))) return rc;
+  k_fft_apply_adj<<<L->n_rep, kApplyThreads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
+                                                       L->d_koff, nz, m->n_lo, L->NS, L->d_w1, L->d_w2);
+  OAM_LAUNCHED();
+  k_fft_cols<<<dim3(Q, cbz), kFftThreads, sm, st>>>(L->d_w2, P, py, nz, P, L->lgP, KC, 1, L->d_w1);
+  OAM_LAUNCHED();
+  k_fft_rows_c2r<<<dim3(py, cbz), kFftThreads, sm, st>>>(L->d_w1, py, px, nz, 0, nz, P, L->lgP, KC, Q,
+                                                         1.0f / ((float)P * (float)P), H);
+  OAM_LAUNCHED();
+  return OAM_OK;
+}

@@ -51,7 +51,7 @@ def standalone(cfg, m, s):
     return x2.cpu().numpy(), x1.cpu().numpy()
 
 
-@pytest.mark.parametrize("prec", [B.OAM_PREC_FP32, B.OAM_PREC_BF16X3])
+@pytest.mark.parametrize("prec", [B.OAM_PREC_FP32, B.OAM_PREC_BF16X3, B.OAM_PREC_FFT])
 def test_batch_graph_equals_standalone_runs(prec):
     cfgs, sigs = [], []
     for cfg in JOBS:
