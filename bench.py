@@ -35,6 +35,11 @@ FP32_LANES_PER_SM = 128
 # same kernel on a 96x96-position case of this workload (441.3 MB for 2945 blocks),
 # scaled by blocks processed (11160 / 2945).  Set to None when the kernel changes.
 TC_TRAFFIC_BYTES = 441.3e6 * 11160 / 2945
+# DRAM bytes per application of the lateral-FFT form on this workload:
+# dram__bytes_read.sum + dram__bytes_write.sum over the five launches of one
+# forward, from an ncu capture of the full 200x200x300 workload (1.190 GB read,
+# 0.242 GB written).  Set to None when those kernels change.
+FFT_TRAFFIC_BYTES = 1.432e9
 
 
 def parse():
@@ -43,7 +48,8 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16x3"])
+    p.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16x3", "fft"],
+                   help="operator form: auto = split-BF16 tensor cores when built; fft = FP32 lateral-FFT form")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -243,6 +249,8 @@ def run_ours(args, rank, world):
         prec = B.OAM_PREC_FP32
     elif args.prec == "bf16x3":
         prec = B.OAM_PREC_BF16X3
+    elif args.prec == "fft":
+        prec = B.OAM_PREC_FFT
     else:
         try:
             make_model(B.OAM_PREC_BF16X3).close()
@@ -252,7 +260,9 @@ def run_ours(args, rank, world):
                 raise
             prec = B.OAM_PREC_FP32
     prec_name = {B.OAM_PREC_FP32: "fp32 CUDA-core operators",
-                 B.OAM_PREC_BF16X3: "split-BF16 (hi*hi+hi*lo+lo*hi) tcgen05 operators, FP32 accumulate"}[prec]
+                 B.OAM_PREC_BF16X3: "split-BF16 (hi*hi+hi*lo+lo*hi) tcgen05 operators, FP32 accumulate",
+                 B.OAM_PREC_FFT: "FP32 lateral-FFT form of the same operators (correlation theorem on a "
+                                 "256x256 zero-padded grid, real slab spectrum per frequency orbit)"}[prec]
 
     # synthetic input for this rank: vessel tree + microspheres, clean signals by A, 20 dB noise
     from paper_2009_10173_gb300 import replicas
@@ -348,7 +358,15 @@ def run_ours(args, rank, world):
     except Exception:
         pass
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    if prec == B.OAM_PREC_FP32:
+    if prec == B.OAM_PREC_FFT:
+        # bytes one application must move: the spectral slab, the input and the
+        # output, and each transform stage's buffer written once and read once
+        gbs = info.op_bytes / (dom_ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "kernel": f"{dom} (lateral-FFT form, 5 launches)", "achieved": gbs, "peak": peak,
+                "unit": "GB/s", "frac": gbs / peak, "traffic": FFT_TRAFFIC_BYTES, "bytes_per_op": info.op_bytes,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    elif prec == B.OAM_PREC_FP32:
         mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
         roof = {"bound": "alu", "kernel": f"{dom} (FP32 FFMA)", "achieved": achieved, "peak": peak,
@@ -363,7 +381,7 @@ def run_ours(args, rank, world):
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
     line = {"metric": METRIC, "value": value, "unit": "volumes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == B.OAM_PREC_FP32 else "bf16", "data": "synthetic",
+            "vs_baseline": None, "dtype": "bf16" if prec == B.OAM_PREC_BF16X3 else "f32", "data": "synthetic",
             "config": config_dict(prec_name),
             "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
             "op_tflops_algorithmic": OPS_PER_STEP * info.flops_per_op / (per_step * 1e-3) / 1e12,

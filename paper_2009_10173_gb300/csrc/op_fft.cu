@@ -44,6 +44,10 @@ struct FftLayout {
   int *d_klo = nullptr, *d_klen = nullptr;  // [nz] union band per depth (absolute samples)
   long long *d_koff = nullptr;              // [nz] offset of depth k in an orbit row
   int4 *d_members = nullptr;                // [n_rep] half-spectrum indices u*P + v (-1 unused)
+  int2 *d_krange = nullptr;                 // [NS] depths [x, y) whose band can hold sample n_lo + j
+  long long *d_noff = nullptr;              // [NS] offset of sample n_lo + j in a transposed orbit row
+  long long row_len_t = 0;                  // sum_j (krange_j.y - krange_j.x)
+  float *d_shat_t = nullptr;                // [n_rep][row_len_t]: S^ by sample, depths krange_j (adjoint)
   float *d_shat = nullptr;                  // [n_rep][row_len]
   float2 *d_w1 = nullptr, *d_w2 = nullptr;  // [Q][P][C] work buffers
   double flops = 0;                         // flops of one application (matrix part + FFTs)
@@ -55,7 +59,7 @@ struct FftLayout {
 namespace {
 
 constexpr int kFftThreads = 256;
-constexpr int kApplyThreads = 256;
+constexpr int kApplyMaxThreads = 512;
 constexpr int kBuildThreads = 128;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -74,7 +78,8 @@ __device__ __forceinline__ void load_twiddles(float2 *tw, int P) {
 // In-place radix-2 decimation-in-time transforms of KC interleaved lines of
 // P complex values (a[i * KC + c], loaded in bit-reversed order), sign -1
 // (forward) or +1 (inverse, unscaled).
-__device__ void fft_lines(float2 *a, const float2 *tw, int P, int KC, bool inverse) {
+template <int KC>
+__device__ void fft_lines(float2 *a, const float2 *tw, int P, bool inverse) {
   __syncthreads();
   const int nb = (P >> 1) * KC;
   for (int half = 1, step = P >> 1; half < P; half <<= 1, step >>= 1) {
@@ -96,8 +101,9 @@ __device__ __forceinline__ int bitrev(int x, int lg) { return (int)(__brev((unsi
 
 // Real rows -> half spectrum along x.  X[py][px][Ctot] (channels c0 .. c0+C-1
 // used), Y[Q][py][C] complex.  Block (y, channel block).
+template <int KC>
 __global__ void __launch_bounds__(kFftThreads) k_fft_rows_r2c(const float *__restrict__ X, int py, int px, int Ctot,
-                                                              int c0, int C, int P, int lgP, int KC, int Q,
+                                                              int c0, int C, int P, int lgP, int Q,
                                                               float2 *__restrict__ Y) {
   extern __shared__ float2 sm[];
   float2 *tw = sm, *a = sm + (P >> 1);
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_r2c(const float *__res
     if (x < px && cb + c < C) v = X[((size_t)y * px + x) * Ctot + c0 + cb + c];
     a[bitrev(x, lgP) * KC + c] = make_float2(v, 0.0f);
   }
-  fft_lines(a, tw, P, KC, false);
+  fft_lines<KC>(a, tw, P, false);
   for (int i = threadIdx.x; i < Q * KC; i += blockDim.x) {
     const int u = i / KC, c = i % KC;
     if (cb + c < C) Y[((size_t)u * py + y) * C + cb + c] = a[u * KC + c];
@@ -118,8 +124,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_r2c(const float *__res
 
 // Complex transform along the row index of Z[Q][nin][C] -> W[Q][nout][C]
 // (rows >= nin read as zero, rows >= nout dropped).  Block (u, channel block).
+template <int KC>
 __global__ void __launch_bounds__(kFftThreads) k_fft_cols(const float2 *__restrict__ Z, int nin, int nout, int C, int P,
-                                                          int lgP, int KC, int inverse, float2 *__restrict__ W) {
+                                                          int lgP, int inverse, float2 *__restrict__ W) {
   extern __shared__ float2 sm[];
   float2 *tw = sm, *a = sm + (P >> 1);
   const int u = blockIdx.x, cb = blockIdx.y * KC;
@@ -130,7 +137,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(const float2 *__restri
     if (r < nin && cb + c < C) v = Z[((size_t)u * nin + r) * C + cb + c];
     a[bitrev(r, lgP) * KC + c] = v;
   }
-  fft_lines(a, tw, P, KC, inverse != 0);
+  fft_lines<KC>(a, tw, P, inverse != 0);
   for (int i = threadIdx.x; i < nout * KC; i += blockDim.x) {
     const int r = i / KC, c = i % KC;
     if (cb + c < C) W[((size_t)u * nout + r) * C + cb + c] = a[r * KC + c];
@@ -140,8 +147,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(const float2 *__restri
 // Half spectrum along x -> real rows, scaled by 1/P^2.  Z[Q][py][C] holds
 // channels c0 .. c0+C-1 of the output X[py][px][Ctot]; every other output
 // channel is written as zero.  Block (y, output channel block).
+template <int KC>
 __global__ void __launch_bounds__(kFftThreads) k_fft_rows_c2r(const float2 *__restrict__ Z, int py, int px, int Ctot,
-                                                              int c0, int C, int P, int lgP, int KC, int Q,
+                                                              int c0, int C, int P, int lgP, int Q,
                                                               float scale, float *__restrict__ X) {
   extern __shared__ float2 sm[];
   float2 *tw = sm, *a = sm + (P >> 1);
@@ -168,7 +176,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_c2r(const float2 *__re
     }
     a[bitrev(f, lgP) * KC + c] = v;
   }
-  fft_lines(a, tw, P, KC, true);
+  fft_lines<KC>(a, tw, P, true);
   for (int i = threadIdx.x; i < px * KC; i += blockDim.x) {
     const int x = i / KC, c = i % KC;
     const int oc = ob + c, zc = oc - c0;
@@ -177,100 +185,164 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_c2r(const float2 *__re
 }
 
 // Forward, per frequency orbit r: s^_f[j] = sum_k S^_r[k][n - klo_k] H^_f[k]
-// for the orbit's member frequencies f, n = n_lo + j.  Block per orbit.
-__global__ void __launch_bounds__(kApplyThreads) k_fft_apply_fwd(const float *__restrict__ shat, long long row_len,
-                                                                 const int4 *__restrict__ members,
-                                                                 const int *__restrict__ klo,
-                                                                 const int *__restrict__ klen,
-                                                                 const long long *__restrict__ koff, int nz,
-                                                                 int n_lo, int NS, const float2 *__restrict__ Hh,
-                                                                 float2 *__restrict__ sh) {
-  extern __shared__ float2 smf[];
-  float2 *Hs = smf;                                     // [4][nz]
-  int *s_lo = reinterpret_cast<int *>(Hs + 4 * nz);      // [nz]
-  int *s_len = s_lo + nz;                                // [nz]
-  long long *s_off = reinterpret_cast<long long *>(s_len + nz);  // [nz], 8-byte aligned (8 nz bytes above)
+// for the orbit's member frequencies f, n = n_lo + j; thread j visits the
+// depths [kr_j.x, kr_j.y) whose band holds n.  Block per orbit.
+__global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_fwd(const float *__restrict__ shat, long long row_len,
+                                                        const int4 *__restrict__ members,
+                                                        const int *__restrict__ klo, const int *__restrict__ klen,
+                                                        const long long *__restrict__ koff,
+                                                        const int2 *__restrict__ krange, int nz, int n_lo, int NS,
+                                                        const float2 *__restrict__ Hh, float2 *__restrict__ sh) {
+  extern __shared__ float4 smf[];
+  float4 *Hs = smf;                                  // [nz][2]: members (0, 1) and (2, 3), (re, im) pairs
+  int *s_lo = reinterpret_cast<int *>(Hs + 2 * nz);   // [nz]
+  int *s_len = s_lo + nz;                             // [nz]
+  long long *s_off = reinterpret_cast<long long *>(s_len + nz);  // [nz]: 40 nz bytes in, 8-byte aligned
   const int r = blockIdx.x;
   const int4 mem = members[r];
-  const int f[4] = {mem.x, mem.y, mem.z, mem.w};
-  for (int i = threadIdx.x; i < 4 * nz; i += blockDim.x) {
-    const int mm = i / nz, k = i % nz;
-    Hs[i] = f[mm] >= 0 ? Hh[(size_t)f[mm] * nz + k] : make_float2(0.0f, 0.0f);
-  }
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    const float2 z = make_float2(0.0f, 0.0f);
+    const float2 h0 = mem.x >= 0 ? Hh[(size_t)mem.x * nz + k] : z, h1 = mem.y >= 0 ? Hh[(size_t)mem.y * nz + k] : z;
+    const float2 h2 = mem.z >= 0 ? Hh[(size_t)mem.z * nz + k] : z, h3 = mem.w >= 0 ? Hh[(size_t)mem.w * nz + k] : z;
+    Hs[2 * k] = make_float4(h0.x, h0.y, h1.x, h1.y);
+    Hs[2 * k + 1] = make_float4(h2.x, h2.y, h3.x, h3.y);
     s_lo[k] = klo[k];
     s_len[k] = klen[k];
     s_off[k] = koff[k];
   }
   __syncthreads();
   const float *row = shat + (size_t)r * row_len;
-  for (int j = threadIdx.x; j < NS; j += blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  // every lane of a warp walks the same depths (coalesced row reads); a lane
+  // whose sample lies outside a depth's band reads nothing there
+  for (int j0 = threadIdx.x - lane; j0 < NS; j0 += blockDim.x) {
+    const int j = j0 + lane;
+    const bool live = j < NS;
     const int n = n_lo + j;
-    float2 acc[4];
-#pragma unroll
-    for (int mm = 0; mm < 4; ++mm) acc[mm] = make_float2(0.0f, 0.0f);
-    for (int k = 0; k < nz; ++k) {
-      const int d = n - s_lo[k];
-      if (d < 0 || d >= s_len[k]) continue;
-      const float sv = row[s_off[k] + d];
-#pragma unroll
-      for (int mm = 0; mm < 4; ++mm) {
-        const float2 h = Hs[mm * nz + k];
-        acc[mm].x = fmaf(sv, h.x, acc[mm].x);
-        acc[mm].y = fmaf(sv, h.y, acc[mm].y);
-      }
-    }
-#pragma unroll
-    for (int mm = 0; mm < 4; ++mm)
-      if (f[mm] >= 0) sh[(size_t)f[mm] * NS + j] = acc[mm];
-  }
-}
-
-// Adjoint, per frequency orbit r: H^_f[k] = sum_{n in band k} S^_r[k][n - klo_k] s^_f[n - n_lo].
-// One warp per depth, lanes over the band, fixed-order butterfly reduction.
-__global__ void __launch_bounds__(kApplyThreads) k_fft_apply_adj(const float *__restrict__ shat, long long row_len,
-                                                                 const int4 *__restrict__ members,
-                                                                 const int *__restrict__ klo,
-                                                                 const int *__restrict__ klen,
-                                                                 const long long *__restrict__ koff, int nz,
-                                                                 int n_lo, int NS, const float2 *__restrict__ sh,
-                                                                 float2 *__restrict__ Hh) {
-  extern __shared__ float2 sma[];
-  float2 *Ss = sma;  // [4][NS]
-  const int r = blockIdx.x;
-  const int4 mem = members[r];
-  const int f[4] = {mem.x, mem.y, mem.z, mem.w};
-  for (int i = threadIdx.x; i < 4 * NS; i += blockDim.x) {
-    const int mm = i / NS, j = i % NS;
-    Ss[i] = f[mm] >= 0 ? sh[(size_t)f[mm] * NS + j] : make_float2(0.0f, 0.0f);
-  }
-  __syncthreads();
-  const float *row = shat + (size_t)r * row_len;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = warp; k < nz; k += nw) {
-    const int lo = klo[k] - n_lo, len = klen[k];
-    const float *rk = row + koff[k];
+    const int2 kr = live ? krange[j] : make_int2(nz, 0);
+    const int k0 = __reduce_min_sync(0xffffffffu, kr.x), k1 = __reduce_max_sync(0xffffffffu, kr.y);
     float acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
-    for (int d = lane; d < len; d += 32) {
-      const float sv = rk[d];
+    int k = k0;
+    for (; k + 4 <= k1; k += 4) {
+      float sv[4];
 #pragma unroll
-      for (int mm = 0; mm < 4; ++mm) {
-        const float2 x = Ss[mm * NS + lo + d];
-        acc[2 * mm] = fmaf(sv, x.x, acc[2 * mm]);
-        acc[2 * mm + 1] = fmaf(sv, x.y, acc[2 * mm + 1]);
+      for (int q = 0; q < 4; ++q) {
+        const int d = n - s_lo[k + q];
+        sv[q] = (live && (unsigned)d < (unsigned)s_len[k + q]) ? __ldg(row + s_off[k + q] + d) : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 a = Hs[2 * (k + q)], b = Hs[2 * (k + q) + 1];
+        acc[0] = fmaf(sv[q], a.x, acc[0]);
+        acc[1] = fmaf(sv[q], a.y, acc[1]);
+        acc[2] = fmaf(sv[q], a.z, acc[2]);
+        acc[3] = fmaf(sv[q], a.w, acc[3]);
+        acc[4] = fmaf(sv[q], b.x, acc[4]);
+        acc[5] = fmaf(sv[q], b.y, acc[5]);
+        acc[6] = fmaf(sv[q], b.z, acc[6]);
+        acc[7] = fmaf(sv[q], b.w, acc[7]);
       }
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-      for (int q = 0; q < 8; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
-    if (lane == 0) {
-#pragma unroll
-      for (int mm = 0; mm < 4; ++mm)
-        if (f[mm] >= 0) Hh[(size_t)f[mm] * nz + k] = make_float2(acc[2 * mm], acc[2 * mm + 1]);
+    for (; k < k1; ++k) {
+      const int d = n - s_lo[k];
+      const float sv = (live && (unsigned)d < (unsigned)s_len[k]) ? __ldg(row + s_off[k] + d) : 0.0f;
+      const float4 a = Hs[2 * k], b = Hs[2 * k + 1];
+      acc[0] = fmaf(sv, a.x, acc[0]);
+      acc[1] = fmaf(sv, a.y, acc[1]);
+      acc[2] = fmaf(sv, a.z, acc[2]);
+      acc[3] = fmaf(sv, a.w, acc[3]);
+      acc[4] = fmaf(sv, b.x, acc[4]);
+      acc[5] = fmaf(sv, b.y, acc[5]);
+      acc[6] = fmaf(sv, b.z, acc[6]);
+      acc[7] = fmaf(sv, b.w, acc[7]);
     }
+    if (!live) continue;
+    if (mem.x >= 0) sh[(size_t)mem.x * NS + j] = make_float2(acc[0], acc[1]);
+    if (mem.y >= 0) sh[(size_t)mem.y * NS + j] = make_float2(acc[2], acc[3]);
+    if (mem.z >= 0) sh[(size_t)mem.z * NS + j] = make_float2(acc[4], acc[5]);
+    if (mem.w >= 0) sh[(size_t)mem.w * NS + j] = make_float2(acc[6], acc[7]);
+  }
+}
+
+// Adjoint, per frequency orbit r: H^_f[k] = sum_n S^_r[k][n] s^_f[n - n_lo], from
+// the orbit's row by sample (entries of sample n_lo + j are depths krange_j).
+// Thread k; every lane of a warp walks the same samples (coalesced reads).
+__global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_adj(const float *__restrict__ shat_t,
+                                                                    long long row_len_t,
+                                                                    const int4 *__restrict__ members,
+                                                                    const int *__restrict__ klo,
+                                                                    const int *__restrict__ klen,
+                                                                    const int2 *__restrict__ krange,
+                                                                    const long long *__restrict__ noff, int nz,
+                                                                    int n_lo, int NS, const float2 *__restrict__ sh,
+                                                                    float2 *__restrict__ Hh) {
+  extern __shared__ float4 sma[];
+  float4 *Ss = sma;                                      // [NS][2]: members (0, 1) and (2, 3)
+  int2 *s_kr = reinterpret_cast<int2 *>(Ss + 2 * NS);     // [NS]
+  long long *s_no = reinterpret_cast<long long *>(s_kr + NS);  // [NS]
+  const int r = blockIdx.x;
+  const int4 mem = members[r];
+  for (int j = threadIdx.x; j < NS; j += blockDim.x) {
+    const float2 z = make_float2(0.0f, 0.0f);
+    const float2 x0 = mem.x >= 0 ? sh[(size_t)mem.x * NS + j] : z, x1 = mem.y >= 0 ? sh[(size_t)mem.y * NS + j] : z;
+    const float2 x2 = mem.z >= 0 ? sh[(size_t)mem.z * NS + j] : z, x3 = mem.w >= 0 ? sh[(size_t)mem.w * NS + j] : z;
+    Ss[2 * j] = make_float4(x0.x, x0.y, x1.x, x1.y);
+    Ss[2 * j + 1] = make_float4(x2.x, x2.y, x3.x, x3.y);
+    s_kr[j] = krange[j];
+    s_no[j] = noff[j];
+  }
+  __syncthreads();
+  const float *row = shat_t + (size_t)r * row_len_t;
+  const int lane = threadIdx.x & 31;
+  for (int k0 = threadIdx.x - lane; k0 < nz; k0 += blockDim.x) {
+    const int k = k0 + lane;
+    const bool live = k < nz && klen[k] > 0;
+    const int lo = live ? klo[k] - n_lo : NS, hi = live ? klo[k] - n_lo + klen[k] : 0;
+    const int j0 = __reduce_min_sync(0xffffffffu, lo), j1 = __reduce_max_sync(0xffffffffu, hi);
+    float acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+    int j = j0;
+    for (; j + 4 <= j1; j += 4) {  // four samples' loads in flight, then their products
+      float sv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int2 kr = s_kr[j + q];
+        sv[q] = (k >= kr.x && k < kr.y) ? __ldg(row + s_no[j + q] + (k - kr.x)) : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 a = Ss[2 * (j + q)], b = Ss[2 * (j + q) + 1];
+        acc[0] = fmaf(sv[q], a.x, acc[0]);
+        acc[1] = fmaf(sv[q], a.y, acc[1]);
+        acc[2] = fmaf(sv[q], a.z, acc[2]);
+        acc[3] = fmaf(sv[q], a.w, acc[3]);
+        acc[4] = fmaf(sv[q], b.x, acc[4]);
+        acc[5] = fmaf(sv[q], b.y, acc[5]);
+        acc[6] = fmaf(sv[q], b.z, acc[6]);
+        acc[7] = fmaf(sv[q], b.w, acc[7]);
+      }
+    }
+    for (; j < j1; ++j) {
+      const int2 kr = s_kr[j];
+      const float sv = (k >= kr.x && k < kr.y) ? __ldg(row + s_no[j] + (k - kr.x)) : 0.0f;
+      const float4 a = Ss[2 * j], b = Ss[2 * j + 1];
+      acc[0] = fmaf(sv, a.x, acc[0]);
+      acc[1] = fmaf(sv, a.y, acc[1]);
+      acc[2] = fmaf(sv, a.z, acc[2]);
+      acc[3] = fmaf(sv, a.w, acc[3]);
+      acc[4] = fmaf(sv, b.x, acc[4]);
+      acc[5] = fmaf(sv, b.y, acc[5]);
+      acc[6] = fmaf(sv, b.z, acc[6]);
+      acc[7] = fmaf(sv, b.w, acc[7]);
+    }
+    if (k >= nz) continue;
+    if (mem.x >= 0) Hh[(size_t)mem.x * nz + k] = make_float2(acc[0], acc[1]);
+    if (mem.y >= 0) Hh[(size_t)mem.y * nz + k] = make_float2(acc[2], acc[3]);
+    if (mem.z >= 0) Hh[(size_t)mem.z * nz + k] = make_float2(acc[4], acc[5]);
+    if (mem.w >= 0) Hh[(size_t)mem.w * nz + k] = make_float2(acc[6], acc[7]);
   }
 }
 
@@ -313,7 +385,11 @@ __global__ void __launch_bounds__(kBuildThreads) k_shat_pass1(const float *__res
 // every orbit r = (v0, u0) with this u0.  Block (entry block, u0).
 __global__ void __launch_bounds__(kBuildThreads) k_shat_pass2(const float *__restrict__ T, long long row_len, int R,
                                                               int P, int Q, const int *__restrict__ rep_of,
-                                                              float *__restrict__ shat) {
+                                                              const int2 *__restrict__ entry_kn, int n_lo,
+                                                              const int2 *__restrict__ krange,
+                                                              const long long *__restrict__ noff,
+                                                              long long row_len_t, float *__restrict__ shat,
+                                                              float *__restrict__ shat_t) {
   extern __shared__ float smb[];
   float *cosT = smb;    // [P]
   float *tv = smb + P;  // [R+1][blockDim]
@@ -327,12 +403,16 @@ __global__ void __launch_bounds__(kBuildThreads) k_shat_pass2(const float *__res
     const float t = T[((size_t)bp * Q + u0) * row_len + e];
     tv[bp * ts + tid] = bp == 0 ? t : 2.0f * t;
   }
+  const int2 kn = entry_kn[e];
+  const int jn = kn.y - n_lo;
+  const long long et = noff[jn] + (kn.x - krange[jn].x);  // same entry in the row by sample
   for (int v0 = 0; v0 < Q; ++v0) {
     const int r = rep_of[v0 * Q + u0];
     if (r < 0) continue;
     float acc = 0.0f;
     for (int bp = 0; bp <= R; ++bp) acc = fmaf(cosT[(v0 * bp) & (P - 1)], tv[bp * ts + tid], acc);
     shat[(size_t)r * row_len + e] = acc;
+    shat_t[(size_t)r * row_len_t + et] = acc;
   }
 }
 
@@ -386,6 +466,24 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
   }
   L->row_len = std::max<long long>(row, 1);
   L->NS = std::max(1, m->n_hi - m->n_lo);
+  std::vector<int2> krange(L->NS, make_int2(0, 0));
+  for (int j = 0; j < L->NS; ++j) {
+    const int n = m->n_lo + j;
+    int kf = nz, kl = -1;
+    for (int k = 0; k < nz; ++k)
+      if (n >= klo[k] && n < klo[k] + klen[k]) {
+        kf = std::min(kf, k);
+        kl = std::max(kl, k);
+      }
+    krange[j] = kl >= kf ? make_int2(kf, kl + 1) : make_int2(0, 0);
+  }
+  std::vector<long long> noff(L->NS, 0);
+  long long rowt = 0;
+  for (int j = 0; j < L->NS; ++j) {
+    noff[j] = rowt;
+    rowt += krange[j].y - krange[j].x;
+  }
+  L->row_len_t = std::max<long long>(rowt, 1);
   L->C = std::max(nz, L->NS);
   std::vector<int2> entry_kn((size_t)L->row_len, make_int2(0, 0));
   for (int k = 0; k < nz; ++k)
@@ -414,6 +512,8 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
   oam_status rc;
   if ((rc = dev_alloc(m, &L->d_klo, nz)) || (rc = dev_alloc(m, &L->d_klen, nz)) ||
       (rc = dev_alloc(m, &L->d_koff, nz)) || (rc = dev_alloc(m, &L->d_members, members.size())) ||
+      (rc = dev_alloc(m, &L->d_krange, (size_t)L->NS)) || (rc = dev_alloc(m, &L->d_noff, (size_t)L->NS)) ||
+      (rc = dev_alloc(m, &L->d_shat_t, (size_t)L->n_rep * L->row_len_t)) ||
       (rc = dev_alloc(m, &L->d_shat, (size_t)L->n_rep * L->row_len)) ||
       (rc = dev_alloc(m, &L->d_w1, (size_t)Q * P * L->C)) || (rc = dev_alloc(m, &L->d_w2, (size_t)Q * P * L->C)))
     return rc;
@@ -422,6 +522,10 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
   OAM_CUDA_TRY(cudaMemcpyAsync(L->d_koff, koff.data(), sizeof(long long) * nz, cudaMemcpyHostToDevice, st));
   OAM_CUDA_TRY(cudaMemcpyAsync(L->d_members, members.data(), sizeof(int4) * members.size(), cudaMemcpyHostToDevice,
                                st));
+  OAM_CUDA_TRY(cudaMemcpyAsync(L->d_krange, krange.data(), sizeof(int2) * krange.size(), cudaMemcpyHostToDevice, st));
+  OAM_CUDA_TRY(cudaMemcpyAsync(L->d_noff, noff.data(), sizeof(long long) * noff.size(), cudaMemcpyHostToDevice, st));
+  // entries of the row by sample whose depth band misses the sample stay zero
+  OAM_CUDA_TRY(cudaMemsetAsync(L->d_shat_t, 0, sizeof(float) * (size_t)L->n_rep * L->row_len_t, st));
   // build S^ (temporaries: entry table, band_hi, rep table, T)
   int2 *d_entry = nullptr;
   int *d_band_hi = nullptr, *d_rep_of = nullptr;
@@ -450,8 +554,9 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
   k_shat_pass1<<<dim3(eblocks, R + 1), kBuildThreads, sb, st>>>(
       m->d_band, m->d_band_lo, d_band_hi, m->band_w, m->d_tap_orbit, R, W, nz, d_entry, L->row_len, P, Q, d_T);
   OAM_LAUNCHED();
-  k_shat_pass2<<<dim3(eblocks, Q), kBuildThreads, sb, st>>>(d_T, L->row_len, R, P, Q, d_rep_of,
-                                                                            L->d_shat);
+  k_shat_pass2<<<dim3(eblocks, Q), kBuildThreads, sb, st>>>(d_T, L->row_len, R, P, Q, d_rep_of, d_entry, m->n_lo,
+                                                            L->d_krange, L->d_noff, L->row_len_t, L->d_shat,
+                                                            L->d_shat_t);
   OAM_LAUNCHED();
   OAM_CUDA_TRY(cudaStreamSynchronize(st));  // host tables above go out of scope
   cudaFreeAsync(d_entry, st);
@@ -475,7 +580,8 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
 void oam::fft_free(oam_model *m, cudaStream_t st) {
   FftLayout *L = m->fft;
   if (!L) return;
-  for (void *p : {(void *)L->d_klo, (void *)L->d_klen, (void *)L->d_koff, (void *)L->d_members, (void *)L->d_shat,
+  for (void *p : {(void *)L->d_klo, (void *)L->d_klen, (void *)L->d_koff, (void *)L->d_members, (void *)L->d_krange,
+                  (void *)L->d_noff, (void *)L->d_shat_t, (void *)L->d_shat,
                   (void *)L->d_w1, (void *)L->d_w2})
     if (p) cudaFreeAsync(p, st);
   delete L;
@@ -495,60 +601,73 @@ oam_status set_smem(const void *fn, size_t bytes) {
 
 }  // namespace
 
-oam_status oam::forward_fft(const oam_model *m, const float *H, float *s, cudaStream_t st) {
-  const FftLayout *L = m->fft;
-  if (!L) return OAM_ERR_UNSUPPORTED;
-  const int P = L->P, Q = L->Q, KC = L->KC, nz = m->grid.nz, py = m->grid.py, px = m->grid.px;
+namespace {
+
+template <int KC>
+oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float *in, float *out, cudaStream_t st) {
+  const int P = L->P, Q = L->Q, lgP = L->lgP, nz = m->grid.nz, py = m->grid.py, px = m->grid.px, NS = L->NS;
   const size_t sm = fft_smem(P, KC);
   oam_status rc;
-  if ((rc = set_smem((const void *)k_fft_rows_r2c, sm)) || (rc = set_smem((const void *)k_fft_cols, sm)) ||
-      (rc = set_smem((const void *)k_fft_rows_c2r, sm)))
+  if ((rc = set_smem((const void *)k_fft_rows_r2c<KC>, sm)) || (rc = set_smem((const void *)k_fft_cols<KC>, sm)) ||
+      (rc = set_smem((const void *)k_fft_rows_c2r<KC>, sm)))
     return rc;
-  ProfScope prof(m, st, true);
-  const unsigned cbz = (unsigned)((nz + KC - 1) / KC), cbs = (unsigned)((L->NS + KC - 1) / KC);
-  k_fft_rows_r2c<<<dim3(py, cbz), kFftThreads, sm, st>>>(H, py, px, nz, 0, nz, P, L->lgP, KC, Q, L->d_w2);
-  OAM_LAUNCHED();
-  k_fft_cols<<<dim3(Q, cbz), kFftThreads, sm, st>>>(L->d_w2, py, P, nz, P, L->lgP, KC, 0, L->d_w1);
-  OAM_LAUNCHED();
-  const size_t sa = sizeof(float2) * 4 * nz + sizeof(int) * 2 * nz + sizeof(long long) * nz;
-  if ((rc = set_smem((const void *)k_fft_apply_fwd, sa))) return rc;
-  k_fft_apply_fwd<<<L->n_rep, kApplyThreads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
-                                                       L->d_koff, nz, m->n_lo, L->NS, L->d_w1, L->d_w2);
-  OAM_LAUNCHED();
-  k_fft_cols<<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, P, py, L->NS, P, L->lgP, KC, 1, L->d_w1);
-  OAM_LAUNCHED();
-  const unsigned cbt = (unsigned)((m->grid.nt + KC - 1) / KC);
-  k_fft_rows_c2r<<<dim3(py, cbt), kFftThreads, sm, st>>>(L->d_w1, py, px, m->grid.nt, m->n_lo, L->NS, P, L->lgP, KC,
-                                                         Q, 1.0f / ((float)P * (float)P), s);
-  OAM_LAUNCHED();
+  const unsigned cbz = (unsigned)((nz + KC - 1) / KC), cbs = (unsigned)((NS + KC - 1) / KC);
+  const float scale = 1.0f / ((float)P * (float)P);
+  const int apply_threads = std::min(kApplyMaxThreads, ((fwd ? NS : nz) + 31) & ~31);
+  if (fwd) {
+    k_fft_rows_r2c<KC><<<dim3(py, cbz), kFftThreads, sm, st>>>(in, py, px, nz, 0, nz, P, lgP, Q, L->d_w2);
+    OAM_LAUNCHED();
+    k_fft_cols<KC><<<dim3(Q, cbz), kFftThreads, sm, st>>>(L->d_w2, py, P, nz, P, lgP, 0, L->d_w1);
+    OAM_LAUNCHED();
+    const size_t sa = sizeof(float4) * 2 * nz + sizeof(int) * (2 * nz + 2) + sizeof(long long) * nz;
+    if ((rc = set_smem((const void *)k_fft_apply_fwd, sa))) return rc;
+    k_fft_apply_fwd<<<L->n_rep, apply_threads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
+                                                         L->d_koff, L->d_krange, nz, m->n_lo, NS, L->d_w1, L->d_w2);
+    OAM_LAUNCHED();
+    k_fft_cols<KC><<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, P, py, NS, P, lgP, 1, L->d_w1);
+    OAM_LAUNCHED();
+    const unsigned cbt = (unsigned)((m->grid.nt + KC - 1) / KC);
+    k_fft_rows_c2r<KC><<<dim3(py, cbt), kFftThreads, sm, st>>>(L->d_w1, py, px, m->grid.nt, m->n_lo, NS, P, lgP, Q,
+                                                               scale, out);
+    OAM_LAUNCHED();
+  } else {
+    k_fft_rows_r2c<KC><<<dim3(py, cbs), kFftThreads, sm, st>>>(in, py, px, m->grid.nt, m->n_lo, NS, P, lgP, Q,
+                                                               L->d_w2);
+    OAM_LAUNCHED();
+    k_fft_cols<KC><<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, py, P, NS, P, lgP, 0, L->d_w1);
+    OAM_LAUNCHED();
+    const size_t sa = (sizeof(float4) * 2 + sizeof(int2) + sizeof(long long)) * NS;
+    if ((rc = set_smem((const void *)k_fft_apply_adj, sa))) return rc;
+    k_fft_apply_adj<<<L->n_rep, apply_threads, sa, st>>>(L->d_shat_t, L->row_len_t, L->d_members, L->d_klo,
+                                                         L->d_klen, L->d_krange, L->d_noff, nz, m->n_lo, NS, L->d_w1,
+                                                         L->d_w2);
+    OAM_LAUNCHED();
+    k_fft_cols<KC><<<dim3(Q, cbz), kFftThreads, sm, st>>>(L->d_w2, P, py, nz, P, lgP, 1, L->d_w1);
+    OAM_LAUNCHED();
+    k_fft_rows_c2r<KC><<<dim3(py, cbz), kFftThreads, sm, st>>>(L->d_w1, py, px, nz, 0, nz, P, lgP, Q, scale, out);
+    OAM_LAUNCHED();
+  }
   return OAM_OK;
 }
 
-oam_status oam::adjoint_fft(const oam_model *m, const float *s, float *H, cudaStream_t st) {
+oam_status run_fft_any(const oam_model *m, bool fwd, const float *in, float *out, cudaStream_t st) {
   const FftLayout *L = m->fft;
   if (!L) return OAM_ERR_UNSUPPORTED;
-  const int P = L->P, Q = L->Q, KC = L->KC, nz = m->grid.nz, py = m->grid.py, px = m->grid.px;
-  const size_t sm = fft_smem(P, KC);
-  oam_status rc;
-  if ((rc = set_smem((const void *)k_fft_rows_r2c, sm)) || (rc = set_smem((const void *)k_fft_cols, sm)) ||
-      (rc = set_smem((const void *)k_fft_rows_c2r, sm)))
-    return rc;
-  ProfScope prof(m, st, false);
-  const unsigned cbz = (unsigned)((nz + KC - 1) / KC), cbs = (unsigned)((L->NS + KC - 1) / KC);
-  k_fft_rows_r2c<<<dim3(py, cbs), kFftThreads, sm, st>>>(s, py, px, m->grid.nt, m->n_lo, L->NS, P, L->lgP, KC, Q,
-                                                         L->d_w2);
-  OAM_LAUNCHED();
-  k_fft_cols<<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, py, P, L->NS, P, L->lgP, KC, 0, L->d_w1);
-  OAM_LAUNCHED();
-  const size_t sa = sizeof(float2) * 4 * L->NS;
-  if ((rc = set_smem((const void *)k_fft_apply_adj, sa))) return rc;
-  k_fft_apply_adj<<<L->n_rep, kApplyThreads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
-                                                       L->d_koff, nz, m->n_lo, L->NS, L->d_w1, L->d_w2);
-  OAM_LAUNCHED();
-  k_fft_cols<<<dim3(Q, cbz), kFftThreads, sm, st>>>(L->d_w2, P, py, nz, P, L->lgP, KC, 1, L->d_w1);
-  OAM_LAUNCHED();
-  k_fft_rows_c2r<<<dim3(py, cbz), kFftThreads, sm, st>>>(L->d_w1, py, px, nz, 0, nz, P, L->lgP, KC, Q,
-                                                         1.0f / ((float)P * (float)P), H);
-  OAM_LAUNCHED();
-  return OAM_OK;
+  ProfScope prof(m, st, fwd);
+  switch (L->KC) {
+    case 16: return run_fft<16>(m, L, fwd, in, out, st);
+    case 8: return run_fft<8>(m, L, fwd, in, out, st);
+    case 4: return run_fft<4>(m, L, fwd, in, out, st);
+    default: return run_fft<2>(m, L, fwd, in, out, st);
+  }
+}
+
+}  // namespace
+
+oam_status oam::forward_fft(const oam_model *m, const float *H, float *s, cudaStream_t st) {
+  return run_fft_any(m, true, H, s, st);
+}
+
+oam_status oam::adjoint_fft(const oam_model *m, const float *s, float *H, cudaStream_t st) {
+  return run_fft_any(m, false, s, H, st);
 }

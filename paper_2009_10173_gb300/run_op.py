@@ -20,7 +20,7 @@ from .model import Model
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--op", default="forward", choices=["forward", "adjoint", "lsqr", "fista"])
-    p.add_argument("--prec", default="bf16x3", choices=["fp32", "bf16x3"])
+    p.add_argument("--prec", default="bf16x3", choices=["fp32", "bf16x3", "fft"])
     p.add_argument("--workload", default="volume_200x200x300", choices=sorted(configs.WORKLOADS))
     for k in ("px", "py", "nz", "nt", "win", "iters"):
         p.add_argument(f"--{k}", type=int, default=None)
@@ -29,7 +29,7 @@ def main():
     a = p.parse_args()
     over = {k: getattr(a, k) for k in ("px", "py", "nz", "nt", "win") if getattr(a, k) is not None}
     cfg = configs.scaled(configs.WORKLOADS[a.workload], **over)
-    prec = B.OAM_PREC_BF16X3 if a.prec == "bf16x3" else B.OAM_PREC_FP32
+    prec = {"bf16x3": B.OAM_PREC_BF16X3, "fp32": B.OAM_PREC_FP32, "fft": B.OAM_PREC_FFT}[a.prec]
     m = Model(cfg, precision=prec)
     H = torch.from_numpy(inputs.phantom(cfg, 1, count=20)).float().cuda()
     s = m.forward(H)
@@ -50,7 +50,7 @@ def main():
     print(json.dumps({"op": a.op, "prec": a.prec, "grid": [cfg["py"], cfg["px"], cfg["nz"], cfg["nt"], cfg["win"]],
                       "ms_per_call": ms, "flops_per_op": m.info.flops_per_op,
                       "alg_tflops": m.info.flops_per_op / ms / 1e9 if a.op in ("forward", "adjoint") else None,
-                      "model_bytes": m.info.device_bytes}))
+                      "model_bytes": m.info.device_bytes, "op_bytes": m.info.op_bytes}))
     m.close()
 
 
