@@ -59,7 +59,7 @@ struct FftLayout {
 namespace {
 
 constexpr int kFftThreads = 256;
-constexpr int kApplyMaxThreads = 512;
+constexpr int kApplyMaxThreads = 1024;
 constexpr int kBuildThreads = 128;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -77,21 +77,50 @@ __device__ __forceinline__ void load_twiddles(float2 *tw, int P) {
 
 // In-place radix-2 decimation-in-time transforms of KC interleaved lines of
 // P complex values (a[i * KC + c], loaded in bit-reversed order), sign -1
-// (forward) or +1 (inverse, unscaled).
+// (forward) or +1 (inverse, unscaled).  Two consecutive stages (spans h and
+// 2h) act on the same four elements {i, i+h, i+2h, i+3h}, so a thread runs
+// both in registers: one shared-memory pass per two stages (a leading single
+// stage when log2 P is odd).
 template <int KC>
-__device__ void fft_lines(float2 *a, const float2 *tw, int P, bool inverse) {
+__device__ void fft_lines(float2 *a, const float2 *tw, int P, int lgP, bool inverse) {
   __syncthreads();
-  const int nb = (P >> 1) * KC;
-  for (int half = 1, step = P >> 1; half < P; half <<= 1, step >>= 1) {
-    for (int id = threadIdx.x; id < nb; id += blockDim.x) {
+  int half = 1;
+  if (lgP & 1) {  // span-1 stage: twiddle 1
+    for (int id = threadIdx.x; id < (P >> 1) * KC; id += blockDim.x) {
+      const int c = id % KC, t = id / KC;
+      const float2 x0 = a[(2 * t) * KC + c], x1 = a[(2 * t + 1) * KC + c];
+      a[(2 * t) * KC + c] = make_float2(x0.x + x1.x, x0.y + x1.y);
+      a[(2 * t + 1) * KC + c] = make_float2(x0.x - x1.x, x0.y - x1.y);
+    }
+    __syncthreads();
+    half = 2;
+  }
+  const float sgn = inverse ? -1.0f : 1.0f;
+  for (; half < P; half <<= 2) {
+    const int s1 = P / (2 * half), s2 = P / (4 * half);  // twiddle strides of the two stages
+    for (int id = threadIdx.x; id < (P >> 2) * KC; id += blockDim.x) {
       const int c = id % KC, t = id / KC;
       const int q = t & (half - 1);
-      const int i0 = 2 * t - q, i1 = i0 + half;
-      float2 w = tw[q * step];
-      if (inverse) w.y = -w.y;
-      const float2 x0 = a[i0 * KC + c], y = cmul(a[i1 * KC + c], w);
+      const int i0 = 4 * (t - q) + q;
+      float2 x0 = a[i0 * KC + c], x1 = a[(i0 + half) * KC + c];
+      float2 x2 = a[(i0 + 2 * half) * KC + c], x3 = a[(i0 + 3 * half) * KC + c];
+      float2 w = tw[q * s1];
+      w.y *= sgn;
+      float2 y = cmul(x1, w);
+      x1 = make_float2(x0.x - y.x, x0.y - y.y);
+      x0 = make_float2(x0.x + y.x, x0.y + y.y);
+      y = cmul(x3, w);
+      x3 = make_float2(x2.x - y.x, x2.y - y.y);
+      x2 = make_float2(x2.x + y.x, x2.y + y.y);
+      float2 wa = tw[q * s2], wb = tw[(q + half) * s2];
+      wa.y *= sgn;
+      wb.y *= sgn;
+      y = cmul(x2, wa);
       a[i0 * KC + c] = make_float2(x0.x + y.x, x0.y + y.y);
-      a[i1 * KC + c] = make_float2(x0.x - y.x, x0.y - y.y);
+      a[(i0 + 2 * half) * KC + c] = make_float2(x0.x - y.x, x0.y - y.y);
+      y = cmul(x3, wb);
+      a[(i0 + half) * KC + c] = make_float2(x1.x + y.x, x1.y + y.y);
+      a[(i0 + 3 * half) * KC + c] = make_float2(x1.x - y.x, x1.y - y.y);
     }
     __syncthreads();
   }
@@ -115,7 +144,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_r2c(const float *__res
     if (x < px && cb + c < C) v = X[((size_t)y * px + x) * Ctot + c0 + cb + c];
     a[bitrev(x, lgP) * KC + c] = make_float2(v, 0.0f);
   }
-  fft_lines<KC>(a, tw, P, false);
+  fft_lines<KC>(a, tw, P, lgP, false);
   for (int i = threadIdx.x; i < Q * KC; i += blockDim.x) {
     const int u = i / KC, c = i % KC;
     if (cb + c < C) Y[((size_t)u * py + y) * C + cb + c] = a[u * KC + c];
@@ -137,7 +166,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(const float2 *__restri
     if (r < nin && cb + c < C) v = Z[((size_t)u * nin + r) * C + cb + c];
     a[bitrev(r, lgP) * KC + c] = v;
   }
-  fft_lines<KC>(a, tw, P, inverse != 0);
+  fft_lines<KC>(a, tw, P, lgP, inverse != 0);
   for (int i = threadIdx.x; i < nout * KC; i += blockDim.x) {
     const int r = i / KC, c = i % KC;
     if (cb + c < C) W[((size_t)u * nout + r) * C + cb + c] = a[r * KC + c];
@@ -176,7 +205,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_c2r(const float2 *__re
     }
     a[bitrev(f, lgP) * KC + c] = v;
   }
-  fft_lines<KC>(a, tw, P, true);
+  fft_lines<KC>(a, tw, P, lgP, true);
   for (int i = threadIdx.x; i < px * KC; i += blockDim.x) {
     const int x = i / KC, c = i % KC;
     const int oc = ob + c, zc = oc - c0;
@@ -212,11 +241,11 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_fwd(const float 
   }
   __syncthreads();
   const float *row = shat + (size_t)r * row_len;
-  const int lane = threadIdx.x & 31;
-  // every lane of a warp walks the same depths (coalesced row reads); a lane
-  // whose sample lies outside a depth's band reads nothing there
-  for (int j0 = threadIdx.x - lane; j0 < NS; j0 += blockDim.x) {
-    const int j = j0 + lane;
+  const int lane = threadIdx.x & 31, sub = lane & 15, ph = lane >> 4;
+  // a warp serves 16 samples; its two half-warps walk alternate depths of the
+  // warp's common depth range (coalesced row reads), then add their sums
+  for (int g0 = (threadIdx.x >> 5) * 16; g0 < NS; g0 += (blockDim.x >> 5) * 16) {
+    const int j = g0 + sub;
     const bool live = j < NS;
     const int n = n_lo + j;
     const int2 kr = live ? krange[j] : make_int2(nz, 0);
@@ -224,17 +253,17 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_fwd(const float 
     float acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
-    int k = k0;
-    for (; k + 4 <= k1; k += 4) {
+    int k = k0 + ph;
+    for (; k + 6 < k1; k += 8) {
       float sv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int d = n - s_lo[k + q];
-        sv[q] = (live && (unsigned)d < (unsigned)s_len[k + q]) ? __ldg(row + s_off[k + q] + d) : 0.0f;
+        const int kk = k + 2 * q, d = n - s_lo[kk];
+        sv[q] = (live && (unsigned)d < (unsigned)s_len[kk]) ? __ldg(row + s_off[kk] + d) : 0.0f;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float4 a = Hs[2 * (k + q)], b = Hs[2 * (k + q) + 1];
+        const float4 a = Hs[2 * (k + 2 * q)], b = Hs[2 * (k + 2 * q) + 1];
         acc[0] = fmaf(sv[q], a.x, acc[0]);
         acc[1] = fmaf(sv[q], a.y, acc[1]);
         acc[2] = fmaf(sv[q], a.z, acc[2]);
@@ -245,7 +274,7 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_fwd(const float 
         acc[7] = fmaf(sv[q], b.w, acc[7]);
       }
     }
-    for (; k < k1; ++k) {
+    for (; k < k1; k += 2) {
       const int d = n - s_lo[k];
       const float sv = (live && (unsigned)d < (unsigned)s_len[k]) ? __ldg(row + s_off[k] + d) : 0.0f;
       const float4 a = Hs[2 * k], b = Hs[2 * k + 1];
@@ -258,7 +287,9 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_fwd(const float 
       acc[6] = fmaf(sv, b.z, acc[6]);
       acc[7] = fmaf(sv, b.w, acc[7]);
     }
-    if (!live) continue;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 16);
+    if (!live || ph != 0) continue;
     if (mem.x >= 0) sh[(size_t)mem.x * NS + j] = make_float2(acc[0], acc[1]);
     if (mem.y >= 0) sh[(size_t)mem.y * NS + j] = make_float2(acc[2], acc[3]);
     if (mem.z >= 0) sh[(size_t)mem.z * NS + j] = make_float2(acc[4], acc[5]);
@@ -295,26 +326,29 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_adj(const float 
   }
   __syncthreads();
   const float *row = shat_t + (size_t)r * row_len_t;
-  const int lane = threadIdx.x & 31;
-  for (int k0 = threadIdx.x - lane; k0 < nz; k0 += blockDim.x) {
-    const int k = k0 + lane;
+  const int lane = threadIdx.x & 31, sub = lane & 15, ph = lane >> 4;
+  // a warp serves 16 depths; its two half-warps walk alternate samples of the
+  // warp's common sample range (coalesced reads), then add their sums
+  for (int g0 = (threadIdx.x >> 5) * 16; g0 < nz; g0 += (blockDim.x >> 5) * 16) {
+    const int k = g0 + sub;
     const bool live = k < nz && klen[k] > 0;
     const int lo = live ? klo[k] - n_lo : NS, hi = live ? klo[k] - n_lo + klen[k] : 0;
     const int j0 = __reduce_min_sync(0xffffffffu, lo), j1 = __reduce_max_sync(0xffffffffu, hi);
     float acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
-    int j = j0;
-    for (; j + 4 <= j1; j += 4) {  // four samples' loads in flight, then their products
+    int j = j0 + ph;
+    for (; j + 6 < j1; j += 8) {
       float sv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int2 kr = s_kr[j + q];
-        sv[q] = (k >= kr.x && k < kr.y) ? __ldg(row + s_no[j + q] + (k - kr.x)) : 0.0f;
+        const int jj = j + 2 * q;
+        const int2 kr = s_kr[jj];
+        sv[q] = (k >= kr.x && k < kr.y) ? __ldg(row + s_no[jj] + (k - kr.x)) : 0.0f;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float4 a = Ss[2 * (j + q)], b = Ss[2 * (j + q) + 1];
+        const float4 a = Ss[2 * (j + 2 * q)], b = Ss[2 * (j + 2 * q) + 1];
         acc[0] = fmaf(sv[q], a.x, acc[0]);
         acc[1] = fmaf(sv[q], a.y, acc[1]);
         acc[2] = fmaf(sv[q], a.z, acc[2]);
@@ -325,7 +359,7 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_adj(const float 
         acc[7] = fmaf(sv[q], b.w, acc[7]);
       }
     }
-    for (; j < j1; ++j) {
+    for (; j < j1; j += 2) {
       const int2 kr = s_kr[j];
       const float sv = (k >= kr.x && k < kr.y) ? __ldg(row + s_no[j] + (k - kr.x)) : 0.0f;
       const float4 a = Ss[2 * j], b = Ss[2 * j + 1];
@@ -338,7 +372,9 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_adj(const float 
       acc[6] = fmaf(sv, b.z, acc[6]);
       acc[7] = fmaf(sv, b.w, acc[7]);
     }
-    if (k >= nz) continue;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 16);
+    if (k >= nz || ph != 0) continue;
     if (mem.x >= 0) Hh[(size_t)mem.x * nz + k] = make_float2(acc[0], acc[1]);
     if (mem.y >= 0) Hh[(size_t)mem.y * nz + k] = make_float2(acc[2], acc[3]);
     if (mem.z >= 0) Hh[(size_t)mem.z * nz + k] = make_float2(acc[4], acc[5]);
@@ -613,7 +649,8 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     return rc;
   const unsigned cbz = (unsigned)((nz + KC - 1) / KC), cbs = (unsigned)((NS + KC - 1) / KC);
   const float scale = 1.0f / ((float)P * (float)P);
-  const int apply_threads = std::min(kApplyMaxThreads, ((fwd ? NS : nz) + 31) & ~31);
+  // one warp per 16 samples (forward) or depths (adjoint)
+  const int apply_threads = std::min(kApplyMaxThreads, 32 * (((fwd ? NS : nz) + 15) / 16));
   if (fwd) {
     k_fft_rows_r2c<KC><<<dim3(py, cbz), kFftThreads, sm, st>>>(in, py, px, nz, 0, nz, P, lgP, Q, L->d_w2);
     OAM_LAUNCHED();
