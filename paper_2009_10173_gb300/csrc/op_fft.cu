@@ -60,6 +60,9 @@ namespace {
 
 constexpr int kFftThreads = 256;
 constexpr int kApplyMaxThreads = 1024;
+constexpr int kUnroll = 8;  // spectral products: independent row loads per lane in flight
+constexpr int kFwdPhases = 2;  // forward products: lane groups of a warp that walk interleaved depths
+constexpr int kFwdChunk = 128;  // forward products: samples per block (0: all samples of the orbit)
 constexpr int kBuildThreads = 128;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -241,12 +244,15 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_fwd(const float 
   }
   __syncthreads();
   const float *row = shat + (size_t)r * row_len;
-  const int lane = threadIdx.x & 31, sub = lane & 15, ph = lane >> 4;
-  // a warp serves 16 samples; its two half-warps walk alternate depths of the
-  // warp's common depth range (coalesced row reads), then add their sums
-  for (int g0 = (threadIdx.x >> 5) * 16; g0 < NS; g0 += (blockDim.x >> 5) * 16) {
+  constexpr int kLanes = 32 / kFwdPhases;  // samples per warp
+  const int lane = threadIdx.x & 31, sub = lane % kLanes, ph = lane / kLanes;
+  const int jb = kFwdChunk > 0 ? blockIdx.y * kFwdChunk : 0;
+  const int je = kFwdChunk > 0 ? min(NS, jb + kFwdChunk) : NS;
+  // a warp serves kLanes samples; its lane groups walk interleaved depths of
+  // the warp's common depth range (coalesced row reads), then add their sums
+  for (int g0 = jb + (threadIdx.x >> 5) * kLanes; g0 < je; g0 += (blockDim.x >> 5) * kLanes) {
     const int j = g0 + sub;
-    const bool live = j < NS;
+    const bool live = j < je;
     const int n = n_lo + j;
     const int2 kr = live ? krange[j] : make_int2(nz, 0);
     const int k0 = __reduce_min_sync(0xffffffffu, kr.x), k1 = __reduce_max_sync(0xffffffffu, kr.y);
@@ -254,16 +260,16 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_fwd(const float 
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
     int k = k0 + ph;
-    for (; k + 6 < k1; k += 8) {
-      float sv[4];
+    for (; k + kFwdPhases * (kUnroll - 1) < k1; k += kFwdPhases * kUnroll) {  // kUnroll loads in flight per lane
+      float sv[kUnroll];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int kk = k + 2 * q, d = n - s_lo[kk];
+      for (int q = 0; q < kUnroll; ++q) {
+        const int kk = k + kFwdPhases * q, d = n - s_lo[kk];
         sv[q] = (live && (unsigned)d < (unsigned)s_len[kk]) ? __ldg(row + s_off[kk] + d) : 0.0f;
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 a = Hs[2 * (k + 2 * q)], b = Hs[2 * (k + 2 * q) + 1];
+      for (int q = 0; q < kUnroll; ++q) {
+        const float4 a = Hs[2 * (k + kFwdPhases * q)], b = Hs[2 * (k + kFwdPhases * q) + 1];
         acc[0] = fmaf(sv[q], a.x, acc[0]);
         acc[1] = fmaf(sv[q], a.y, acc[1]);
         acc[2] = fmaf(sv[q], a.z, acc[2]);
@@ -274,7 +280,7 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_fwd(const float 
         acc[7] = fmaf(sv[q], b.w, acc[7]);
       }
     }
-    for (; k < k1; k += 2) {
+    for (; k < k1; k += kFwdPhases) {
       const int d = n - s_lo[k];
       const float sv = (live && (unsigned)d < (unsigned)s_len[k]) ? __ldg(row + s_off[k] + d) : 0.0f;
       const float4 a = Hs[2 * k], b = Hs[2 * k + 1];
@@ -288,7 +294,9 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_fwd(const float 
       acc[7] = fmaf(sv, b.w, acc[7]);
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 16);
+    for (int off = 16; off >= kLanes; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
     if (!live || ph != 0) continue;
     if (mem.x >= 0) sh[(size_t)mem.x * NS + j] = make_float2(acc[0], acc[1]);
     if (mem.y >= 0) sh[(size_t)mem.y * NS + j] = make_float2(acc[2], acc[3]);
@@ -338,16 +346,16 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_adj(const float 
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
     int j = j0 + ph;
-    for (; j + 6 < j1; j += 8) {
-      float sv[4];
+    for (; j + 2 * (kUnroll - 1) < j1; j += 2 * kUnroll) {  // kUnroll loads in flight per lane
+      float sv[kUnroll];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < kUnroll; ++q) {
         const int jj = j + 2 * q;
         const int2 kr = s_kr[jj];
         sv[q] = (k >= kr.x && k < kr.y) ? __ldg(row + s_no[jj] + (k - kr.x)) : 0.0f;
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < kUnroll; ++q) {
         const float4 a = Ss[2 * (j + 2 * q)], b = Ss[2 * (j + 2 * q) + 1];
         acc[0] = fmaf(sv[q], a.x, acc[0]);
         acc[1] = fmaf(sv[q], a.y, acc[1]);
@@ -658,7 +666,9 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     OAM_LAUNCHED();
     const size_t sa = sizeof(float4) * 2 * nz + sizeof(int) * (2 * nz + 2) + sizeof(long long) * nz;
     if ((rc = set_smem((const void *)k_fft_apply_fwd, sa))) return rc;
-    k_fft_apply_fwd<<<L->n_rep, apply_threads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
+    const int fchunk = kFwdChunk > 0 ? kFwdChunk : NS;
+    const int fwd_threads = std::min(kApplyMaxThreads, 32 * ((fchunk + 32 / kFwdPhases - 1) / (32 / kFwdPhases)));
+    k_fft_apply_fwd<<<dim3(L->n_rep, (NS + fchunk - 1) / fchunk), fwd_threads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
                                                          L->d_koff, L->d_krange, nz, m->n_lo, NS, L->d_w1, L->d_w2);
     OAM_LAUNCHED();
     k_fft_cols<KC><<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, P, py, NS, P, lgP, 1, L->d_w1);

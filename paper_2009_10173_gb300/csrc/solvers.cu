@@ -105,26 +105,49 @@ __global__ void k_init_scalars(Scalars *S, double damp, double t, double L, doub
   S->ticket = 0;
 }
 
+// Element loops: every vector the solvers touch is 16-byte aligned, so
+// threads stride over float4 groups; the last n % 4 elements go to the first
+// threads of the grid.  A group's squares are summed in FP32 (four positive
+// terms) and added to the thread's FP64 accumulator.
+#define OAM_GROUPS(g, n4) \
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < (n4); g += (size_t)gridDim.x * blockDim.x)
+#define OAM_TAIL(i, n) \
+  for (size_t i = ((n) & ~size_t(3)) + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (n); \
+       i += (size_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ float sq4(float4 v) { return v.x * v.x + v.y * v.y + (v.z * v.z + v.w * v.w); }
+__device__ __forceinline__ float4 ld4(const float *p, size_t g) { return reinterpret_cast<const float4 *>(p)[g]; }
+__device__ __forceinline__ void st4(float *p, size_t g, float4 v) { reinterpret_cast<float4 *>(p)[g] = v; }
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float4 mul4(float4 x, float a) { return make_float4(x.x * a, x.y * a, x.z * a, x.w * a); }
+
 __global__ void k_fill(float *x, size_t n, float v) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) x[i] = v;
+  OAM_GROUPS(g, n / 4) st4(x, g, make_float4(v, v, v, v));
+  OAM_TAIL(i, n) x[i] = v;
 }
 
 // dst = src * (*scale); skipped when the iteration is past a stop.
 __global__ void k_scale(float *dst, const float *src, size_t n, const double *scale, const Scalars *S, int it) {
   if (S && it > S->stop_at) return;
   const float f = (float)*scale;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = src[i] * f;
+  OAM_GROUPS(g, n / 4) st4(dst, g, mul4(ld4(src, g), f));
+  OAM_TAIL(i, n) dst[i] = src[i] * f;
 }
 
 // ------------------------------------------------------------------ LSQR
+// sum of squares of x (FP32 groups, FP64 across groups)
+__device__ __forceinline__ double sumsq(const float *x, size_t n) {
+  double acc = 0;
+  OAM_GROUPS(g, n / 4) acc += (double)sq4(ld4(x, g));
+  OAM_TAIL(i, n) acc += (double)(x[i] * x[i]);
+  return acc;
+}
+
 // beta_1 = ||s||
 __global__ void k_lsqr_beta0(const float *s, size_t n, Scalars *S) {
-  double acc = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float v = s[i];
-    acc += (double)(v * v);
-  }
+  const double acc = sumsq(s, n);
   double ta, tb;
   if (finish_blocks<false>(S, acc, 0.0, &ta, &tb) && threadIdx.x == 0) {
     S->beta = sqrt(ta);
@@ -136,11 +159,7 @@ __global__ void k_lsqr_beta0(const float *s, size_t n, Scalars *S) {
 
 // alpha_1 = ||A^T u_1||, rhobar = alpha, phibar = beta
 __global__ void k_lsqr_alpha0(const float *th, size_t n, Scalars *S) {
-  double acc = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float v = th[i];
-    acc += (double)(v * v);
-  }
+  const double acc = sumsq(th, n);
   double ta, tb;
   if (finish_blocks<false>(S, acc, 0.0, &ta, &tb) && threadIdx.x == 0) {
     S->alpha = sqrt(ta);
@@ -156,7 +175,13 @@ __global__ void k_lsqr_alpha0(const float *th, size_t n, Scalars *S) {
 // v = th / alpha, w = v, x = 0
 __global__ void k_lsqr_vw0(const float *th, float *v, float *w, float *x, size_t n, const Scalars *S) {
   const float ia = (float)S->inv_alpha;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  OAM_GROUPS(g, n / 4) {
+    const float4 t = mul4(ld4(th, g), ia);
+    st4(v, g, t);
+    st4(w, g, t);
+    st4(x, g, make_float4(0.f, 0.f, 0.f, 0.f));
+  }
+  OAM_TAIL(i, n) {
     const float t = th[i] * ia;
     v[i] = t;
     w[i] = t;
@@ -169,7 +194,12 @@ __global__ void k_lsqr_u(const float *ts, float *u, size_t n, Scalars *S, int it
   if (it > S->stop_at) return;
   const float al = (float)S->alpha;
   double acc = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  OAM_GROUPS(g, n / 4) {
+    const float4 v = fma4(-al, ld4(u, g), ld4(ts, g));
+    st4(u, g, v);
+    acc += (double)sq4(v);
+  }
+  OAM_TAIL(i, n) {
     const float v = fmaf(-al, u[i], ts[i]);
     u[i] = v;
     acc += (double)(v * v);
@@ -188,7 +218,12 @@ __global__ void k_lsqr_v(const float *th, float *v, size_t n, Scalars *S, int it
   if (it > S->stop_at) return;
   const float be = (float)S->beta;
   double acc = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  OAM_GROUPS(g, n / 4) {
+    const float4 t = fma4(-be, ld4(v, g), ld4(th, g));
+    st4(v, g, t);
+    acc += (double)sq4(t);
+  }
+  OAM_TAIL(i, n) {
     const float t = fmaf(-be, v[i], th[i]);
     v[i] = t;
     acc += (double)(t * t);
@@ -223,7 +258,13 @@ __global__ void k_lsqr_v(const float *th, float *v, size_t n, Scalars *S, int it
 __global__ void k_lsqr_xw(float *v, float *w, float *x, size_t n, const Scalars *S, int it) {
   if (it > S->stop_at) return;
   const float ia = (float)S->inv_alpha, cx = (float)S->cx, cw = (float)S->cw;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  OAM_GROUPS(g, n / 4) {
+    const float4 vv = mul4(ld4(v, g), ia), ww = ld4(w, g);
+    st4(x, g, fma4(cx, ww, ld4(x, g)));
+    st4(w, g, fma4(-cw, ww, vv));
+    st4(v, g, vv);
+  }
+  OAM_TAIL(i, n) {
     const float vv = v[i] * ia;
     const float ww = w[i];
     x[i] = fmaf(cx, ww, x[i]);
@@ -235,12 +276,7 @@ __global__ void k_lsqr_xw(float *v, float *w, float *x, size_t n, const Scalars 
 // ------------------------------------------------------------------ FISTA
 // mu = ||A^T A v|| / ||v||, inv_norm = 1 / ||A^T A v||
 __global__ void k_power_norms(const float *th, const float *v, size_t n, Scalars *S) {
-  double a = 0, b = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float p = th[i], q = v[i];
-    a += (double)(p * p);
-    b += (double)(q * q);
-  }
+  const double a = sumsq(th, n), b = sumsq(v, n);
   double ta, tb;
   if (finish_blocks<false>(S, a, b, &ta, &tb) && threadIdx.x == 0) {
     const double nt = sqrt(ta), nv = sqrt(tb);
@@ -252,17 +288,27 @@ __global__ void k_power_norms(const float *th, const float *v, size_t n, Scalars
 
 // lambda = lambda_rel * max |A^T s|
 __global__ void k_lambda_rel(const float *th, size_t n, Scalars *S, double lambda_rel) {
-  double m = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    m = fmax(m, (double)fabsf(th[i]));
+  float m = 0.0f;
+  OAM_GROUPS(g, n / 4) {
+    const float4 v = ld4(th, g);
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  OAM_TAIL(i, n) m = fmaxf(m, fabsf(th[i]));
   double ta, tb;
-  if (finish_blocks<true>(S, m, 0.0, &ta, &tb) && threadIdx.x == 0) S->lambda = lambda_rel * ta;
+  if (finish_blocks<true>(S, (double)m, 0.0, &ta, &tb) && threadIdx.x == 0) S->lambda = lambda_rel * ta;
 }
 
 // r = A Y - s
 __global__ void k_sub(float *r, const float *s, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    r[i] -= s[i];
+  OAM_GROUPS(g, n / 4) {
+    const float4 a = ld4(r, g), b = ld4(s, g);
+    st4(r, g, make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w));
+  }
+  OAM_TAIL(i, n) r[i] -= s[i];
+}
+
+__device__ __forceinline__ float prox(float z, float thr, int nonneg) {
+  return nonneg ? fmaxf(z - thr, 0.0f) : copysignf(fmaxf(fabsf(z) - thr, 0.0f), z);
 }
 
 // x_new = prox(Y - (2/L) g, lambda/L); Y = x_new + ((t-1)/t') (x_new - x); x = x_new; t = t'
@@ -271,13 +317,17 @@ __global__ void k_fista_step(const float *g, float *Y, float *x, size_t n, Scala
   const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
   const float mom = (float)((t - 1.0) / tn);
   const float step = (float)(2.0 / S->L), thr = (float)(S->lambda / S->L);
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  OAM_GROUPS(q, n / 4) {
+    const float4 z = fma4(-step, ld4(g, q), ld4(Y, q)), xo = ld4(x, q);
+    const float4 xn = make_float4(prox(z.x, thr, nonneg), prox(z.y, thr, nonneg), prox(z.z, thr, nonneg),
+                                  prox(z.w, thr, nonneg));
+    st4(Y, q, make_float4(fmaf(mom, xn.x - xo.x, xn.x), fmaf(mom, xn.y - xo.y, xn.y), fmaf(mom, xn.z - xo.z, xn.z),
+                          fmaf(mom, xn.w - xo.w, xn.w)));
+    st4(x, q, xn);
+  }
+  OAM_TAIL(i, n) {
     const float z = fmaf(-step, g[i], Y[i]);
-    float xn;
-    if (nonneg)
-      xn = fmaxf(z - thr, 0.0f);
-    else
-      xn = copysignf(fmaxf(fabsf(z) - thr, 0.0f), z);
+    const float xn = prox(z, thr, nonneg);
     const float xo = x[i];
     Y[i] = fmaf(mom, xn - xo, xn);
     x[i] = xn;
@@ -289,12 +339,19 @@ __global__ void k_fista_step(const float *g, float *Y, float *x, size_t n, Scala
 // objective pieces: sum (A x - s)^2 over signals, sum |x| over the volume
 __global__ void k_objective(const float *ax, const float *s, size_t ns, const float *x, size_t nv, Scalars *S) {
   double a = 0, b = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ns; i += (size_t)gridDim.x * blockDim.x) {
+  OAM_GROUPS(g, ns / 4) {
+    const float4 p = ld4(ax, g), q = ld4(s, g);
+    a += (double)sq4(make_float4(p.x - q.x, p.y - q.y, p.z - q.z, p.w - q.w));
+  }
+  OAM_TAIL(i, ns) {
     const float r = ax[i] - s[i];
     a += (double)(r * r);
   }
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nv; i += (size_t)gridDim.x * blockDim.x)
-    b += (double)fabsf(x[i]);
+  OAM_GROUPS(g, nv / 4) {
+    const float4 v = ld4(x, g);
+    b += (double)(fabsf(v.x) + fabsf(v.y) + (fabsf(v.z) + fabsf(v.w)));
+  }
+  OAM_TAIL(i, nv) b += (double)fabsf(x[i]);
   double ta, tb;
   if (finish_blocks<false>(S, a, b, &ta, &tb) && threadIdx.x == 0) {
     S->sum_a = ta;
@@ -319,8 +376,8 @@ WorkLayout layout(const oam_model *m) {
   return L;
 }
 
-int red_grid(const oam_model *m) { return std::min(kRedBlocks, 2 * std::max(1, m->sm_count)); }
-int vec_grid(const oam_model *m) { return 4 * std::max(1, m->sm_count); }
+int red_grid(const oam_model *m) { return std::min(kRedBlocks, 4 * std::max(1, m->sm_count)); }
+int vec_grid(const oam_model *m) { return 8 * std::max(1, m->sm_count); }
 
 }  // namespace
 
