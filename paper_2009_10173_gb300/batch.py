@@ -82,9 +82,12 @@ def main():
     p.add_argument("--jobs", type=int, default=16)
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=1)
+    p.add_argument("--prec", default="bf16x3", choices=["bf16x3", "fft", "fp32"],
+                   help="operator form: split-BF16 tensor cores, FP32 lateral-FFT form, or plain FP32")
     a = p.parse_args()
-    cfgs, signals = prepare(configs.batch_workload(a.jobs))
-    batch = Batch(cfgs, signals)
+    prec = {"bf16x3": B.OAM_PREC_BF16X3, "fft": B.OAM_PREC_FFT, "fp32": B.OAM_PREC_FP32}[a.prec]
+    cfgs, signals = prepare(configs.batch_workload(a.jobs), prec)
+    batch = Batch(cfgs, signals, precision=prec, autotune=(prec == B.OAM_PREC_BF16X3))
     for _ in range(a.warmup):
         batch.run()
     torch.cuda.synchronize()
@@ -98,6 +101,7 @@ def main():
     flops = sum((1 + 2 * c["lsqr_iters"] + 2 * c["power_iters"] + 1 + 2 * c["fista_iters"]) *
                 c["_model"].info.flops_per_op for c in cfgs)
     print(json.dumps({"workload": f"batch of {a.jobs} uneven reconstructions (30 LSQR + 50 FISTA each)",
+                      "prec": a.prec,
                       "ms_per_batch": ms, "volumes_per_s": a.jobs / (ms / 1e3),
                       "op_tflops_algorithmic": flops / (ms * 1e-3) / 1e12,
                       "jobs": [[c["py"], c["px"], c["nz"], c["nt"], round(c["focal_m"] * 1e3, 2),

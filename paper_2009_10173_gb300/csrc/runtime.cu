@@ -239,6 +239,13 @@ size_t footprint_estimate(const oam_server_opts &o, const oam_grid &g) {
     model += (R + 1) * (size_t)g.px * g.py * 512 * sizeof(float);   // per-|b| partial sums
     model += (size_t)(g.py + 2 * R + 2) * (g.px + R) * 512 * sizeof(float);  // staged input
   }
+  if (o.precision == OAM_PREC_FFT) {
+    size_t P = 2;
+    while (P < (size_t)std::max(g.py, g.px) + R) P <<= 1;
+    const size_t Q = P / 2 + 1, reps = Q * (Q + 1) / 2;
+    model += 2 * reps * g.nz * 256 * sizeof(float);                 // spectral slab, two orders (union bands <= 256)
+    model += 2 * Q * P * (size_t)std::max(g.nz, g.nt) * 8;          // complex work buffers
+  }
   const size_t work = 256 * 1024 + 2 * sig_bytes(g) + 3 * vol_bytes(g);
   return model + sig_bytes(g) + 2 * vol_bytes(g) + work;
 }

@@ -35,27 +35,143 @@ __device__ __forceinline__ double delta_dist(const Geo &g, int b, int a, int k, 
   return __ddiv_rn(num, __dadd_rn(d, g.F));
 }
 
-// Per (orbit, depth): min and max of d - F over the patches.
-__global__ void k_delta_range(Geo g, const Patch *__restrict__ patch, int M, const int *orb_b,
-                              const int *orb_a, int nz, double2 *out) {
+// ---------------------------------------------------------------- double-word FP32
+// A pair (h, l) of floats with |l| <= ulp(h)/2 carries about 48 significand
+// bits, enough for patch arrivals to 1e-11 samples, at FP32 instruction rates
+// (this GPU's FP64 rate is far lower).  Error-free transforms and the add,
+// multiply, divide and square-root steps follow Joldes, Muller and Popescu,
+// "Tight and rigorous error bounds for basic building blocks of double-word
+// arithmetic" (ACM TOMS 2017); the _rn intrinsics keep the compiler from
+// contracting or reordering them.
+struct DW {
+  float h, l;
+};
+__device__ __forceinline__ DW fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DW two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), ap = __fsub_rn(s, b), bp = __fsub_rn(s, ap);
+  return {s, __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp))};
+}
+__device__ __forceinline__ DW two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DW dw_add(DW x, DW y) {
+  const DW s = two_sum(x.h, y.h), t = two_sum(x.l, y.l);
+  const DW v = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+  return fast_two_sum(v.h, __fadd_rn(t.l, v.l));
+}
+__device__ __forceinline__ DW dw_mul(DW x, DW y) {
+  const DW c = two_prod(x.h, y.h);
+  const float t = __fmaf_rn(x.l, y.h, __fmaf_rn(x.h, y.l, __fmul_rn(x.l, y.l)));
+  return fast_two_sum(c.h, __fadd_rn(c.l, t));
+}
+__device__ __forceinline__ DW dw_mul_f(DW x, float y) {
+  const DW c = two_prod(x.h, y);
+  const DW t = fast_two_sum(c.h, __fmul_rn(x.l, y));
+  return fast_two_sum(t.h, __fadd_rn(t.l, c.l));
+}
+__device__ __forceinline__ DW dw_div(DW x, DW y) {
+  const float th = __fdiv_rn(x.h, y.h);
+  const DW r = dw_mul_f(y, th);
+  const float d = __fadd_rn(__fsub_rn(x.h, r.h), __fsub_rn(x.l, r.l));
+  return fast_two_sum(th, __fdiv_rn(d, y.h));
+}
+__device__ __forceinline__ DW dw_sqrt(DW x) {  // x > 0: one Newton step from the FP32 root
+  const float s = __fsqrt_rn(x.h);
+  const float e = __fadd_rn(__fmaf_rn(-s, s, x.h), x.l);
+  return fast_two_sum(s, __fdiv_rn(e, __fmul_rn(2.0f, s)));
+}
+__device__ __forceinline__ DW to_dw(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
+// Patch normal as double words and weight in mm^2 per metre of distance.
+struct __align__(32) PatchDW {
+  float xh, xl, yh, yl, zh, zl, w, pad;
+};
+
+__global__ void k_patch_dw(const Patch *__restrict__ patch, int M, PatchDW *__restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    const Patch p = patch[j];
+    const DW x = to_dw(p.x), y = to_dw(p.y), z = to_dw(p.z);
+    out[j] = PatchDW{x.h, x.l, y.h, y.l, z.h, z.l, (float)(p.w * 1e-3), 0.0f};
+  }
+}
+
+// d - F in plain FP32 (same cancellation-free form).  Its error is below
+// 4e-7 |r|, r the voxel offset (|d - F| <= |r|).
+__device__ __forceinline__ float delta_dist_f(float rx, float ry, float rz, float r2, float F, const PatchDW &p) {
+  const float rn = rx * p.xh + ry * p.yh + rz * p.zh;
+  const float num = 2.0f * F * rn + r2;
+  const float d = sqrtf(F * F + num);
+  return num / (d + F);
+}
+
+template <bool kMax>
+__device__ __forceinline__ float block_ext(float v, float *sh) {
+  for (int off = 16; off; off >>= 1) {
+    const float o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = kMax ? fmaxf(v, o) : fminf(v, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = sh[0];
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) v = kMax ? fmaxf(v, sh[i]) : fminf(v, sh[i]);
+  return v;
+}
+
+// Per (orbit, depth): min and max of d - F over the patches, exactly as FP64
+// evaluates them.  Plain FP32 distances locate the extremes; only patches
+// within 1e-5 |r| of the FP32 extremes (a bound 25x the FP32 error) are
+// evaluated in FP64, so the true FP64 extremes are always among them.
+__global__ void k_delta_range(Geo g, const Patch *__restrict__ patch, const PatchDW *__restrict__ pdw, int M,
+                              const int *orb_b, const int *orb_a, int nz, double2 *out) {
+  __shared__ float shf[32];
+  __shared__ double slo[32], shi[32];
   const int o = blockIdx.x, k = blockIdx.y;
   const int b = orb_b[o], a = orb_a[o];
+  const double rxd = a * g.dx, ryd = b * g.dy, rzd = g.z0 + k * g.dz;
+  const float rx = (float)rxd, ry = (float)ryd, rz = (float)rzd;
+  const float r2 = (float)(rxd * rxd + ryd * ryd + rzd * rzd), F = (float)g.F;
+  float lo32 = INFINITY, hi32 = -INFINITY;
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    const float dd = delta_dist_f(rx, ry, rz, r2, F, pdw[j]);
+    lo32 = fminf(lo32, dd);
+    hi32 = fmaxf(hi32, dd);
+  }
+  lo32 = block_ext<false>(lo32, shf);
+  hi32 = block_ext<true>(hi32, shf);
+  const float tol = 1e-5f * sqrtf(r2);
   double lo = INFINITY, hi = -INFINITY;
   for (int j = threadIdx.x; j < M; j += blockDim.x) {
-    double dd = delta_dist(g, b, a, k, patch[j]);
-    lo = fmin(lo, dd);
-    hi = fmax(hi, dd);
+    const float dd = delta_dist_f(rx, ry, rz, r2, F, pdw[j]);
+    if (dd <= lo32 + tol || dd >= hi32 - tol) {
+      const double d64 = delta_dist(g, b, a, k, patch[j]);
+      if (dd <= lo32 + tol) lo = fmin(lo, d64);
+      if (dd >= hi32 - tol) hi = fmax(hi, d64);
+    }
   }
   for (int off = 16; off; off >>= 1) {
     lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
     hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
   }
-  __shared__ double slo[32], shi[32];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { slo[w] = lo; shi[w] = hi; }
+  if (l == 0) {
+    slo[w] = lo;
+    shi[w] = hi;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) { lo = fmin(lo, slo[i]); hi = fmax(hi, shi[i]); }
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      lo = fmin(lo, slo[i]);
+      hi = fmax(hi, shi[i]);
+    }
     out[o * nz + k] = make_double2(lo, hi);
   }
 }
@@ -63,34 +179,41 @@ __global__ void k_delta_range(Geo g, const Patch *__restrict__ patch, int M, con
 constexpr int kPatchChunk = 512;
 
 // Band values: thread i of block (o, k) owns sample lo + i (+ blockDim.x ...).
-// Each patch's arrival d (samples, FP64) is split into an integer part and an
-// FP32 fraction, so tau = (n - floor d) - frac(d) is the FP32 rounding of the
-// exact offset; the EIR derivative is evaluated in FP32 and the patch sum is a
+// Each patch's arrival D = (fs/c)(d - F) + fs(F/c - t0) (samples, double-word
+// FP32, ~1e-11 samples) is split into an integer part and an FP32 fraction,
+// so tau = (n - floor D) - frac(D) is the FP32 rounding of the offset; the EIR derivative is evaluated in FP32 and the patch sum is a
 // compensated (Kahan) FP32 sum.  Patches are visited in index order, so every
 // entry is a fixed-order sum.
-__global__ void k_slab_values(Geo g, const Patch *__restrict__ patch, int M, const int *orb_b,
+__global__ void k_slab_values(Geo g, const PatchDW *__restrict__ pdw, int M, const int *orb_b,
                               const int *orb_a, int nz, const int *band_lo, const int *band_hi,
                               int band_w, float *band) {
   const int o = blockIdx.x, k = blockIdx.y;
   const int b = orb_b[o], a = orb_a[o];
   const int lo = band_lo[o * nz + k], hi = band_hi[o * nz + k];
-  __shared__ float sI[kPatchChunk];  // floor(d), exact
-  __shared__ float sF[kPatchChunk];  // d - floor(d) in [0, 1)
+  __shared__ float sI[kPatchChunk];  // floor(D), exact
+  __shared__ float sF[kPatchChunk];  // D - floor(D)
   __shared__ float sW[kPatchChunk];
   const int per = (band_w + blockDim.x - 1) / blockDim.x;  // samples per thread (<= 4)
   const float cut = (float)g.cut;
   float sum[4] = {0, 0, 0, 0}, comp[4] = {0, 0, 0, 0};
+  // block constants as double words (voxel offset, |r|^2, F, 2F, F^2, fs/c, G)
+  const double rxd = a * g.dx, ryd = b * g.dy, rzd = g.z0 + k * g.dz;
+  const DW rx = to_dw(rxd), ry = to_dw(ryd), rz = to_dw(rzd), r2 = to_dw(rxd * rxd + ryd * ryd + rzd * rzd);
+  const DW Fw = to_dw(g.F), F2w = to_dw(2.0 * g.F), FFw = to_dw(g.F * g.F), ks = to_dw(g.ks), G = to_dw(g.G);
   for (int j0 = 0; j0 < M; j0 += kPatchChunk) {
     const int cnt = min(kPatchChunk, M - j0);
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-      Patch p = patch[j0 + j];
-      double dd = delta_dist(g, b, a, k, p);
-      const double d = __dadd_rn(__dmul_rn(g.ks, dd), g.G);
-      const double di = floor(d);
-      sI[j] = (float)di;
-      sF[j] = (float)(d - di);
-      sW[j] = (float)(p.w / ((g.F + dd) * 1e3));  // mm^2 / mm
+      const PatchDW p = pdw[j0 + j];
+      const DW rn = dw_add(dw_add(dw_mul(rx, DW{p.xh, p.xl}), dw_mul(ry, DW{p.yh, p.yl})), dw_mul(rz, DW{p.zh, p.zl}));
+      const DW num = dw_add(dw_mul(F2w, rn), r2);
+      const DW d = dw_sqrt(dw_add(FFw, num));
+      const DW dd = dw_div(num, dw_add(d, Fw));       // d - F, metres
+      const DW D = dw_add(dw_mul(ks, dd), G);          // arrival, samples
+      const float fl = floorf(D.h);
+      sI[j] = fl;
+      sF[j] = __fadd_rn(__fsub_rn(D.h, fl), D.l);      // D.h - fl is exact
+      sW[j] = __fdiv_rn(p.w, dw_add(Fw, dd).h);        // (mm^2 / 1e3) / metres = mm^2 / mm
     }
     __syncthreads();
     for (int r = 0; r < per; ++r) {
@@ -197,7 +320,11 @@ oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
   g.invs2 = (float)(1.0 / (m->sigma_s * m->sigma_s));
   g.omega = (float)m->omega;
 
-  k_delta_range<<<dim3(O, nz), 256, 0, st>>>(g, m->d_patch, m->M, d_orb_b, d_orb_a, nz, d_range);
+  PatchDW *d_pdw = nullptr;  // double-word patches, freed with the other temporaries
+  OAM_CUDA_TRY(cudaMallocAsync((void **)&d_pdw, sizeof(PatchDW) * m->M, st));
+  k_patch_dw<<<(m->M + 255) / 256, 256, 0, st>>>(m->d_patch, m->M, d_pdw);
+  OAM_LAUNCHED();
+  k_delta_range<<<dim3(O, nz), 256, 0, st>>>(g, m->d_patch, d_pdw, m->M, d_orb_b, d_orb_a, nz, d_range);
   OAM_LAUNCHED();
   std::vector<double2> h_range((size_t)O * nz);
   OAM_CUDA_TRY(cudaMemcpyAsync(h_range.data(), d_range, sizeof(double2) * O * nz, cudaMemcpyDeviceToHost, st));
@@ -217,6 +344,7 @@ oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
     cudaFreeAsync(d_orb_b, st);
     cudaFreeAsync(d_orb_a, st);
     cudaFreeAsync(d_range, st);
+    cudaFreeAsync(d_pdw, st);
     return OAM_ERR_WINDOW;
   }
   m->G = g.G;
@@ -269,7 +397,7 @@ oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
   OAM_CUDA_TRY(cudaMemcpyAsync(d_band_hi, m->h_band_hi.data(), sizeof(int) * O * nz, cudaMemcpyHostToDevice, st));
   if ((rc = dev_alloc(m, &m->d_band, (size_t)O * nz * m->band_w))) return rc;
   const int threads = m->band_w <= 128 ? 128 : 256;
-  k_slab_values<<<dim3(O, nz), threads, 0, st>>>(g, m->d_patch, m->M, d_orb_b, d_orb_a, nz, m->d_band_lo,
+  k_slab_values<<<dim3(O, nz), threads, 0, st>>>(g, d_pdw, m->M, d_orb_b, d_orb_a, nz, m->d_band_lo,
                                                   d_band_hi, m->band_w, m->d_band);
   OAM_LAUNCHED();
 
@@ -349,6 +477,7 @@ oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
   cudaFreeAsync(d_orb_b, st);
   cudaFreeAsync(d_orb_a, st);
   cudaFreeAsync(d_range, st);
+  cudaFreeAsync(d_pdw, st);
   cudaFreeAsync(d_band_hi, st);
   return OAM_OK;
 }

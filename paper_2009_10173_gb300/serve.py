@@ -91,15 +91,18 @@ def main():
     p.add_argument("--pool", type=int, default=12)
     p.add_argument("--slots", type=int, default=8)
     p.add_argument("--budget-gb", type=float, default=150.0)
+    p.add_argument("--prec", default="bf16x3", choices=["bf16x3", "fft", "fp32"],
+                   help="operator form of the served models")
     a = p.parse_args()
-    pool = [Instance(configs.served_request(2000 + j), B.OAM_PREC_BF16X3) for j in range(a.pool)]
+    prec = {"bf16x3": B.OAM_PREC_BF16X3, "fft": B.OAM_PREC_FFT, "fp32": B.OAM_PREC_FP32}[a.prec]
+    pool = [Instance(configs.served_request(2000 + j), prec) for j in range(a.pool)]
     for k, rate in enumerate(a.rates):
-        server = make_server(a.budget_gb * 1e9, a.slots)
+        server = make_server(a.budget_gb * 1e9, a.slots, precision=prec)
         res, _ = run_rate(server, pool, rate, a.requests, seed=3000 + k)
         B.oam_server_stop(server)
         res.update({"workload": "served: Poisson arrivals, sizes as the batched workload plus occasional "
                                 "200x200x300 volumes, 30 LSQR + 50 FISTA each",
-                    "slots": a.slots, "budget_gb": a.budget_gb, "pool_instances": a.pool})
+                    "slots": a.slots, "budget_gb": a.budget_gb, "pool_instances": a.pool, "prec": a.prec})
         print(json.dumps(res), flush=True)
 
 
