@@ -23,6 +23,7 @@ struct Geo {
   float inv2s2;   // 1 / (2 sigma_s^2)
   float invs2;    // 1 / sigma_s^2
   float omega;    // 2 pi fc / fs
+  float cyc;      // 2 fc / fs: the phase omega * tau in units of pi
 };
 
 // d - F for the voxel at lateral offset (a dx, b dy), depth k, and patch normal n.
@@ -225,7 +226,7 @@ __global__ void k_slab_values(Geo g, const PatchDW *__restrict__ pdw, int M, con
         const float tau = (nf - sI[j]) - sF[j];
         if (fabsf(tau) <= cut) {
           float sn, cs;
-          sincosf(g.omega * tau, &sn, &cs);
+          sincospif(g.cyc * tau, &sn, &cs);  // exact reduction of the argument modulo 2
           const float env = expf(-tau * tau * g.inv2s2);
           const float v = -env * (tau * g.invs2 * cs + g.omega * sn);
           const float y = sW[j] * v - c;
@@ -319,6 +320,7 @@ oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
   g.inv2s2 = (float)(1.0 / (2.0 * m->sigma_s * m->sigma_s));
   g.invs2 = (float)(1.0 / (m->sigma_s * m->sigma_s));
   g.omega = (float)m->omega;
+  g.cyc = (float)(m->omega / M_PI);
 
   PatchDW *d_pdw = nullptr;  // double-word patches, freed with the other temporaries
   OAM_CUDA_TRY(cudaMallocAsync((void **)&d_pdw, sizeof(PatchDW) * m->M, st));
