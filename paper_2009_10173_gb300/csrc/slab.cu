@@ -21,6 +21,7 @@ struct Geo {
   double G;       // fs * (F/c - t0)
   double cut;     // truncation, samples
   float inv2s2;   // 1 / (2 sigma_s^2)
+  float env2;     // log2(e) / (2 sigma_s^2): envelope exp(-tau^2 / (2 sigma_s^2)) = 2^(-env2 tau^2)
   float invs2;    // 1 / sigma_s^2
   float omega;    // 2 pi fc / fs
   float cyc;      // 2 fc / fs: the phase omega * tau in units of pi
@@ -227,7 +228,7 @@ __global__ void k_slab_values(Geo g, const PatchDW *__restrict__ pdw, int M, con
         if (fabsf(tau) <= cut) {
           float sn, cs;
           sincospif(g.cyc * tau, &sn, &cs);  // exact reduction of the argument modulo 2
-          const float env = expf(-tau * tau * g.inv2s2);
+          const float env = exp2f(-tau * tau * g.env2);
           const float v = -env * (tau * g.invs2 * cs + g.omega * sn);
           const float y = sW[j] * v - c;
           const float t = s + y;
@@ -318,6 +319,7 @@ oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
   g.ks = gr.fs_hz / m->sensor.c_mps;
   g.cut = m->cut;
   g.inv2s2 = (float)(1.0 / (2.0 * m->sigma_s * m->sigma_s));
+  g.env2 = (float)(1.0 / (2.0 * m->sigma_s * m->sigma_s * std::log(2.0)));
   g.invs2 = (float)(1.0 / (m->sigma_s * m->sigma_s));
   g.omega = (float)m->omega;
   g.cyc = (float)(m->omega / M_PI);
