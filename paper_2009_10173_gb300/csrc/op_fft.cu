@@ -132,25 +132,35 @@ __device__ void fft_lines(float2 *a, const float2 *tw, int P, int lgP, bool inve
 __device__ __forceinline__ int bitrev(int x, int lg) { return (int)(__brev((unsigned)x) >> (32 - lg)); }
 
 // Real rows -> half spectrum along x.  X[py][px][Ctot] (channels c0 .. c0+C-1
-// used), Y[Q][py][C] complex.  Block (y, channel block).
+// used), Y[Q][py][C] complex.  Block (y, channel block of KC).  Channels l and
+// l + KC/2 ride as the real and imaginary parts of one complex line; with
+// Z = FFT(x + i y), X(u) = (Z(u) + conj Z(-u)) / 2 and Y(u) = (Z(u) - conj Z(-u)) / 2i.
 template <int KC>
 __global__ void __launch_bounds__(kFftThreads) k_fft_rows_r2c(const float *__restrict__ X, int py, int px, int Ctot,
                                                               int c0, int C, int P, int lgP, int Q,
                                                               float2 *__restrict__ Y) {
+  constexpr int KH = KC / 2;  // complex lines
   extern __shared__ float2 sm[];
   float2 *tw = sm, *a = sm + (P >> 1);
   const int y = blockIdx.x, cb = blockIdx.y * KC;
   load_twiddles(tw, P);
-  for (int i = threadIdx.x; i < P * KC; i += blockDim.x) {
-    const int x = i / KC, c = i % KC;
-    float v = 0.0f;
-    if (x < px && cb + c < C) v = X[((size_t)y * px + x) * Ctot + c0 + cb + c];
-    a[bitrev(x, lgP) * KC + c] = make_float2(v, 0.0f);
+  for (int i = threadIdx.x; i < P * KH; i += blockDim.x) {
+    const int x = i / KH, l = i % KH;
+    float re = 0.0f, im = 0.0f;
+    if (x < px) {
+      const float *row = X + ((size_t)y * px + x) * Ctot + c0 + cb;
+      if (cb + l < C) re = row[l];
+      if (cb + l + KH < C) im = row[l + KH];
+    }
+    a[bitrev(x, lgP) * KH + l] = make_float2(re, im);
   }
-  fft_lines<KC>(a, tw, P, lgP, false);
+  fft_lines<KH>(a, tw, P, lgP, false);
   for (int i = threadIdx.x; i < Q * KC; i += blockDim.x) {
-    const int u = i / KC, c = i % KC;
-    if (cb + c < C) Y[((size_t)u * py + y) * C + cb + c] = a[u * KC + c];
+    const int u = i / KC, c = i % KC, l = c % KH;
+    if (cb + c >= C) continue;
+    const float2 z = a[u * KH + l], w = a[((P - u) & (P - 1)) * KH + l];
+    Y[((size_t)u * py + y) * C + cb + c] = c < KH ? make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y))
+                                                  : make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
   }
 }
 
@@ -178,11 +188,15 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(const float2 *__restri
 
 // Half spectrum along x -> real rows, scaled by 1/P^2.  Z[Q][py][C] holds
 // channels c0 .. c0+C-1 of the output X[py][px][Ctot]; every other output
-// channel is written as zero.  Block (y, output channel block).
+// channel is written as zero.  Block (y, output channel block of KC).
+// Channels l and l + KC/2 share one complex line W = X + i Y (each extended
+// Hermitian, the imaginary parts of its u = 0 and u = P/2 terms dropped): the
+// inverse transform's real and imaginary parts are the two real rows.
 template <int KC>
 __global__ void __launch_bounds__(kFftThreads) k_fft_rows_c2r(const float2 *__restrict__ Z, int py, int px, int Ctot,
                                                               int c0, int C, int P, int lgP, int Q,
                                                               float scale, float *__restrict__ X) {
+  constexpr int KH = KC / 2;
   extern __shared__ float2 sm[];
   float2 *tw = sm, *a = sm + (P >> 1);
   const int y = blockIdx.x, ob = blockIdx.y * KC;
@@ -194,25 +208,29 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_c2r(const float2 *__re
     return;
   }
   load_twiddles(tw, P);
-  for (int i = threadIdx.x; i < P * KC; i += blockDim.x) {
-    const int f = i / KC, c = i % KC;
-    const int zc = ob + c - c0;
-    float2 v = make_float2(0.0f, 0.0f);
-    if (zc >= 0 && zc < C) {
-      if (f < Q) {
-        v = Z[((size_t)f * py + y) * C + zc];
-      } else {  // Hermitian extension: Z(P - f) conjugated
-        const float2 w = Z[((size_t)(P - f) * py + y) * C + zc];
-        v = make_float2(w.x, -w.y);
-      }
+  for (int i = threadIdx.x; i < P * KH; i += blockDim.x) {
+    const int f = i / KH, l = i % KH;
+    const int fh = f < Q ? f : P - f;  // Hermitian source column
+    float2 xs = make_float2(0.0f, 0.0f), ys = make_float2(0.0f, 0.0f);
+    const int zx = ob + l - c0, zy = ob + l + KH - c0;
+    if (zx >= 0 && zx < C) xs = Z[((size_t)fh * py + y) * C + zx];
+    if (zy >= 0 && zy < C) ys = Z[((size_t)fh * py + y) * C + zy];
+    if (f == 0 || f == (P >> 1)) {
+      xs.y = 0.0f;
+      ys.y = 0.0f;
+    } else if (f >= Q) {
+      xs.y = -xs.y;
+      ys.y = -ys.y;
     }
-    a[bitrev(f, lgP) * KC + c] = v;
+    a[bitrev(f, lgP) * KH + l] = make_float2(xs.x - ys.y, xs.y + ys.x);
   }
-  fft_lines<KC>(a, tw, P, lgP, true);
+  fft_lines<KH>(a, tw, P, lgP, true);
   for (int i = threadIdx.x; i < px * KC; i += blockDim.x) {
-    const int x = i / KC, c = i % KC;
+    const int x = i / KC, c = i % KC, l = c % KH;
     const int oc = ob + c, zc = oc - c0;
-    if (oc < Ctot) X[((size_t)y * px + x) * Ctot + oc] = (zc >= 0 && zc < C) ? a[x * KC + c].x * scale : 0.0f;
+    if (oc >= Ctot) continue;
+    const float2 v = a[x * KH + l];
+    X[((size_t)y * px + x) * Ctot + oc] = (zc >= 0 && zc < C) ? (c < KH ? v.x : v.y) * scale : 0.0f;
   }
 }
 
@@ -650,17 +668,17 @@ namespace {
 template <int KC>
 oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float *in, float *out, cudaStream_t st) {
   const int P = L->P, Q = L->Q, lgP = L->lgP, nz = m->grid.nz, py = m->grid.py, px = m->grid.px, NS = L->NS;
-  const size_t sm = fft_smem(P, KC);
+  const size_t sm = fft_smem(P, KC), smr = fft_smem(P, KC / 2);  // row kernels: two channels per line
   oam_status rc;
-  if ((rc = set_smem((const void *)k_fft_rows_r2c<KC>, sm)) || (rc = set_smem((const void *)k_fft_cols<KC>, sm)) ||
-      (rc = set_smem((const void *)k_fft_rows_c2r<KC>, sm)))
+  if ((rc = set_smem((const void *)k_fft_rows_r2c<KC>, smr)) || (rc = set_smem((const void *)k_fft_cols<KC>, sm)) ||
+      (rc = set_smem((const void *)k_fft_rows_c2r<KC>, smr)))
     return rc;
   const unsigned cbz = (unsigned)((nz + KC - 1) / KC), cbs = (unsigned)((NS + KC - 1) / KC);
   const float scale = 1.0f / ((float)P * (float)P);
   // one warp per 16 samples (forward) or depths (adjoint)
   const int apply_threads = std::min(kApplyMaxThreads, 32 * (((fwd ? NS : nz) + 15) / 16));
   if (fwd) {
-    k_fft_rows_r2c<KC><<<dim3(py, cbz), kFftThreads, sm, st>>>(in, py, px, nz, 0, nz, P, lgP, Q, L->d_w2);
+    k_fft_rows_r2c<KC><<<dim3(py, cbz), kFftThreads, smr, st>>>(in, py, px, nz, 0, nz, P, lgP, Q, L->d_w2);
     OAM_LAUNCHED();
     k_fft_cols<KC><<<dim3(Q, cbz), kFftThreads, sm, st>>>(L->d_w2, py, P, nz, P, lgP, 0, L->d_w1);
     OAM_LAUNCHED();
@@ -674,11 +692,11 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     k_fft_cols<KC><<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, P, py, NS, P, lgP, 1, L->d_w1);
     OAM_LAUNCHED();
     const unsigned cbt = (unsigned)((m->grid.nt + KC - 1) / KC);
-    k_fft_rows_c2r<KC><<<dim3(py, cbt), kFftThreads, sm, st>>>(L->d_w1, py, px, m->grid.nt, m->n_lo, NS, P, lgP, Q,
+    k_fft_rows_c2r<KC><<<dim3(py, cbt), kFftThreads, smr, st>>>(L->d_w1, py, px, m->grid.nt, m->n_lo, NS, P, lgP, Q,
                                                                scale, out);
     OAM_LAUNCHED();
   } else {
-    k_fft_rows_r2c<KC><<<dim3(py, cbs), kFftThreads, sm, st>>>(in, py, px, m->grid.nt, m->n_lo, NS, P, lgP, Q,
+    k_fft_rows_r2c<KC><<<dim3(py, cbs), kFftThreads, smr, st>>>(in, py, px, m->grid.nt, m->n_lo, NS, P, lgP, Q,
                                                                L->d_w2);
     OAM_LAUNCHED();
     k_fft_cols<KC><<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, py, P, NS, P, lgP, 0, L->d_w1);
@@ -691,7 +709,7 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     OAM_LAUNCHED();
     k_fft_cols<KC><<<dim3(Q, cbz), kFftThreads, sm, st>>>(L->d_w2, P, py, nz, P, lgP, 1, L->d_w1);
     OAM_LAUNCHED();
-    k_fft_rows_c2r<KC><<<dim3(py, cbz), kFftThreads, sm, st>>>(L->d_w1, py, px, nz, 0, nz, P, lgP, Q, scale, out);
+    k_fft_rows_c2r<KC><<<dim3(py, cbz), kFftThreads, smr, st>>>(L->d_w1, py, px, nz, 0, nz, P, lgP, Q, scale, out);
     OAM_LAUNCHED();
   }
   return OAM_OK;

@@ -377,7 +377,7 @@ void server_loop(oam_server *S) {
 extern "C" oam_status oam_request_footprint(int32_t precision, const oam_grid *grid, size_t *bytes) {
   if (!grid || !bytes || grid->win < 1 || grid->px < 1 || grid->py < 1 || grid->nz < 1 || grid->nt < 1)
     return OAM_ERR_INVALID_ARG;
-  if (precision != OAM_PREC_FP32 && precision != OAM_PREC_BF16X3) return OAM_ERR_INVALID_ARG;
+  if (precision != OAM_PREC_FP32 && precision != OAM_PREC_BF16X3 && precision != OAM_PREC_FFT) return OAM_ERR_INVALID_ARG;
   oam_server_opts o{};
   o.precision = precision;
   *bytes = footprint_estimate(o, *grid);
@@ -387,7 +387,7 @@ extern "C" oam_status oam_request_footprint(int32_t precision, const oam_grid *g
 extern "C" oam_status oam_server_create(const oam_server_opts *opts, oam_server **out) {
   if (!opts || !out || opts->max_slots < 1 || opts->max_slots > 256 || opts->hbm_budget_bytes == 0 ||
       opts->lsqr_iters < 0 || opts->fista_iters < 0 || opts->power_iters < 1 ||
-      (opts->precision != OAM_PREC_FP32 && opts->precision != OAM_PREC_BF16X3))
+      (opts->precision != OAM_PREC_FP32 && opts->precision != OAM_PREC_BF16X3 && opts->precision != OAM_PREC_FFT))
     return OAM_ERR_INVALID_ARG;
   *out = nullptr;
   oam_server *S = new (std::nothrow) oam_server();

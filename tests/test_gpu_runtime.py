@@ -120,8 +120,8 @@ def _serve(server, reqs):
     return outs
 
 
-def _server(budget=8 << 30, slots=3, iters=(6, 5, 4)):
-    opts = B.OamServerOpts(budget, slots, B.OAM_PREC_BF16X3, iters[0], iters[1], iters[2], 1e-3)
+def _server(budget=8 << 30, slots=3, iters=(6, 5, 4), prec=B.OAM_PREC_BF16X3):
+    opts = B.OamServerOpts(budget, slots, prec, iters[0], iters[1], iters[2], 1e-3)
     return B.oam_server_create(opts)
 
 
@@ -173,3 +173,18 @@ def test_server_budget_failure_and_timeout():
     B.oam_server_stop(srv)
     assert st.peak_running == 1
     assert st.peak_reserved_bytes <= int(need * 1.5)
+
+
+def test_server_with_fft_form_models_matches_standalone():
+    """Requests served with lateral-FFT form models give exactly the images of
+    the same reconstruction run directly on a model of that form."""
+    reqs = [_request(JOBS[0]), _request(JOBS[2])]
+    srv = _server(slots=2, prec=B.OAM_PREC_FFT)
+    outs = _serve(srv, reqs)
+    B.oam_server_stop(srv)
+    for (cfg, s), (rid, x2, x1) in zip(reqs, outs):
+        m = Model(cfg, precision=B.OAM_PREC_FFT)
+        ref2, ref1 = standalone(cfg, m, s.cuda())
+        m.close()
+        assert np.array_equal(x2.numpy(), ref2)
+        assert np.array_equal(x1.numpy(), ref1)
