@@ -32,14 +32,14 @@ OPS_PER_STEP = (1 + 2 * LSQR_ITERS) + (2 * POWER_ITERS + 1 + 2 * FISTA_ITERS)
 FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the tensor-core operator kernel (k_corr_fold) on this
 # workload: dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of the
-# same kernel on a 96x96-position case of this workload (441.3 MB for 2945 blocks),
+# same kernel on a 96x96-position case of this workload (440.8 MB for 2945 blocks),
 # scaled by blocks processed (11160 / 2945).  Set to None when the kernel changes.
-TC_TRAFFIC_BYTES = 441.3e6 * 11160 / 2945
+TC_TRAFFIC_BYTES = 440.8e6 * 11160 / 2945
 # DRAM bytes per application of the lateral-FFT form on this workload:
 # dram__bytes_read.sum + dram__bytes_write.sum over the five launches of one
-# forward, from an ncu capture of the full 200x200x300 workload (1.190 GB read,
-# 0.242 GB written).  Set to None when those kernels change.
-FFT_TRAFFIC_BYTES = 1.432e9
+# forward, from an ncu capture of the full 200x200x300 workload (1.677 GB read,
+# 0.247 GB written).  Set to None when those kernels change.
+FFT_TRAFFIC_BYTES = 1.9225e9
 
 
 def parse():
@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16x3", "fft"],
                    help="operator form: auto = split-BF16 tensor cores when built; fft = FP32 lateral-FFT form")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true",
+                   help="skip the short measurement of the other operator form in the default run")
     return p.parse_args()
 
 
@@ -279,8 +281,8 @@ def run_ours(args, rank, world):
 
     keep = []
 
-    def step(s_in, profile=False):
-        m = make_model(prec)
+    def step(s_in, profile=False, form=None):
+        m = make_model(prec if form is None else form)
         if profile:
             B.oam_profile_enable(m.handle, True)
         x2, _ = m.lsqr(s_in, LSQR_ITERS, want_info=False)
@@ -292,6 +294,41 @@ def run_ours(args, rank, world):
         if dist:
             tdist.barrier()
         torch.cuda.synchronize()
+
+    def other_form(form, steps=3, warmup=2):
+        # the same reconstruction with another operator form, timed the same way
+        for _ in range(warmup):
+            mm, _, _ = step(s_dev, form=form)
+            mm.close()
+        barrier()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        models = []
+        evs[0].record()
+        for i in range(steps):
+            mm, _, _ = step(s_dev, profile=True, form=form)
+            models.append(mm)
+            flush.zero_()
+            evs[i + 1].record()
+        barrier()
+        ms = evs[0].elapsed_time(evs[-1]) / steps
+        pr = [B.oam_profile_read(mm.handle) for mm in models]
+        inf = models[0].info
+        for mm in models:
+            mm.close()
+        f_ms = sum(q.forward_ms for q in pr) / max(1, sum(q.forward_calls for q in pr))
+        a_ms = sum(q.adjoint_ms for q in pr) / max(1, sum(q.adjoint_calls for q in pr))
+        gbs = inf.op_bytes / (f_ms * 1e-3) / 1e9
+        hbm = 6800.0
+        try:
+            hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", hbm)
+        except Exception:
+            pass
+        return {"precision": "FP32 lateral-FFT form of the same operators (exact restatement)",
+                "value": steps / (evs[0].elapsed_time(evs[-1]) / 1e3), "unit": "volumes/s", "ms_per_step": ms,
+                "op_ms": {"forward": f_ms, "adjoint": a_ms},
+                "roofline": {"bound": "hbm", "kernel": "forward (lateral-FFT form, 5 launches)", "achieved": gbs,
+                             "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": FFT_TRAFFIC_BYTES,
+                             "bytes_per_op": inf.op_bytes}}
 
     for _ in range(args.warmup):
         m, _, _ = step(s_dev)
@@ -390,6 +427,8 @@ def run_ours(args, rank, world):
             "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "volumes/s",
                     "h2d_bytes_per_step": int(s_host.numel() * 4), "d2h_bytes_per_step": 2 * vol_bytes},
             "clocks": clk, "wall_s_timed": wall}
+    if world == 1 and args.prec == "auto" and not args.no_forms:
+        line["forms"] = {"lateral_fft": other_form(B.OAM_PREC_FFT)}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_entry(info.flops_per_op)
     print(json.dumps(line), flush=True)
