@@ -62,7 +62,8 @@ constexpr int kFftThreads = 256;
 constexpr int kApplyMaxThreads = 1024;
 constexpr int kUnroll = 8;  // spectral products: independent row loads per lane in flight
 constexpr int kFwdPhases = 2;  // forward products: lane groups of a warp that walk interleaved depths
-constexpr int kFwdChunk = 128;  // forward products: samples per block (0: all samples of the orbit)
+constexpr int kFwdChunk = 256;  // forward products: samples per block (0: all samples of the orbit)
+constexpr int kAdjChunk = 128;  // adjoint products: depths per block (0: all depths of the orbit)
 constexpr int kBuildThreads = 128;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -248,7 +249,9 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_fwd(const float 
   int *s_lo = reinterpret_cast<int *>(Hs + 2 * nz);   // [nz]
   int *s_len = s_lo + nz;                             // [nz]
   long long *s_off = reinterpret_cast<long long *>(s_len + nz);  // [nz]: 40 nz bytes in, 8-byte aligned
-  const int r = blockIdx.x;
+  // linear grid, chunk fastest: an orbit's sample chunks run back to back and share its vectors in L2
+  const int nch = kFwdChunk > 0 ? (NS + kFwdChunk - 1) / kFwdChunk : 1;
+  const int r = (int)(blockIdx.x / nch), chunk = (int)(blockIdx.x % nch);
   const int4 mem = members[r];
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
     const float2 z = make_float2(0.0f, 0.0f);
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_fwd(const float 
   const float *row = shat + (size_t)r * row_len;
   constexpr int kLanes = 32 / kFwdPhases;  // samples per warp
   const int lane = threadIdx.x & 31, sub = lane % kLanes, ph = lane / kLanes;
-  const int jb = kFwdChunk > 0 ? blockIdx.y * kFwdChunk : 0;
+  const int jb = kFwdChunk > 0 ? chunk * kFwdChunk : 0;
   const int je = kFwdChunk > 0 ? min(NS, jb + kFwdChunk) : NS;
   // a warp serves kLanes samples; its lane groups walk interleaved depths of
   // the warp's common depth range (coalesced row reads), then add their sums
@@ -339,7 +342,10 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_adj(const float 
   float4 *Ss = sma;                                      // [NS][2]: members (0, 1) and (2, 3)
   int2 *s_kr = reinterpret_cast<int2 *>(Ss + 2 * NS);     // [NS]
   long long *s_no = reinterpret_cast<long long *>(s_kr + NS);  // [NS]
-  const int r = blockIdx.x;
+  // linear grid, chunk fastest: an orbit's depth chunks run back to back
+  const int nch = kAdjChunk > 0 ? (nz + kAdjChunk - 1) / kAdjChunk : 1;
+  const int r = (int)(blockIdx.x / nch), chunk = (int)(blockIdx.x % nch);
+  const int kb = kAdjChunk > 0 ? chunk * kAdjChunk : 0, ke = kAdjChunk > 0 ? min(nz, kb + kAdjChunk) : nz;
   const int4 mem = members[r];
   for (int j = threadIdx.x; j < NS; j += blockDim.x) {
     const float2 z = make_float2(0.0f, 0.0f);
@@ -355,9 +361,9 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_adj(const float 
   const int lane = threadIdx.x & 31, sub = lane & 15, ph = lane >> 4;
   // a warp serves 16 depths; its two half-warps walk alternate samples of the
   // warp's common sample range (coalesced reads), then add their sums
-  for (int g0 = (threadIdx.x >> 5) * 16; g0 < nz; g0 += (blockDim.x >> 5) * 16) {
+  for (int g0 = kb + (threadIdx.x >> 5) * 16; g0 < ke; g0 += (blockDim.x >> 5) * 16) {
     const int k = g0 + sub;
-    const bool live = k < nz && klen[k] > 0;
+    const bool live = k < ke && klen[k] > 0;
     const int lo = live ? klo[k] - n_lo : NS, hi = live ? klo[k] - n_lo + klen[k] : 0;
     const int j0 = __reduce_min_sync(0xffffffffu, lo), j1 = __reduce_max_sync(0xffffffffu, hi);
     float acc[8];
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(kApplyMaxThreads) k_fft_apply_adj(const float 
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 16);
-    if (k >= nz || ph != 0) continue;
+    if (k >= ke || ph != 0) continue;
     if (mem.x >= 0) Hh[(size_t)mem.x * nz + k] = make_float2(acc[0], acc[1]);
     if (mem.y >= 0) Hh[(size_t)mem.y * nz + k] = make_float2(acc[2], acc[3]);
     if (mem.z >= 0) Hh[(size_t)mem.z * nz + k] = make_float2(acc[4], acc[5]);
@@ -675,8 +681,6 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     return rc;
   const unsigned cbz = (unsigned)((nz + KC - 1) / KC), cbs = (unsigned)((NS + KC - 1) / KC);
   const float scale = 1.0f / ((float)P * (float)P);
-  // one warp per 16 samples (forward) or depths (adjoint)
-  const int apply_threads = std::min(kApplyMaxThreads, 32 * (((fwd ? NS : nz) + 15) / 16));
   if (fwd) {
     k_fft_rows_r2c<KC><<<dim3(py, cbz), kFftThreads, smr, st>>>(in, py, px, nz, 0, nz, P, lgP, Q, L->d_w2);
     OAM_LAUNCHED();
@@ -686,7 +690,7 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     if ((rc = set_smem((const void *)k_fft_apply_fwd, sa))) return rc;
     const int fchunk = kFwdChunk > 0 ? kFwdChunk : NS;
     const int fwd_threads = std::min(kApplyMaxThreads, 32 * ((fchunk + 32 / kFwdPhases - 1) / (32 / kFwdPhases)));
-    k_fft_apply_fwd<<<dim3(L->n_rep, (NS + fchunk - 1) / fchunk), fwd_threads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
+    k_fft_apply_fwd<<<(unsigned)(L->n_rep * ((NS + fchunk - 1) / fchunk)), fwd_threads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
                                                          L->d_koff, L->d_krange, nz, m->n_lo, NS, L->d_w1, L->d_w2);
     OAM_LAUNCHED();
     k_fft_cols<KC><<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, P, py, NS, P, lgP, 1, L->d_w1);
@@ -703,7 +707,9 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     OAM_LAUNCHED();
     const size_t sa = (sizeof(float4) * 2 + sizeof(int2) + sizeof(long long)) * NS;
     if ((rc = set_smem((const void *)k_fft_apply_adj, sa))) return rc;
-    k_fft_apply_adj<<<L->n_rep, apply_threads, sa, st>>>(L->d_shat_t, L->row_len_t, L->d_members, L->d_klo,
+    const int achunk = kAdjChunk > 0 ? kAdjChunk : nz;
+    const int adj_threads = std::min(kApplyMaxThreads, 32 * ((achunk + 15) / 16));
+    k_fft_apply_adj<<<(unsigned)(L->n_rep * ((nz + achunk - 1) / achunk)), adj_threads, sa, st>>>(L->d_shat_t, L->row_len_t, L->d_members, L->d_klo,
                                                          L->d_klen, L->d_krange, L->d_noff, nz, m->n_lo, NS, L->d_w1,
                                                          L->d_w2);
     OAM_LAUNCHED();
