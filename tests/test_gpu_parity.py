@@ -301,3 +301,23 @@ def test_full_size_lsqr_residual_estimate():
         assert abs(info.rnorm - true) / true < 1e-3
         assert info.rnorm <= prev
         prev = info.rnorm
+
+
+@pytest.mark.parametrize("px", [300, 600, 1100])
+def test_fft_form_wide_grids(px):
+    """Transform sizes P = 512, 1024 and 2048 (fewer channels per FFT block)
+    on thin grids the oracle applies directly."""
+    cfg = configs.scaled(C0, px=px, py=3, nz=9, nt=128, win=3, n_patches=200)
+    S = oracle.slab(cfg)
+    m = Model(cfg, precision=B.OAM_PREC_FFT)
+    H = inputs.gaussian((cfg["py"], cfg["px"], cfg["nz"]), 41)
+    s = inputs.gaussian((cfg["py"], cfg["px"], cfg["nt"]), 42)
+    assert rel(host(m.forward(dev(H))), oracle.forward(S, H.astype(np.float32))) < TOL[B.OAM_PREC_FFT]
+    assert rel(host(m.adjoint(dev(s))), oracle.adjoint(S, s.astype(np.float32))) < TOL[B.OAM_PREC_FFT]
+    m.close()
+
+
+def test_fft_form_rejects_grids_beyond_its_transform_size():
+    with pytest.raises(B.OamError) as e:
+        Model(configs.scaled(C0, px=2100, py=2, nz=4, nt=128, win=3, n_patches=200), precision=B.OAM_PREC_FFT)
+    assert e.value.code == B.OAM_ERR_UNSUPPORTED
