@@ -690,8 +690,9 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     if ((rc = set_smem((const void *)k_fft_apply_fwd, sa))) return rc;
     const int fchunk = kFwdChunk > 0 ? kFwdChunk : NS;
     const int fwd_threads = std::min(kApplyMaxThreads, 32 * ((fchunk + 32 / kFwdPhases - 1) / (32 / kFwdPhases)));
-    k_fft_apply_fwd<<<(unsigned)(L->n_rep * ((NS + fchunk - 1) / fchunk)), fwd_threads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
-                                                         L->d_koff, L->d_krange, nz, m->n_lo, NS, L->d_w1, L->d_w2);
+    const unsigned fblocks = (unsigned)(L->n_rep * ((NS + fchunk - 1) / fchunk));
+    k_fft_apply_fwd<<<fblocks, fwd_threads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
+                                                      L->d_koff, L->d_krange, nz, m->n_lo, NS, L->d_w1, L->d_w2);
     OAM_LAUNCHED();
     k_fft_cols<KC><<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, P, py, NS, P, lgP, 1, L->d_w1);
     OAM_LAUNCHED();
@@ -709,9 +710,9 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     if ((rc = set_smem((const void *)k_fft_apply_adj, sa))) return rc;
     const int achunk = kAdjChunk > 0 ? kAdjChunk : nz;
     const int adj_threads = std::min(kApplyMaxThreads, 32 * ((achunk + 15) / 16));
-    k_fft_apply_adj<<<(unsigned)(L->n_rep * ((nz + achunk - 1) / achunk)), adj_threads, sa, st>>>(L->d_shat_t, L->row_len_t, L->d_members, L->d_klo,
-                                                         L->d_klen, L->d_krange, L->d_noff, nz, m->n_lo, NS, L->d_w1,
-                                                         L->d_w2);
+    const unsigned ablocks = (unsigned)(L->n_rep * ((nz + achunk - 1) / achunk));
+    k_fft_apply_adj<<<ablocks, adj_threads, sa, st>>>(L->d_shat_t, L->row_len_t, L->d_members, L->d_klo, L->d_klen,
+                                                      L->d_krange, L->d_noff, nz, m->n_lo, NS, L->d_w1, L->d_w2);
     OAM_LAUNCHED();
     k_fft_cols<KC><<<dim3(Q, cbz), kFftThreads, sm, st>>>(L->d_w2, P, py, nz, P, lgP, 1, L->d_w1);
     OAM_LAUNCHED();

@@ -377,7 +377,8 @@ void server_loop(oam_server *S) {
 extern "C" oam_status oam_request_footprint(int32_t precision, const oam_grid *grid, size_t *bytes) {
   if (!grid || !bytes || grid->win < 1 || grid->px < 1 || grid->py < 1 || grid->nz < 1 || grid->nt < 1)
     return OAM_ERR_INVALID_ARG;
-  if (precision != OAM_PREC_FP32 && precision != OAM_PREC_BF16X3 && precision != OAM_PREC_FFT) return OAM_ERR_INVALID_ARG;
+  if (precision != OAM_PREC_FP32 && precision != OAM_PREC_BF16X3 && precision != OAM_PREC_FFT)
+    return OAM_ERR_INVALID_ARG;
   oam_server_opts o{};
   o.precision = precision;
   *bytes = footprint_estimate(o, *grid);

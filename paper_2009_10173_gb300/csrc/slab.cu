@@ -183,9 +183,10 @@ constexpr int kPatchChunk = 512;
 // Band values: thread i of block (o, k) owns sample lo + i (+ blockDim.x ...).
 // Each patch's arrival D = (fs/c)(d - F) + fs(F/c - t0) (samples, double-word
 // FP32, ~1e-11 samples) is split into an integer part and an FP32 fraction,
-// so tau = (n - floor D) - frac(D) is the FP32 rounding of the offset; the EIR derivative is evaluated in FP32 and the patch sum is a
-// compensated (Kahan) FP32 sum.  Patches are visited in index order, so every
-// entry is a fixed-order sum.
+// so tau = (n - floor D) - frac(D) is the FP32 rounding of the offset.  The
+// EIR derivative is evaluated in FP32 (phase through sincospi, envelope through
+// exp2) and the patch sum is a compensated (Kahan) FP32 sum.  Patches are
+// visited in index order, so every entry is a fixed-order sum.
 __global__ void k_slab_values(Geo g, const PatchDW *__restrict__ pdw, int M, const int *orb_b,
                               const int *orb_a, int nz, const int *band_lo, const int *band_hi,
                               int band_w, float *band) {
