@@ -182,20 +182,28 @@ constexpr int kPatchChunk = 512;
 
 // Band values: thread i of block (o, k) owns sample lo + i (+ blockDim.x ...).
 // Each patch's arrival D = (fs/c)(d - F) + fs(F/c - t0) (samples, double-word
-// FP32, ~1e-11 samples) is split into an integer part and an FP32 fraction,
-// so tau = (n - floor D) - frac(D) is the FP32 rounding of the offset.  The
-// EIR derivative is evaluated in FP32 (phase through sincospi, envelope through
-// exp2) and the patch sum is a compensated (Kahan) FP32 sum.  Patches are
+// FP32, ~1e-11 samples) is split into the nearest sample n_ref and a fraction
+// f = D - n_ref in [-1/2, 1/2], so tau = (n - n_ref) - f is the FP32 rounding
+// of the offset.  The phase omega*tau is a rotation: the patch's own
+// (cos, sin)(-omega f) turned by a table entry (cos, sin)(omega t) for the
+// integer t = n - n_ref (|t| <= cut + 1/2); both arguments are small, so the
+// result stays within a few ulp.  The envelope is exp2 of a pre-scaled
+// argument and the patch sum is a compensated (Kahan) FP32 sum.  Patches are
 // visited in index order, so every entry is a fixed-order sum.
 __global__ void k_slab_values(Geo g, const PatchDW *__restrict__ pdw, int M, const int *orb_b,
                               const int *orb_a, int nz, const int *band_lo, const int *band_hi,
-                              int band_w, float *band) {
+                              int band_w, int T0, float *band) {
+  extern __shared__ float2 rot[];  // [2 T0 + 1]: (cos, sin)(omega t), t = -T0 .. T0
   const int o = blockIdx.x, k = blockIdx.y;
   const int b = orb_b[o], a = orb_a[o];
   const int lo = band_lo[o * nz + k], hi = band_hi[o * nz + k];
-  __shared__ float sI[kPatchChunk];  // floor(D), exact
-  __shared__ float sF[kPatchChunk];  // D - floor(D)
+  __shared__ float4 sP[kPatchChunk];  // (n_ref, f, cos(omega f), -sin(omega f))
   __shared__ float sW[kPatchChunk];
+  for (int t = threadIdx.x; t <= 2 * T0; t += blockDim.x) {
+    float sn, cs;
+    sincospif(g.cyc * (float)(t - T0), &sn, &cs);
+    rot[t] = make_float2(cs, sn);
+  }
   const int per = (band_w + blockDim.x - 1) / blockDim.x;  // samples per thread (<= 4)
   const float cut = (float)g.cut;
   float sum[4] = {0, 0, 0, 0}, comp[4] = {0, 0, 0, 0};
@@ -211,12 +219,14 @@ __global__ void k_slab_values(Geo g, const PatchDW *__restrict__ pdw, int M, con
       const DW rn = dw_add(dw_add(dw_mul(rx, DW{p.xh, p.xl}), dw_mul(ry, DW{p.yh, p.yl})), dw_mul(rz, DW{p.zh, p.zl}));
       const DW num = dw_add(dw_mul(F2w, rn), r2);
       const DW d = dw_sqrt(dw_add(FFw, num));
-      const DW dd = dw_div(num, dw_add(d, Fw));       // d - F, metres
-      const DW D = dw_add(dw_mul(ks, dd), G);          // arrival, samples
-      const float fl = floorf(D.h);
-      sI[j] = fl;
-      sF[j] = __fadd_rn(__fsub_rn(D.h, fl), D.l);      // D.h - fl is exact
-      sW[j] = __fdiv_rn(p.w, dw_add(Fw, dd).h);        // (mm^2 / 1e3) / metres = mm^2 / mm
+      const DW dd = dw_div(num, dw_add(d, Fw));        // d - F, metres
+      const DW D = dw_add(dw_mul(ks, dd), G);           // arrival, samples
+      const float nr = rintf(D.h);
+      const float f = __fadd_rn(__fsub_rn(D.h, nr), D.l);  // D.h - nr is exact
+      float sn, cs;
+      sincospif(g.cyc * f, &sn, &cs);
+      sP[j] = make_float4(nr, f, cs, -sn);
+      sW[j] = __fdiv_rn(p.w, dw_add(Fw, dd).h);         // (mm^2 / 1e3) / metres = mm^2 / mm
     }
     __syncthreads();
     for (int r = 0; r < per; ++r) {
@@ -225,16 +235,19 @@ __global__ void k_slab_values(Geo g, const PatchDW *__restrict__ pdw, int M, con
       const float nf = (float)n;
       float s = sum[r], c = comp[r];
       for (int j = 0; j < cnt; ++j) {
-        const float tau = (nf - sI[j]) - sF[j];
+        const float4 q = sP[j];
+        const float t = nf - q.x;  // exact integer
+        const float tau = t - q.y;
         if (fabsf(tau) <= cut) {
-          float sn, cs;
-          sincospif(g.cyc * tau, &sn, &cs);  // exact reduction of the argument modulo 2
+          const float2 e = rot[__float2int_rn(t) + T0];  // |t| <= cut + 1/2 < T0
+          const float cs = e.x * q.z - e.y * q.w;        // cos(omega t - omega f)
+          const float sn = e.y * q.z + e.x * q.w;        // sin(omega t - omega f)
           const float env = exp2f(-tau * tau * g.env2);
           const float v = -env * (tau * g.invs2 * cs + g.omega * sn);
           const float y = sW[j] * v - c;
-          const float t = s + y;
-          c = (t - s) - y;
-          s = t;
+          const float u = s + y;
+          c = (u - s) - y;
+          s = u;
         }
       }
       sum[r] = s;
@@ -402,8 +415,9 @@ oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
   OAM_CUDA_TRY(cudaMemcpyAsync(d_band_hi, m->h_band_hi.data(), sizeof(int) * O * nz, cudaMemcpyHostToDevice, st));
   if ((rc = dev_alloc(m, &m->d_band, (size_t)O * nz * m->band_w))) return rc;
   const int threads = m->band_w <= 128 ? 128 : 256;
-  k_slab_values<<<dim3(O, nz), threads, 0, st>>>(g, d_pdw, m->M, d_orb_b, d_orb_a, nz, m->d_band_lo,
-                                                  d_band_hi, m->band_w, m->d_band);
+  const int T0 = (int)std::floor(m->cut + 0.5) + 1;  // rotation table half-length
+  k_slab_values<<<dim3(O, nz), threads, sizeof(float2) * (2 * T0 + 1), st>>>(
+      g, d_pdw, m->M, d_orb_b, d_orb_a, nz, m->d_band_lo, d_band_hi, m->band_w, T0, m->d_band);
   OAM_LAUNCHED();
 
   // FP32 forward layout
