@@ -16,6 +16,9 @@ benchmark's CPU-baseline leg import this package; the product path
   slab slice.
 * ``oracle.solvers``: LSQR for Eq. 5 with Eq. 6 (MB-L2) and FISTA for Eq. 5
   with Eq. 7 (MB-L1), written from the published algorithms the paper names.
+* ``oracle.bandpass``: the band-pass filtering of signals and model along
+  time that precedes inversion in the Results (a windowed-sinc FIR, applied
+  as a direct sum).
 """
 import ctypes
 import math
