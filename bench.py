@@ -40,6 +40,10 @@ TC_TRAFFIC_BYTES = 440.8e6 * 11160 / 2945
 # forward, from an ncu capture of the full 200x200x300 workload (1.189 GB read,
 # 0.243 GB written).  Set to None when those kernels change.
 FFT_TRAFFIC_BYTES = 1.4327e9
+# Band-pass filter along time: half length of the 0.5-80 MHz FIR, and the DRAM
+# bytes of one application (no ncu capture of this kernel yet: null).
+FIR_HALF = 511
+FIR_TRAFFIC_BYTES = None
 
 
 def parse():
@@ -52,7 +56,8 @@ def parse():
                    help="operator form: auto = split-BF16 tensor cores when built; fft = FP32 lateral-FFT form")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true",
-                   help="skip the short measurement of the other operator form in the default run")
+                   help="skip the short measurements of the other operator form, the band-pass filter and "
+                        "the Tikhonov sweep in the default run")
     return p.parse_args()
 
 
@@ -330,6 +335,58 @@ def run_ours(args, rank, world):
                              "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": FFT_TRAFFIC_BYTES,
                              "bytes_per_op": inf.op_bytes}}
 
+    def extensions(reps=20, n_damps=8):
+        # band-pass filter along time (0.5-80 MHz, 1023 taps: the second
+        # simulation's band) and the Tikhonov sweep, on the lateral-FFT model
+        mm = make_model(B.OAM_PREC_FFT)
+        taps = B.oam_bandpass_taps(0.5e6, 80e6, cfg["fs_hz"], FIR_HALF)
+        mm.set_filter(taps)
+        sig = s_dev.clone()
+        out = torch.empty_like(sig)
+        for _ in range(3):
+            mm.filter_signals(sig, out)
+        barrier()
+        ev_f = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev_f[0].record()
+        for _ in range(reps):  # 2 x 164 MB per application, more than L2 holds
+            mm.filter_signals(sig, out)
+        ev_f[1].record()
+        barrier()
+        fir_ms = ev_f[0].elapsed_time(ev_f[1]) / reps
+        fir_bytes = 2 * sig.numel() * 4
+        hbm = 6800.0
+        try:
+            hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", hbm)
+        except Exception:
+            pass
+        gbs = fir_bytes / (fir_ms * 1e-3) / 1e9
+        # filtered MB-L2: signals through F, then LSQR with F A
+        sf = mm.filter_signals(sig)
+        _, inf = mm.lsqr(sf, LSQR_ITERS)
+        damps = [0.0] + [inf.anorm * f for f in (1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1)][:n_damps - 1]
+        mm.lsqr_sweep(sf, 2, damps, want_info=False)
+        barrier()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        mm.lsqr_sweep(sf, LSQR_ITERS, damps, want_info=False)
+        e[1].record()
+        for d in damps:
+            mm.lsqr(sf, LSQR_ITERS, damp=d, want_info=False)
+        e[2].record()
+        barrier()
+        sweep_ms, single_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        fir_size = mm.info.filter_size
+        mm.close()
+        return {"bandpass_filter": {"band_hz": [0.5e6, 80e6], "taps": 2 * FIR_HALF + 1, "transform": fir_size,
+                                    "ms": fir_ms, "roofline": {"bound": "hbm", "kernel": "k_fir_lines",
+                                                               "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                                               "frac": gbs / hbm, "bytes_per_launch": fir_bytes,
+                                                               "traffic": FIR_TRAFFIC_BYTES}},
+                "tikhonov_sweep": {"damps": len(damps), "iters": LSQR_ITERS, "filtered": True,
+                                   "sweep_ms": sweep_ms, "separate_solves_ms": single_ms,
+                                   "speedup": single_ms / sweep_ms,
+                                   "solves_per_s": len(damps) / (sweep_ms / 1e3)}}
+
     for _ in range(args.warmup):
         m, _, _ = step(s_dev)
         m.close()
@@ -429,6 +486,8 @@ def run_ours(args, rank, world):
             "clocks": clk, "wall_s_timed": wall}
     if world == 1 and args.prec == "auto" and not args.no_forms:
         line["forms"] = {"lateral_fft": other_form(B.OAM_PREC_FFT)}
+    if world == 1 and not args.no_forms:
+        line["extensions"] = extensions()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_entry(info.flops_per_op)
     print(json.dumps(line), flush=True)

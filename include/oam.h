@@ -111,6 +111,8 @@ typedef struct {
                                                     and FFTs for OAM_PREC_FFT; 0 for OAM_PREC_FP32 */
   double op_bytes;     /* OAM_PREC_FFT: device bytes read + written per application (the
                           spectral slab dominates); 0 otherwise */
+  int32_t filter_half_len; /* L of the band-pass filter set by oam_model_set_filter, -1: none */
+  int32_t filter_size;     /* its transform length NF (0: none) */
 } oam_model_info;
 
 /* Build the model slab on the device (Methods: Forward modeling, Eqs. 1-4;
@@ -140,6 +142,42 @@ oam_status oam_forward(const oam_model *model, const float *d_H, float *d_s, voi
 /* H = A^T s.  d_s: py*px*nt floats (input), d_H: py*px*nz floats (output,
  * fully overwritten). */
 oam_status oam_adjoint(const oam_model *model, const float *d_s, float *d_H, void *stream);
+
+/* ------------------------------------------------------ band-pass filtering */
+/* Results (second simulation, in vivo): the raw signals and the model matrix
+ * are band-pass filtered (0.5-80 MHz; 1-120 MHz in vivo) before inversion.
+ * The filter F is a zero-phase FIR with 2L + 1 even taps h[-L..L] (h[-m] =
+ * h[m]), run along time over every A-line of nt samples with samples outside
+ * [0, nt) taken as zero and the centred nt outputs kept:
+ *   (F s)[y][x][n] = sum_{m=-L}^{L} h[|m|] s[y][x][n - m].
+ * Filtering every slab column S[b][a][k][:] with F turns A into F A (F runs
+ * along time, A laterally and over depth, so they commute), and F is
+ * symmetric, so the filtered adjoint is A^T F. */
+#define OAM_MAX_FIR_HALF 8191
+
+/* Design taps[0..half_len] (host memory, half_len + 1 doubles) of the
+ * Blackman-windowed sinc band-pass [f_lo_hz, f_hi_hz]:
+ *   h[m] = w[m] (2 f_hi/fs sinc(2 f_hi m/fs) - 2 f_lo/fs sinc(2 f_lo m/fs)),
+ *   w[m] = 0.42 + 0.5 cos(pi m/(L+1)) + 0.08 cos(2 pi m/(L+1)),
+ * sinc(x) = sin(pi x)/(pi x).  Host only (no device call).  Errors:
+ * OAM_ERR_INVALID_ARG unless 0 <= f_lo < f_hi <= fs/2, 0 <= half_len <=
+ * OAM_MAX_FIR_HALF and taps != NULL. */
+oam_status oam_bandpass_taps(double f_lo_hz, double f_hi_hz, double fs_hz, int32_t half_len, double *taps);
+
+/* Make the model's forward operator F A and its adjoint A^T F (also inside
+ * the solvers, batches and autotuning) for the even FIR taps[0..half_len]
+ * (host memory, copied).  taps == NULL or half_len < 0 removes the filter.
+ * The transform length is the smallest power of two NF >= nt + min(L, nt-1);
+ * NF > 8192 is rejected (OAM_ERR_INVALID_ARG), as are non-finite taps.
+ * Allocates the filter's spectrum and one signal-sized staging buffer (owned
+ * by the model, counted in device_bytes) on `stream` and synchronises it.
+ * Set the filter before recording batches that use the model. */
+oam_status oam_model_set_filter(oam_model *model, const double *taps, int32_t half_len, void *stream);
+
+/* d_out = F d_in over py*px A-lines of nt samples with the model's filter
+ * (OAM_ERR_INVALID_ARG when none is set).  d_in and d_out may be the same
+ * buffer.  Use it on measured signals before solving with a filtered model. */
+oam_status oam_filter_signals(const oam_model *model, const float *d_in, float *d_out, void *stream);
 
 /* ---------------------------------------------------------------- solvers */
 /* MB-L2: Eq. 5 with the Tikhonov term of Eq. 6 (lambda = damp^2), solved by
@@ -203,6 +241,23 @@ oam_status oam_l1_fista(const oam_model *model, const float *d_s, float *d_x, co
  * cudaFree or allocating library routine is called. */
 oam_status oam_lsqr_noalloc(const oam_model *model, const float *d_s, float *d_x, const oam_lsqr_opts *opts,
                             oam_lsqr_info *info, void *stream);
+
+/* Tikhonov sweep: MB-L2 (Eq. 5 with Eq. 6) for n_damps weights lambda_i =
+ * damps[i]^2 at once.  LSQR's Golub-Kahan bidiagonalisation (u, v, alpha,
+ * beta) does not depend on the damp, only the plane rotations and the x and w
+ * updates do, so one forward and one adjoint per iteration serve every damp;
+ * each damp keeps its own rotations and its own w.  Result i is the same as
+ * oam_lsqr with damp = damps[i] and the same iters (same kernels, same
+ * reduction order).  d_x: host array of n_damps device pointers to volumes
+ * (outputs, 16-byte aligned); damps: host, finite, >= 0; 1 <= n_damps <=
+ * OAM_MAX_SWEEP.  d_work: at least oam_lsqr_sweep_work_bytes(model, n_damps)
+ * bytes, 256-byte aligned.  If infos != NULL (n_damps entries) the call
+ * synchronises `stream` and fills them. */
+#define OAM_MAX_SWEEP 32
+oam_status oam_lsqr_sweep(const oam_model *model, const float *d_s, int32_t n_damps, const double *damps,
+                          float *const *d_x, int32_t iters, oam_lsqr_info *infos, void *d_work, size_t work_bytes,
+                          void *stream);
+oam_status oam_lsqr_sweep_work_bytes(const oam_model *model, int32_t n_damps, size_t *bytes);
 
 /* Workspace bytes for solver 0 = LSQR, 1 = FISTA. */
 oam_status oam_solver_work_bytes(const oam_model *model, int32_t solver, size_t *bytes);

@@ -21,7 +21,11 @@ EXPORTED = ("oam_build_model", "oam_model_free", "oam_model_get_info", "oam_mode
             "oam_version", "oam_profile_enable", "oam_profile_read", "oam_launch_count", "oam_lsqr_noalloc",
             "oam_model_autotune", "oam_batch_create", "oam_batch_set_job", "oam_batch_run", "oam_batch_free",
             "oam_server_create", "oam_server_submit", "oam_server_poll", "oam_server_wait", "oam_server_stats",
-            "oam_server_stop", "oam_request_footprint")
+            "oam_server_stop", "oam_request_footprint", "oam_bandpass_taps", "oam_model_set_filter",
+            "oam_filter_signals", "oam_lsqr_sweep", "oam_lsqr_sweep_work_bytes")
+
+OAM_MAX_FIR_HALF = 8191
+OAM_MAX_SWEEP = 32
 
 
 class OamSensor(ctypes.Structure):
@@ -45,7 +49,7 @@ class OamModelInfo(ctypes.Structure):
                 ("n_orbits", ctypes.c_int32), ("precision", ctypes.c_int32), ("nnz", ctypes.c_int64),
                 ("flops_per_op", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
                 ("exec_flops_forward", ctypes.c_double), ("exec_flops_adjoint", ctypes.c_double),
-                ("op_bytes", ctypes.c_double)]
+                ("op_bytes", ctypes.c_double), ("filter_half_len", ctypes.c_int32), ("filter_size", ctypes.c_int32)]
 
 
 class OamLsqrOpts(ctypes.Structure):
@@ -134,6 +138,12 @@ def lib():
         L.oam_server_stats.argtypes = [vp, P(OamServerStats)]
         L.oam_server_stop.argtypes = [vp]
         L.oam_request_footprint.argtypes = [i32, P(OamGrid), P(sz)]
+        f64 = ctypes.c_double
+        L.oam_bandpass_taps.argtypes = [f64, f64, f64, i32, P(f64)]
+        L.oam_model_set_filter.argtypes = [vp, P(f64), i32, vp]
+        L.oam_filter_signals.argtypes = [vp, vp, vp, vp]
+        L.oam_lsqr_sweep.argtypes = [vp, vp, i32, P(f64), P(vp), i32, P(OamLsqrInfo), vp, sz, vp]
+        L.oam_lsqr_sweep_work_bytes.argtypes = [vp, i32, P(sz)]
         for f in EXPORTED:
             if f not in ("oam_status_string", "oam_version", "oam_launch_count"):
                 getattr(L, f).restype = ctypes.c_int
@@ -236,6 +246,47 @@ def oam_l1_fista(model, s, x, opts, work, stream=None, want_info=True):
 
 def oam_version():
     return lib().oam_version()
+
+
+def oam_bandpass_taps(f_lo_hz, f_hi_hz, fs_hz, half_len):
+    """Half taps h[0..half_len] of the windowed-sinc band-pass (host only), as a list."""
+    taps = (ctypes.c_double * (int(half_len) + 1))() if half_len >= 0 else None
+    _check("oam_bandpass_taps", lib().oam_bandpass_taps(float(f_lo_hz), float(f_hi_hz), float(fs_hz),
+                                                        int(half_len), taps))
+    return list(taps)
+
+
+def oam_model_set_filter(model, taps, stream=None):
+    """Filter the model's operators with the even FIR taps[0..L] (None removes it)."""
+    if taps is None:
+        _check("oam_model_set_filter", lib().oam_model_set_filter(model, None, -1, _stream(stream)))
+        return
+    arr = (ctypes.c_double * len(taps))(*[float(t) for t in taps])
+    _check("oam_model_set_filter", lib().oam_model_set_filter(model, arr, len(taps) - 1, _stream(stream)))
+
+
+def oam_filter_signals(model, s_in, s_out, stream=None):
+    _check("oam_filter_signals", lib().oam_filter_signals(model, _ptr(s_in), _ptr(s_out), _stream(stream)))
+
+
+def oam_lsqr_sweep_work_bytes(model, n_damps):
+    n = ctypes.c_size_t()
+    _check("oam_lsqr_sweep_work_bytes", lib().oam_lsqr_sweep_work_bytes(model, int(n_damps), ctypes.byref(n)))
+    return n.value
+
+
+def oam_lsqr_sweep(model, s, damps, xs, iters, work, stream=None, want_info=True):
+    """LSQR for every damp in ``damps`` from one bidiagonalisation; xs: one volume per damp."""
+    n = len(damps)
+    if len(xs) != n:
+        raise ValueError("one output volume per damp")
+    dv = (ctypes.c_double * n)(*[float(d) for d in damps])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    infos = (OamLsqrInfo * n)()
+    _check("oam_lsqr_sweep", lib().oam_lsqr_sweep(model, _ptr(s), n, dv, xp, int(iters),
+                                                  infos if want_info else None, _ptr(work),
+                                                  work.numel() * work.element_size(), _stream(stream)))
+    return list(infos)
 
 
 def oam_profile_enable(model, enable=True):

@@ -103,6 +103,7 @@ void free_model(oam_model *m, cudaStream_t st) {
   if (!m) return;
   tc_free(m, st);
   fft_free(m, st);
+  fir_free(m, st);
   for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
   void *ptrs[] = {m->d_status, m->d_tap_orbit, m->d_patch, m->d_band_lo, m->d_band, m->d_fwd_krange, m->d_fwd_off,
                   m->d_fwd, m->d_adj_nrange, m->d_adj_off, m->d_adj};
@@ -287,6 +288,8 @@ oam_status oam_model_get_info(const oam_model *m, oam_model_info *info) {
   info->exec_flops_forward = m->precision == OAM_PREC_FFT ? fft_flops(m) : tc_exec_flops(m, 0);
   info->exec_flops_adjoint = m->precision == OAM_PREC_FFT ? fft_flops(m) : tc_exec_flops(m, 1);
   info->op_bytes = fft_bytes(m);
+  info->filter_half_len = m->fir ? fir_half_len(m) : -1;
+  info->filter_size = m->fir ? fir_size(m) : 0;
   return OAM_OK;
 }
 
@@ -311,13 +314,23 @@ oam_status oam_adjoint(const oam_model *m, const float *d_s, float *d_H, void *s
 
 }  // extern "C"
 
+// A filtered model (oam_model_set_filter) applies F A and A^T F.
 oam_status oam::apply_forward(const oam_model *m, const float *H, float *s, cudaStream_t st) {
-  if (m->precision == OAM_PREC_BF16X3) return forward_tc(m, H, s, st);
-  if (m->precision == OAM_PREC_FFT) return forward_fft(m, H, s, st);
-  return forward_fp32(m, H, s, st);
+  oam_status rc;
+  if (m->precision == OAM_PREC_BF16X3) rc = forward_tc(m, H, s, st);
+  else if (m->precision == OAM_PREC_FFT) rc = forward_fft(m, H, s, st);
+  else rc = forward_fp32(m, H, s, st);
+  if (rc || !m->fir) return rc;
+  return fir_apply(m, s, s, st);
 }
 
 oam_status oam::apply_adjoint(const oam_model *m, const float *s, float *H, cudaStream_t st) {
+  if (m->fir) {
+    float *fs = fir_stage(m);
+    oam_status rc = fir_apply(m, s, fs, st);
+    if (rc) return rc;
+    s = fs;
+  }
   if (m->precision == OAM_PREC_BF16X3) return adjoint_tc(m, s, H, st);
   if (m->precision == OAM_PREC_FFT) return adjoint_fft(m, s, H, st);
   return adjoint_fp32(m, s, H, st);

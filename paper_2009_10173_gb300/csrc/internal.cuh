@@ -35,6 +35,8 @@ struct __align__(32) Patch {
 struct TcLayout;
 // Lateral-FFT form of the operators (OAM_PREC_FFT); defined in op_fft.cu.
 struct FftLayout;
+// Band-pass filter along time of a filtered model; defined in op_filter.cu.
+struct FirLayout;
 
 }  // namespace oam
 
@@ -84,6 +86,7 @@ struct oam_model {
   float *d_tc_part = nullptr;  // per-part partial sums of the tensor-core operators
 
   oam::FftLayout *fft = nullptr;  // lateral-FFT form (OAM_PREC_FFT)
+  oam::FirLayout *fir = nullptr;  // band-pass filter: forward is F A, adjoint A^T F (none: nullptr)
 
   int *d_status = nullptr;  // device error word (bounded waits that ran out)
   cudaStream_t alloc_stream = nullptr;  // stream of the stream-ordered allocations (the build stream)
@@ -158,6 +161,13 @@ oam_status forward_fft(const oam_model *m, const float *H, float *s, cudaStream_
 oam_status adjoint_fft(const oam_model *m, const float *s, float *H, cudaStream_t st);
 double fft_flops(const oam_model *m);
 double fft_bytes(const oam_model *m);
+
+// op_filter.cu: y = F x over the model's py*px A-lines (x and y may alias)
+oam_status fir_apply(const oam_model *m, const float *x, float *y, cudaStream_t st);
+float *fir_stage(const oam_model *m);
+int fir_half_len(const oam_model *m);
+int fir_size(const oam_model *m);
+void fir_free(oam_model *m, cudaStream_t st);
 
 // free every device buffer of a model with cudaFreeAsync on `st`, then the model
 void model_release(oam_model *m, cudaStream_t st);

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -29,6 +30,19 @@ struct Scalars {
   unsigned int pad;
   double partial_a[kRedBlocks];
   double partial_b[kRedBlocks];
+};
+
+// One damp of a Tikhonov sweep: its plane-rotation recurrence and the
+// coefficients of its x and w updates (the bidiagonalisation is shared).
+struct DampState {
+  double damp, rhobar, phibar, cx, cw, anorm2, arnorm;
+};
+constexpr int kMaxDamps = OAM_MAX_SWEEP;
+struct SweepDamps {
+  double d[kMaxDamps];
+};
+struct SweepX {
+  float *x[kMaxDamps];
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -145,6 +159,13 @@ __device__ __forceinline__ double sumsq(const float *x, size_t n) {
   return acc;
 }
 
+// FP64 products and sums rounded one operation at a time: the LSQR scalar
+// code is inlined at several call sites, and a fused multiply-add formed at
+// one site but not another would make a sweep's scalars differ from the
+// single solve's in the last bit.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double sumsq_rn(double a, double b) { return __dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)); }
+
 // beta_1 = ||s||
 __global__ void k_lsqr_beta0(const float *s, size_t n, Scalars *S) {
   const double acc = sumsq(s, n);
@@ -157,8 +178,9 @@ __global__ void k_lsqr_beta0(const float *s, size_t n, Scalars *S) {
   }
 }
 
-// alpha_1 = ||A^T u_1||, rhobar = alpha, phibar = beta
-__global__ void k_lsqr_alpha0(const float *th, size_t n, Scalars *S) {
+// alpha_1 = ||A^T u_1||, rhobar = alpha, phibar = beta (also for each of the
+// nd damps of a sweep in D)
+__global__ void k_lsqr_alpha0(const float *th, size_t n, Scalars *S, DampState *D, int nd) {
   const double acc = sumsq(th, n);
   double ta, tb;
   if (finish_blocks<false>(S, acc, 0.0, &ta, &tb) && threadIdx.x == 0) {
@@ -169,6 +191,12 @@ __global__ void k_lsqr_alpha0(const float *th, size_t n, Scalars *S) {
     S->phibar = S->beta;
     S->anorm2 = S->alpha * S->alpha;
     S->arnorm = S->alpha * S->beta;
+    for (int i = 0; i < nd; ++i) {
+      D[i].rhobar = S->alpha;
+      D[i].phibar = S->beta;
+      D[i].anorm2 = S->alpha * S->alpha;
+      D[i].arnorm = S->alpha * S->beta;
+    }
   }
 }
 
@@ -190,7 +218,7 @@ __global__ void k_lsqr_vw0(const float *th, float *v, float *w, float *x, size_t
 }
 
 // beta u = A v - alpha u   (u updated in place, unnormalised; beta from its norm)
-__global__ void k_lsqr_u(const float *ts, float *u, size_t n, Scalars *S, int it) {
+__global__ void k_lsqr_u(const float *ts, float *u, size_t n, Scalars *S, int it, DampState *D, int nd) {
   if (it > S->stop_at) return;
   const float al = (float)S->alpha;
   double acc = 0;
@@ -208,13 +236,36 @@ __global__ void k_lsqr_u(const float *ts, float *u, size_t n, Scalars *S, int it
   if (finish_blocks<false>(S, acc, 0.0, &ta, &tb) && threadIdx.x == 0) {
     S->beta = sqrt(ta);
     S->inv_beta = S->beta > 0 ? 1.0 / S->beta : 0.0;
-    S->anorm2 += S->beta * S->beta + S->damp * S->damp;
+    S->anorm2 = __dadd_rn(S->anorm2, sumsq_rn(S->beta, S->damp));
+    for (int i = 0; i < nd; ++i) D[i].anorm2 = __dadd_rn(D[i].anorm2, sumsq_rn(S->beta, D[i].damp));
     if (!(S->beta > 0)) S->stop_at = it;
   }
 }
 
-// alpha v = A^T u - beta v, then the plane rotations (FP64).
-__global__ void k_lsqr_v(const float *th, float *v, size_t n, Scalars *S, int it) {
+// One step's plane rotations (FP64): the first eliminates the damping term,
+// the second the sub-diagonal beta; updates (rhobar, phibar) and returns the
+// x and w coefficients phi/rho and theta/rho.
+__device__ __forceinline__ void lsqr_rotate(double alpha, double beta, double damp, double &rhobar, double &phibar,
+                                            double &cx, double &cw, double &arnorm) {
+  double rhobar1 = rhobar;
+  if (damp > 0) {
+    rhobar1 = sqrt(sumsq_rn(rhobar, damp));
+    phibar = mul_rn(rhobar / rhobar1, phibar);
+  }
+  const double rho = sqrt(sumsq_rn(rhobar1, beta));
+  const double c = rhobar1 / rho, sn = beta / rho;
+  const double theta = mul_rn(sn, alpha);
+  rhobar = -mul_rn(c, alpha);
+  const double phi = mul_rn(c, phibar);
+  phibar = mul_rn(sn, phibar);
+  cx = phi / rho;
+  cw = theta / rho;
+  arnorm = fabs(mul_rn(mul_rn(phibar, alpha), c));
+}
+
+// alpha v = A^T u - beta v, then the plane rotations (FP64), for the solve's
+// own damp and for each of the nd damps of a sweep in D.
+__global__ void k_lsqr_v(const float *th, float *v, size_t n, Scalars *S, int it, DampState *D, int nd) {
   if (it > S->stop_at) return;
   const float be = (float)S->beta;
   double acc = 0;
@@ -233,23 +284,19 @@ __global__ void k_lsqr_v(const float *th, float *v, size_t n, Scalars *S, int it
     const double alpha = sqrt(ta);
     S->alpha = alpha;
     S->inv_alpha = alpha > 0 ? 1.0 / alpha : 0.0;
-    S->anorm2 += alpha * alpha;
+    S->anorm2 = __dadd_rn(S->anorm2, mul_rn(alpha, alpha));
     if (!(alpha > 0) && S->stop_at > it) S->stop_at = it;
-    double rhobar = S->rhobar, phibar = S->phibar;
-    double rhobar1 = rhobar;
-    if (S->damp > 0) {
-      rhobar1 = sqrt(rhobar * rhobar + S->damp * S->damp);
-      phibar = (rhobar / rhobar1) * phibar;
+    double rhobar = S->rhobar, phibar = S->phibar, cx, cw, arnorm;
+    lsqr_rotate(alpha, S->beta, S->damp, rhobar, phibar, cx, cw, arnorm);
+    S->rhobar = rhobar;
+    S->phibar = phibar;
+    S->cx = cx;
+    S->cw = cw;
+    S->arnorm = arnorm;
+    for (int i = 0; i < nd; ++i) {
+      D[i].anorm2 = __dadd_rn(D[i].anorm2, mul_rn(alpha, alpha));
+      lsqr_rotate(alpha, S->beta, D[i].damp, D[i].rhobar, D[i].phibar, D[i].cx, D[i].cw, D[i].arnorm);
     }
-    const double rho = sqrt(rhobar1 * rhobar1 + S->beta * S->beta);
-    const double c = rhobar1 / rho, sn = S->beta / rho;
-    const double theta = sn * alpha;
-    S->rhobar = -c * alpha;
-    const double phi = c * phibar;
-    S->phibar = sn * phibar;
-    S->cx = phi / rho;
-    S->cw = theta / rho;
-    S->arnorm = fabs(S->phibar * alpha * c);
     S->iters_done = it + 1;
   }
 }
@@ -270,6 +317,63 @@ __global__ void k_lsqr_xw(float *v, float *w, float *x, size_t n, const Scalars 
     x[i] = fmaf(cx, ww, x[i]);
     w[i] = fmaf(-cw, ww, vv);
     v[i] = vv;
+  }
+}
+
+// Sweep start: every damp's state, then v = th / alpha, w_i = v, x_i = 0.
+__global__ void k_sweep_init(DampState *D, SweepDamps damps, int nd) {
+  const int i = threadIdx.x;
+  if (i < nd) D[i] = DampState{damps.d[i], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+}
+
+__global__ void k_sweep_vw0(const float *th, float *v, float *W, size_t wstride, SweepX X, int nd, size_t n,
+                            const Scalars *S) {
+  const float ia = (float)S->inv_alpha;
+  OAM_GROUPS(g, n / 4) {
+    const float4 t = mul4(ld4(th, g), ia);
+    st4(v, g, t);
+    for (int i = 0; i < nd; ++i) {
+      st4(W + i * wstride, g, t);
+      st4(X.x[i], g, make_float4(0.f, 0.f, 0.f, 0.f));
+    }
+  }
+  OAM_TAIL(j, n) {
+    const float t = th[j] * ia;
+    v[j] = t;
+    for (int i = 0; i < nd; ++i) {
+      W[i * wstride + j] = t;
+      X.x[i][j] = 0.0f;
+    }
+  }
+}
+
+// v = vhat / alpha once; then for each damp i: x_i += (phi_i/rho_i) w_i,
+// w_i = v - (theta_i/rho_i) w_i (the arithmetic of k_lsqr_xw).
+__global__ void k_sweep_xw(float *v, float *W, size_t wstride, SweepX X, int nd, size_t n, const Scalars *S,
+                           const DampState *D, int it) {
+  if (it > S->stop_at) return;
+  __shared__ float2 coef[kMaxDamps];
+  if (threadIdx.x < nd) coef[threadIdx.x] = make_float2((float)D[threadIdx.x].cx, (float)D[threadIdx.x].cw);
+  __syncthreads();
+  const float ia = (float)S->inv_alpha;
+  OAM_GROUPS(g, n / 4) {
+    const float4 vv = mul4(ld4(v, g), ia);
+    for (int i = 0; i < nd; ++i) {
+      float *w = W + i * wstride, *x = X.x[i];
+      const float4 ww = ld4(w, g);
+      st4(x, g, fma4(coef[i].x, ww, ld4(x, g)));
+      st4(w, g, fma4(-coef[i].y, ww, vv));
+    }
+    st4(v, g, vv);
+  }
+  OAM_TAIL(j, n) {
+    const float vv = v[j] * ia;
+    for (int i = 0; i < nd; ++i) {
+      const float ww = W[i * wstride + j];
+      X.x[i][j] = fmaf(coef[i].x, ww, X.x[i][j]);
+      W[i * wstride + j] = fmaf(-coef[i].y, ww, vv);
+    }
+    v[j] = vv;
   }
 }
 
@@ -419,18 +523,18 @@ extern "C" oam_status oam_lsqr(const oam_model *m, const float *d_s, float *d_x,
   k_scale<<<VG, kThreads, 0, st>>>(u, d_s, ns, &S->inv_beta, nullptr, 0);
   OAM_LAUNCH_CHECK();
   OAM_TRY(apply_adjoint(m, u, th, st));
-  k_lsqr_alpha0<<<RG, kThreads, 0, st>>>(th, nv, S);
+  k_lsqr_alpha0<<<RG, kThreads, 0, st>>>(th, nv, S, nullptr, 0);
   OAM_LAUNCH_CHECK();
   k_lsqr_vw0<<<VG, kThreads, 0, st>>>(th, v, w, d_x, nv, S);
   OAM_LAUNCH_CHECK();
   for (int it = 0; it < opts->iters; ++it) {
     OAM_TRY(apply_forward(m, v, ts, st));
-    k_lsqr_u<<<RG, kThreads, 0, st>>>(ts, u, ns, S, it);
+    k_lsqr_u<<<RG, kThreads, 0, st>>>(ts, u, ns, S, it, nullptr, 0);
     OAM_LAUNCH_CHECK();
     k_scale<<<VG, kThreads, 0, st>>>(u, u, ns, &S->inv_beta, S, it);
     OAM_LAUNCH_CHECK();
     OAM_TRY(apply_adjoint(m, u, th, st));
-    k_lsqr_v<<<RG, kThreads, 0, st>>>(th, v, nv, S, it);
+    k_lsqr_v<<<RG, kThreads, 0, st>>>(th, v, nv, S, it, nullptr, 0);
     OAM_LAUNCH_CHECK();
     k_lsqr_xw<<<VG, kThreads, 0, st>>>(v, w, d_x, nv, S, it);
     OAM_LAUNCH_CHECK();
@@ -444,6 +548,100 @@ extern "C" oam_status oam_lsqr(const oam_model *m, const float *d_s, float *d_x,
     info->rnorm = std::fabs(h.phibar);
     info->arnorm = h.arnorm;
     info->anorm = std::sqrt(h.anorm2);
+  }
+  return OAM_OK;
+}
+
+namespace {
+
+// Sweep workspace: scalars, the damp states, u and A v (signals), v and A^T u
+// (volumes), then one w per damp.
+struct SweepLayout {
+  size_t scal, damps, sig, vol;
+  size_t total(int nd) const { return scal + damps + 2 * sig + (2 + (size_t)nd) * vol; }
+};
+
+SweepLayout sweep_layout(const oam_model *m) {
+  const WorkLayout W = layout(m);
+  return SweepLayout{W.scal, align256(sizeof(DampState) * kMaxDamps), W.sig, W.vol};
+}
+
+}  // namespace
+
+extern "C" oam_status oam_lsqr_sweep_work_bytes(const oam_model *m, int32_t n_damps, size_t *bytes) {
+  if (!m || !bytes || n_damps < 1 || n_damps > kMaxDamps) return OAM_ERR_INVALID_ARG;
+  *bytes = sweep_layout(m).total(n_damps);
+  return OAM_OK;
+}
+
+extern "C" oam_status oam_lsqr_sweep(const oam_model *m, const float *d_s, int32_t n_damps, const double *damps,
+                                     float *const *d_x, int32_t iters, oam_lsqr_info *infos, void *d_work,
+                                     size_t work_bytes, void *stream) {
+  if (!m || !d_s || !damps || !d_x || !d_work || iters < 0) return OAM_ERR_INVALID_ARG;
+  if (n_damps < 1 || n_damps > kMaxDamps) return OAM_ERR_INVALID_ARG;
+  const SweepLayout L = sweep_layout(m);
+  if (work_bytes < L.total(n_damps) || (reinterpret_cast<uintptr_t>(d_work) & 255)) return OAM_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_s) & 15) return OAM_ERR_INVALID_ARG;
+  SweepDamps dv{};
+  SweepX X{};
+  for (int i = 0; i < n_damps; ++i) {
+    if (!(damps[i] >= 0) || !std::isfinite(damps[i])) return OAM_ERR_INVALID_ARG;
+    if (!d_x[i] || (reinterpret_cast<uintptr_t>(d_x[i]) & 15)) return OAM_ERR_INVALID_ARG;
+    dv.d[i] = damps[i];
+    X.x[i] = d_x[i];
+  }
+  cudaStream_t st = as_stream(stream);
+  char *base = static_cast<char *>(d_work);
+  Scalars *S = reinterpret_cast<Scalars *>(base);
+  DampState *D = reinterpret_cast<DampState *>(base + L.scal);
+  char *vec = base + L.scal + L.damps;
+  float *u = reinterpret_cast<float *>(vec);
+  float *ts = reinterpret_cast<float *>(vec + L.sig);
+  float *v = reinterpret_cast<float *>(vec + 2 * L.sig);
+  float *th = reinterpret_cast<float *>(vec + 2 * L.sig + L.vol);
+  float *W = reinterpret_cast<float *>(vec + 2 * L.sig + 2 * L.vol);
+  const size_t wstride = L.vol / sizeof(float);
+  const size_t ns = sig_elems(m), nv = vol_elems(m);
+  const int RG = red_grid(m), VG = vec_grid(m);
+
+  k_init_scalars<<<1, 1, 0, st>>>(S, 0.0, 1.0, 0.0, 0.0);
+  OAM_LAUNCH_CHECK();
+  k_sweep_init<<<1, kMaxDamps, 0, st>>>(D, dv, n_damps);
+  OAM_LAUNCH_CHECK();
+  k_lsqr_beta0<<<RG, kThreads, 0, st>>>(d_s, ns, S);
+  OAM_LAUNCH_CHECK();
+  k_scale<<<VG, kThreads, 0, st>>>(u, d_s, ns, &S->inv_beta, nullptr, 0);
+  OAM_LAUNCH_CHECK();
+  OAM_TRY(apply_adjoint(m, u, th, st));
+  k_lsqr_alpha0<<<RG, kThreads, 0, st>>>(th, nv, S, D, n_damps);
+  OAM_LAUNCH_CHECK();
+  k_sweep_vw0<<<VG, kThreads, 0, st>>>(th, v, W, wstride, X, n_damps, nv, S);
+  OAM_LAUNCH_CHECK();
+  for (int it = 0; it < iters; ++it) {
+    OAM_TRY(apply_forward(m, v, ts, st));
+    k_lsqr_u<<<RG, kThreads, 0, st>>>(ts, u, ns, S, it, D, n_damps);
+    OAM_LAUNCH_CHECK();
+    k_scale<<<VG, kThreads, 0, st>>>(u, u, ns, &S->inv_beta, S, it);
+    OAM_LAUNCH_CHECK();
+    OAM_TRY(apply_adjoint(m, u, th, st));
+    k_lsqr_v<<<RG, kThreads, 0, st>>>(th, v, nv, S, it, D, n_damps);
+    OAM_LAUNCH_CHECK();
+    k_sweep_xw<<<VG, kThreads, 0, st>>>(v, W, wstride, X, n_damps, nv, S, D, it);
+    OAM_LAUNCH_CHECK();
+  }
+  if (infos) {
+    Scalars h;
+    std::vector<DampState> hd(n_damps);
+    OAM_CUDA_TRY(cudaMemcpyAsync(&h, S, offsetof(Scalars, partial_a), cudaMemcpyDeviceToHost, st));
+    OAM_CUDA_TRY(cudaMemcpyAsync(hd.data(), D, sizeof(DampState) * n_damps, cudaMemcpyDeviceToHost, st));
+    OAM_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < n_damps; ++i) {
+      infos[i].iters_done = h.iters_done;
+      infos[i].stop_reason = (h.stop_at != 0x7fffffff) ? 1 : 0;
+      infos[i].rnorm = std::fabs(hd[i].phibar);
+      infos[i].arnorm = hd[i].arnorm;
+      infos[i].anorm = std::sqrt(hd[i].anorm2);
+    }
   }
   return OAM_OK;
 }

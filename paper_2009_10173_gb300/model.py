@@ -81,6 +81,30 @@ class Model:
         info = B.oam_lsqr(self.handle, s, out, B.OamLsqrOpts(iters, damp), self.workspace(0), stream, want_info)
         return out, info
 
+    def lsqr_sweep(self, s, iters, damps, stream=None, want_info=True):
+        """MB-L2 for each damp (lambda = damp^2) from one bidiagonalisation: (volumes, infos)."""
+        self._check(s, self.sig_shape)
+        xs = [self.empty_volume() for _ in damps]
+        n = B.oam_lsqr_sweep_work_bytes(self.handle, len(damps))
+        w = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
+        off = (-w.data_ptr()) % 256
+        infos = B.oam_lsqr_sweep(self.handle, s, damps, xs, iters, w[off:off + n], stream, want_info)
+        return xs, infos
+
+    # ------------------------------------------------------------ band-pass filter
+    def set_filter(self, taps, stream=None):
+        """Make forward F A and adjoint A^T F for the even FIR taps[0..L] (None removes it)."""
+        B.oam_model_set_filter(self.handle, taps, stream)
+        self.info = B.oam_model_get_info(self.handle)
+
+    def filter_signals(self, s, out=None, stream=None):
+        """F s with the model's filter (out may be s)."""
+        self._check(s, self.sig_shape)
+        out = self.empty_signals() if out is None else out
+        self._check(out, self.sig_shape)
+        B.oam_filter_signals(self.handle, s, out, stream)
+        return out
+
     def fista(self, s, iters, power_iters=20, lam=-1.0, lambda_rel=1e-3, L=0.0, nonneg=True, v0=None,
               compute_objective=False, out=None, stream=None, want_info=True):
         self._check(s, self.sig_shape)
