@@ -15,14 +15,17 @@
 //
 // On the device F is a circular convolution of length NF, a power of two with
 // NF >= nt + min(L, nt - 1), so no wrap reaches [0, nt).  Each pair of A-lines
-// is one complex line (real and imaginary parts), transformed in shared memory
-// by a radix-2 decimation-in-frequency FFT (natural order in, bit-reversed
-// order out), multiplied by the filter's spectrum (real because the taps are
-// even, pre-scaled by 1/NF, stored in bit-reversed order) and transformed back
-// by a decimation-in-time inverse FFT (bit-reversed in, natural order out), so
-// no permutation pass is needed.  The three smallest spans of both transforms
-// and the product run in registers on 8-point groups; the other stages go two
-// per shared-memory pass.  Each sample is read from and written to HBM once.
+// is one complex line (real and imaginary parts), transformed by a radix-2
+// decimation-in-frequency FFT (natural order in, bit-reversed order out),
+// multiplied by the filter's spectrum (real because the taps are even,
+// pre-scaled by 1/NF, stored in bit-reversed order) and transformed back by a
+// decimation-in-time inverse FFT (bit-reversed in, natural order out), so no
+// permutation pass is needed.  Stages run in registers, up to four per pass
+// over shared memory: the first forward pass reads the A-lines from global
+// memory, the three smallest spans of both transforms and the product share
+// one pass on 8-point groups, and the last inverse pass writes the filtered
+// A-lines to global memory.  Each sample is read from and written to HBM once
+// and goes through shared memory four times each way at NF = 2048.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -50,9 +53,9 @@ namespace {
 using namespace oam::fftdev;
 
 constexpr int kFirThreads = 256;
-constexpr int kFirMaxSize = 8192;  // largest transform: 96 KB of shared memory (twiddles, one line pair)
+constexpr int kFirMaxSize = 8192;  // largest transform: 65 KB of shared memory per line pair
 
-size_t fir_smem(int NF, int KC) { return sizeof(float2) * ((size_t)NF / 2 + (size_t)KC * NF + NF / 8); }
+size_t fir_smem(int NF, int KC) { return sizeof(float2) * ((size_t)KC * NF + NF / 8); }
 
 // Shared-memory layout of KC interleaved complex lines: point i of line c at
 // i*KC + c, plus one pad slot after every 8 points so that the 8-point groups
@@ -61,94 +64,130 @@ template <int KC>
 __device__ __forceinline__ int slot(int i, int c) { return i * KC + c + (i >> 3); }
 
 constexpr float kRsqrt2 = 0.70710678118654752f;  // cos(pi/4) = sin(pi/4)
+constexpr float kCos8 = 0.92387953251128676f;    // cos(pi/8)
+constexpr float kSin8 = 0.38268343236508977f;    // sin(pi/8)
 
-// The outer decimation-in-frequency stages (spans P/2 down to 8; sign -1):
-// span s maps (u, w) at (j, j + s) of each block of 2s to (u + w, (u - w) W_2s^j).
-// Two stages per shared-memory pass (spans 2h and h act on {i, i+h, i+2h, i+3h});
-// a leading single stage when their count log2 P - 3 is odd.
-template <int KC>
-__device__ void dif_outer(float2 *a, const float2 *tw, int P, int lgP) {
-  int h;
-  if ((lgP - 3) & 1) {
-    const int s = P >> 1;
-    for (int id = threadIdx.x; id < s * KC; id += blockDim.x) {
-      const int c = id % KC, j = id / KC;
-      const float2 u = a[slot<KC>(j, c)], w = a[slot<KC>(j + s, c)];
-      a[slot<KC>(j, c)] = make_float2(u.x + w.x, u.y + w.y);
-      a[slot<KC>(j + s, c)] = cmul(make_float2(u.x - w.x, u.y - w.y), tw[j]);
-    }
-    __syncthreads();
-    h = P >> 3;
-  } else {
-    h = P >> 2;
-  }
-  for (; h >= 8; h >>= 2) {
-    const int s1 = P / (4 * h), s2 = P / (2 * h);  // W_4h^j = tw[j s1], W_2h^j = tw[j s2]
-    for (int id = threadIdx.x; id < (P >> 2) * KC; id += blockDim.x) {
-      const int c = id % KC, t = id / KC;
-      const int q = t & (h - 1);
-      const int i0 = 4 * (t - q) + q;
-      const float2 x0 = a[slot<KC>(i0, c)], x1 = a[slot<KC>(i0 + h, c)];
-      const float2 x2 = a[slot<KC>(i0 + 2 * h, c)], x3 = a[slot<KC>(i0 + 3 * h, c)];
-      const float2 y0 = make_float2(x0.x + x2.x, x0.y + x2.y);
-      const float2 y2 = cmul(make_float2(x0.x - x2.x, x0.y - x2.y), tw[q * s1]);
-      const float2 y1 = make_float2(x1.x + x3.x, x1.y + x3.y);
-      const float2 y3 = cmul(make_float2(x1.x - x3.x, x1.y - x3.y), tw[(q + h) * s1]);
-      const float2 w = tw[q * s2];
-      a[slot<KC>(i0, c)] = make_float2(y0.x + y1.x, y0.y + y1.y);
-      a[slot<KC>(i0 + h, c)] = cmul(make_float2(y0.x - y1.x, y0.y - y1.y), w);
-      a[slot<KC>(i0 + 2 * h, c)] = make_float2(y2.x + y3.x, y2.y + y3.y);
-      a[slot<KC>(i0 + 3 * h, c)] = cmul(make_float2(y2.x - y3.x, y2.y - y3.y), w);
-    }
-    __syncthreads();
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// W_N^u = exp(-2 pi i u / N) for N <= 16 (u < N/2), from the constants above.
+__device__ __forceinline__ float2 w_small(int N, int u) {
+  const int e = u * (16 / N);  // in sixteenths
+  switch (e) {
+    case 0: return make_float2(1.0f, 0.0f);
+    case 1: return make_float2(kCos8, -kSin8);
+    case 2: return make_float2(kRsqrt2, -kRsqrt2);
+    case 3: return make_float2(kSin8, -kCos8);
+    case 4: return make_float2(0.0f, -1.0f);
+    case 5: return make_float2(-kSin8, -kCos8);
+    case 6: return make_float2(-kRsqrt2, -kRsqrt2);
+    default: return make_float2(-kCos8, -kSin8);  // 7
   }
 }
 
-// The outer decimation-in-time inverse stages (spans 8 up to P/2; sign +1):
-// span s maps (u, w) at (j, j + s) to (u + w conj(W_2s^j), u - w conj(W_2s^j)).
-// Two stages per pass (spans h and 2h), a trailing single stage when their
-// count is odd.
-template <int KC>
-__device__ void dit_outer(float2 *a, const float2 *tw, int P, int lgP) {
-  int h = 8;
-  for (; 4 * h <= P; h <<= 2) {
-    const int s1 = P / (2 * h), s2 = P / (4 * h);  // W_2h^j = tw[j s1], W_4h^j = tw[j s2]
-    for (int id = threadIdx.x; id < (P >> 2) * KC; id += blockDim.x) {
-      const int c = id % KC, t = id / KC;
-      const int q = t & (h - 1);
-      const int i0 = 4 * (t - q) + q;
-      float2 x0 = a[slot<KC>(i0, c)], x1 = a[slot<KC>(i0 + h, c)];
-      float2 x2 = a[slot<KC>(i0 + 2 * h, c)], x3 = a[slot<KC>(i0 + 3 * h, c)];
-      float2 w = tw[q * s1];
-      w.y = -w.y;
-      float2 y = cmul(x1, w);
-      x1 = make_float2(x0.x - y.x, x0.y - y.y);
-      x0 = make_float2(x0.x + y.x, x0.y + y.y);
-      y = cmul(x3, w);
-      x3 = make_float2(x2.x - y.x, x2.y - y.y);
-      x2 = make_float2(x2.x + y.x, x2.y + y.y);
-      float2 wa = tw[q * s2], wb = tw[(q + h) * s2];
-      wa.y = -wa.y;
-      wb.y = -wb.y;
-      y = cmul(x2, wa);
-      a[slot<KC>(i0, c)] = make_float2(x0.x + y.x, x0.y + y.y);
-      a[slot<KC>(i0 + 2 * h, c)] = make_float2(x0.x - y.x, x0.y - y.y);
-      y = cmul(x3, wb);
-      a[slot<KC>(i0 + h, c)] = make_float2(x1.x + y.x, x1.y + y.y);
-      a[slot<KC>(i0 + 3 * h, c)] = make_float2(x1.x - y.x, x1.y - y.y);
+// One shared-memory pass of R = 2^r decimation-in-frequency stages with spans
+// 2^(k+r-1) down to 2^k, in registers, for point group (c, q, blk): the
+// points i0 + m 2^k, i0 = blk 2^(k+r) + q, q < 2^k.  Span S = 2^(k+j) maps
+// (u, w) at (p, p + S) to (u + w, (u - w) W_2S^(p mod S)) with
+// p mod S = q + (m mod 2^j) 2^k, so its twiddle is W_2S^q W_2^(j+1)^(m mod 2^j):
+// the first factor is b^(2^(r-1-j)) for b = W_2^(k+r)^q (one sincospif, then
+// squarings), the second a constant.  Loads come from global memory (points at
+// or beyond nt read as zero) when kFromGlobal, else from shared memory.
+template <int KC, int r, bool kFromGlobal>
+__device__ __forceinline__ void dif_pass(float2 *a, int NF, int k, const float *x, long long line0, long long n_lines,
+                                         int nt) {
+  constexpr int R = 1 << r;
+  const int groups = NF >> r;
+  for (int id = threadIdx.x; id < groups * KC; id += blockDim.x) {
+    const int c = id % KC, t = id / KC;
+    const int q = t & ((1 << k) - 1), blk = t >> k;
+    const int i0 = (blk << (k + r)) | q;
+    float2 v[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int n = i0 + (m << k);
+      if (kFromGlobal) {
+        const long long l0 = line0 + 2 * c, l1 = l0 + 1;
+        float re = 0.0f, im = 0.0f;
+        if (n < nt) {
+          if (l0 < n_lines) re = x[l0 * nt + n];
+          if (l1 < n_lines) im = x[l1 * nt + n];
+        }
+        v[m] = make_float2(re, im);
+      } else {
+        v[m] = a[slot<KC>(n, c)];
+      }
     }
-    __syncthreads();
+    float2 pw[r];  // pw[j] = W_2^(k+j+1)^q
+    sincospif(-2.0f * (float)q / (float)(1 << (k + r)), &pw[r - 1].y, &pw[r - 1].x);
+#pragma unroll
+    for (int j = r - 2; j >= 0; --j) pw[j] = cmul(pw[j + 1], pw[j + 1]);
+#pragma unroll
+    for (int j = r - 1; j >= 0; --j) {
+      const int S = 1 << j;
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        if (m & S) continue;
+        const float2 u = v[m], w = v[m + S];
+        v[m] = cadd(u, w);
+        const int um = m & (S - 1);
+        const float2 tw = um == 0 ? pw[j] : cmul(pw[j], w_small(2 * S, um));
+        v[m + S] = cmul(csub(u, w), tw);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) a[slot<KC>(i0 + (m << k), c)] = v[m];
   }
-  if (2 * h == P) {  // h = P/2 left over
-    for (int id = threadIdx.x; id < h * KC; id += blockDim.x) {
-      const int c = id % KC, j = id / KC;
-      float2 w = tw[j];
-      w.y = -w.y;
-      const float2 u = a[slot<KC>(j, c)], v = cmul(a[slot<KC>(j + h, c)], w);
-      a[slot<KC>(j, c)] = make_float2(u.x + v.x, u.y + v.y);
-      a[slot<KC>(j + h, c)] = make_float2(u.x - v.x, u.y - v.y);
+}
+
+// The matching decimation-in-time inverse pass (spans 2^k up to 2^(k+r-1)):
+// (u, w) at (p, p + S) go to (u + w conj(W), u - w conj(W)), W as above.
+// Results go to global memory (points below nt only) when kToGlobal, else
+// back to shared memory.
+template <int KC, int r, bool kToGlobal>
+__device__ __forceinline__ void dit_pass(float2 *a, int NF, int k, float *y, long long line0, long long n_lines,
+                                         int nt) {
+  constexpr int R = 1 << r;
+  const int groups = NF >> r;
+  for (int id = threadIdx.x; id < groups * KC; id += blockDim.x) {
+    const int c = id % KC, t = id / KC;
+    const int q = t & ((1 << k) - 1), blk = t >> k;
+    const int i0 = (blk << (k + r)) | q;
+    float2 v[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = a[slot<KC>(i0 + (m << k), c)];
+    float2 pw[r];
+    sincospif(-2.0f * (float)q / (float)(1 << (k + r)), &pw[r - 1].y, &pw[r - 1].x);
+#pragma unroll
+    for (int j = r - 2; j >= 0; --j) pw[j] = cmul(pw[j + 1], pw[j + 1]);
+#pragma unroll
+    for (int j = 0; j < r; ++j) {
+      const int S = 1 << j;
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        if (m & S) continue;
+        const int um = m & (S - 1);
+        const float2 tw = um == 0 ? pw[j] : cmul(pw[j], w_small(2 * S, um));
+        const float2 u = v[m], w = cmul(v[m + S], cconj(tw));
+        v[m] = cadd(u, w);
+        v[m + S] = csub(u, w);
+      }
     }
-    __syncthreads();
+    if (kToGlobal) {
+      const long long l0 = line0 + 2 * c, l1 = l0 + 1;
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int n = i0 + (m << k);
+        if (n < nt) {
+          if (l0 < n_lines) y[l0 * nt + n] = v[m].x;
+          if (l1 < n_lines) y[l1 * nt + n] = v[m].y;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < R; ++m) a[slot<KC>(i0 + (m << k), c)] = v[m];
+    }
   }
 }
 
@@ -217,41 +256,61 @@ __device__ __forceinline__ void mid_group(float2 *a, int g, int c, const float4 
   for (int j = 0; j < 8; ++j) a[slot<KC>(8 * g + j, c)] = v[j];
 }
 
-// y = F x for n_lines A-lines of nt samples (x and y may alias).  Block b
-// holds real lines 2 KC b .. 2 KC b + 2 KC - 1; complex line c carries real
-// lines 2c (real part) and 2c + 1 (imaginary part).  hb: the filter's
-// spectrum over NF, in bit-reversed order (NF floats).
+// First forward pass (from global memory) and last inverse pass (to global
+// memory) with r0 = ((log2 NF - 3) mod 4, or 4) stages at k = log2 NF - r0.
+template <int KC, bool kForward>
+__device__ __forceinline__ void edge_pass(int r0, float2 *a, int NF, int k, const float *x, float *y, long long line0,
+                                          long long n_lines, int nt) {
+  switch (r0) {
+    case 1:
+      if (kForward) dif_pass<KC, 1, true>(a, NF, k, x, line0, n_lines, nt);
+      else dit_pass<KC, 1, true>(a, NF, k, y, line0, n_lines, nt);
+      break;
+    case 2:
+      if (kForward) dif_pass<KC, 2, true>(a, NF, k, x, line0, n_lines, nt);
+      else dit_pass<KC, 2, true>(a, NF, k, y, line0, n_lines, nt);
+      break;
+    case 3:
+      if (kForward) dif_pass<KC, 3, true>(a, NF, k, x, line0, n_lines, nt);
+      else dit_pass<KC, 3, true>(a, NF, k, y, line0, n_lines, nt);
+      break;
+    default:
+      if (kForward) dif_pass<KC, 4, true>(a, NF, k, x, line0, n_lines, nt);
+      else dit_pass<KC, 4, true>(a, NF, k, y, line0, n_lines, nt);
+      break;
+  }
+}
+
+// y = F x for n_lines A-lines of nt samples (x and y may alias: a block reads
+// all of its lines before it writes any).  Block b holds real lines
+// 2 KC b .. 2 KC b + 2 KC - 1; complex line c carries real lines 2c (real
+// part) and 2c + 1 (imaginary part).  NF >= 16.  hb: the filter's spectrum
+// over NF, in bit-reversed order (NF floats, 16-byte aligned).  Forward
+// stages: spans NF/2 .. 2^k0 straight from global memory, then passes of four
+// down to span 8, then the register middle (spans 4, 2, 1, the product and
+// back); the inverse mirrors them and its last pass writes to global memory.
 template <int KC>
 __global__ void __launch_bounds__(kFirThreads) k_fir_lines(const float *x, float *y, long long n_lines, int nt,
                                                            int NF, int lgNF, const float *__restrict__ hb) {
-  extern __shared__ float2 sm[];
-  float2 *tw = sm, *a = sm + (NF >> 1);
+  extern __shared__ float2 a[];
   const long long line0 = (long long)blockIdx.x * (2 * KC);
-  load_twiddles(tw, NF);
-  for (int i = threadIdx.x; i < KC * NF; i += blockDim.x) {
-    const int c = i % KC, n = i / KC;
-    const long long l0 = line0 + 2 * c, l1 = l0 + 1;
-    float re = 0.0f, im = 0.0f;
-    if (n < nt) {
-      if (l0 < n_lines) re = x[l0 * nt + n];
-      if (l1 < n_lines) im = x[l1 * nt + n];
-    }
-    a[slot<KC>(n, c)] = make_float2(re, im);
-  }
+  const int r0 = ((lgNF - 3) & 3) ? ((lgNF - 3) & 3) : 4;
+  const int k0 = lgNF - r0;
+  edge_pass<KC, true>(r0, a, NF, k0, x, nullptr, line0, n_lines, nt);
   __syncthreads();
-  dif_outer<KC>(a, tw, NF, lgNF);
+  for (int k = k0 - 4; k >= 3; k -= 4) {
+    dif_pass<KC, 4, false>(a, NF, k, nullptr, 0, 0, 0);
+    __syncthreads();
+  }
   const int groups = NF >> 3;
   for (int id = threadIdx.x; id < groups * KC; id += blockDim.x)
     mid_group<KC>(a, id % groups, id / groups, reinterpret_cast<const float4 *>(hb));
   __syncthreads();
-  dit_outer<KC>(a, tw, NF, lgNF);
-  for (int i = threadIdx.x; i < KC * nt; i += blockDim.x) {
-    const int c = i % KC, n = i / KC;
-    const long long l0 = line0 + 2 * c, l1 = l0 + 1;
-    const float2 v = a[slot<KC>(n, c)];
-    if (l0 < n_lines) y[l0 * nt + n] = v.x;
-    if (l1 < n_lines) y[l1 * nt + n] = v.y;
+  for (int k = 3; k + 4 <= k0; k += 4) {
+    dit_pass<KC, 4, false>(a, NF, k, nullptr, 0, 0, 0);
+    __syncthreads();
   }
+  edge_pass<KC, false>(r0, a, NF, k0, nullptr, y, line0, n_lines, nt);
 }
 
 oam_status set_smem(const void *fn, size_t bytes) {
@@ -336,7 +395,7 @@ oam_status oam_model_set_filter(oam_model *m, const double *taps, int32_t half_l
     if (!std::isfinite(taps[i])) return OAM_ERR_INVALID_ARG;
   const int nt = m->grid.nt;
   const int Le = std::min(half_len, nt - 1);  // taps that can reach [0, nt)
-  int NF = 8, lg = 3;  // at least one 8-point group
+  int NF = 16, lg = 4;  // at least one outer stage on each side of the 8-point middle
   while (NF < nt + Le) {
     NF <<= 1;
     ++lg;
