@@ -41,9 +41,9 @@ TC_TRAFFIC_BYTES = 440.8e6 * 11160 / 2945
 # 0.243 GB written).  Set to None when those kernels change.
 FFT_TRAFFIC_BYTES = 1.4327e9
 # Band-pass filter along time: half length of the 0.5-80 MHz FIR, and the DRAM
-# bytes of one application (no ncu capture of this kernel yet: null).
+# bytes of one application (ncu, profiles/k_fir_lines_200x200x1024_L511.md).
 FIR_HALF = 511
-FIR_TRAFFIC_BYTES = None
+FIR_TRAFFIC_BYTES = 163.96e6 + 120.01e6
 
 
 def parse():

@@ -40,7 +40,7 @@ namespace oam {
 
 struct FirLayout {
   int L = 0;                 // half length as set (taps with |m| >= nt never reach the output)
-  int NF = 0, lgNF = 0, KC = 0;  // transform size, its log2, complex lines per block
+  int NF = 0, lgNF = 0, KP = 0;  // transform size, its log2, complex line pairs per block
   float *d_hb = nullptr;     // [NF] spectrum of the taps over NF, in bit-reversed order
   float *d_stage = nullptr;  // signal-sized staging buffer: F s ahead of the adjoint
   size_t bytes = 0;          // device bytes of the two buffers
@@ -53,23 +53,13 @@ namespace {
 using namespace oam::fftdev;
 
 constexpr int kFirThreads = 256;
-constexpr int kFirMaxSize = 8192;  // largest transform: 65 KB of shared memory per line pair
+constexpr int kFirMaxSize = 8192;  // largest transform: 132 KB of shared memory per line pair
 
-size_t fir_smem(int NF, int KC) { return sizeof(float2) * ((size_t)KC * NF + NF / 8); }
-
-// Shared-memory layout of KC interleaved complex lines: point i of line c at
-// i*KC + c, plus one pad slot after every 8 points so that the 8-point groups
-// of the middle pass, read with the group index fastest, spread over all banks.
-template <int KC>
-__device__ __forceinline__ int slot(int i, int c) { return i * KC + c + (i >> 3); }
+size_t fir_smem(int NF, int KP) { return sizeof(ulonglong2) * ((size_t)KP * NF + NF / 8); }
 
 constexpr float kRsqrt2 = 0.70710678118654752f;  // cos(pi/4) = sin(pi/4)
 constexpr float kCos8 = 0.92387953251128676f;    // cos(pi/8)
 constexpr float kSin8 = 0.38268343236508977f;    // sin(pi/8)
-
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
 // W_N^u = exp(-2 pi i u / N) for N <= 16 (u < N/2), from the constants above.
 __device__ __forceinline__ float2 w_small(int N, int u) {
@@ -86,37 +76,104 @@ __device__ __forceinline__ float2 w_small(int N, int u) {
   }
 }
 
+// Packed FP32 pairs (two lanes of one 64-bit register) and their arithmetic.
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {  // a b + c
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_splat(float v) { return f2_pack(v, v); }
+__device__ __forceinline__ float2 f2_unpack(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+
+// The same point of two complex lines c and c + 1: re = (re_c, re_c+1),
+// im = (im_c, im_c+1).  Every operation below acts on both lines at once.
+struct Cx2 {
+  uint64_t re, im;
+};
+__device__ __forceinline__ Cx2 x_add(Cx2 a, Cx2 b) { return Cx2{f2_add(a.re, b.re), f2_add(a.im, b.im)}; }
+__device__ __forceinline__ Cx2 x_sub(Cx2 a, Cx2 b) { return Cx2{f2_sub(a.re, b.re), f2_sub(a.im, b.im)}; }
+// a w for one complex w shared by both lines
+__device__ __forceinline__ Cx2 x_mul(Cx2 a, float2 w) {
+  const uint64_t wr = f2_splat(w.x), wi = f2_splat(w.y), nwi = f2_splat(-w.y);
+  return Cx2{f2_fma(a.re, wr, f2_mul(a.im, nwi)), f2_fma(a.im, wr, f2_mul(a.re, wi))};
+}
+
+// Shared-memory layout: one 16-byte slot per (point i, line pair p) holding
+// (re_c, re_c+1, im_c, im_c+1), at i*KP + p, plus one pad slot after every 8
+// points, so that 8-point groups read with the group index fastest land in
+// distinct bank groups.  Points 2^k apart (2^k >= 8) are (KP << k) + 2^(k-3)
+// slots apart.
+template <int KP>
+__device__ __forceinline__ int slot(int i, int p) { return i * KP + p + (i >> 3); }
+
 // One shared-memory pass of R = 2^r decimation-in-frequency stages with spans
-// 2^(k+r-1) down to 2^k, in registers, for point group (c, q, blk): the
-// points i0 + m 2^k, i0 = blk 2^(k+r) + q, q < 2^k.  Span S = 2^(k+j) maps
-// (u, w) at (p, p + S) to (u + w, (u - w) W_2S^(p mod S)) with
-// p mod S = q + (m mod 2^j) 2^k, so its twiddle is W_2S^q W_2^(j+1)^(m mod 2^j):
+// 2^(k+r-1) down to 2^k, in registers, for point group (p, q, blk): the
+// points i0 + m 2^k, i0 = blk 2^(k+r) + q, q < 2^k, of line pair p.  Span
+// S = 2^(k+j) maps (u, w) at (n, n + S) to (u + w, (u - w) W_2S^(n mod S)) with
+// n mod S = q + (m mod 2^j) 2^k, so its twiddle is W_2S^q W_2^(j+1)^(m mod 2^j):
 // the first factor is b^(2^(r-1-j)) for b = W_2^(k+r)^q (one sincospif, then
-// squarings), the second a constant.  Loads come from global memory (points at
-// or beyond nt read as zero) when kFromGlobal, else from shared memory.
-template <int KC, int r, bool kFromGlobal>
-__device__ __forceinline__ void dif_pass(float2 *a, int NF, int k, const float *x, long long line0, long long n_lines,
-                                         int nt) {
+// squarings), the second a constant.  With kFromGlobal the points come from
+// the A-lines in global memory (points at or beyond nt, and lines at or beyond
+// n_lines, read as zero): line pair p is real lines line0 + 4p .. line0 + 4p + 3
+// as (re_c, im_c, re_c+1, im_c+1).
+template <int KP, int r, bool kFromGlobal>
+__device__ __forceinline__ void dif_pass(ulonglong2 *a, int NF, int k, const float *x, long long line0,
+                                         long long n_lines, int nt) {
   constexpr int R = 1 << r;
   const int groups = NF >> r;
-  for (int id = threadIdx.x; id < groups * KC; id += blockDim.x) {
-    const int c = id % KC, t = id / KC;
+  const int ds = (KP << k) + (1 << (k - 3));
+  for (int id = threadIdx.x; id < groups * KP; id += blockDim.x) {
+    const int p = id % KP, t = id / KP;
     const int q = t & ((1 << k) - 1), blk = t >> k;
     const int i0 = (blk << (k + r)) | q;
-    float2 v[R];
+    const int s0 = slot<KP>(i0, p);
+    Cx2 v[R];
+    if (kFromGlobal) {
+      const long long lb = line0 + 4 * p;
+      const bool ok0 = lb < n_lines, ok1 = lb + 1 < n_lines, ok2 = lb + 2 < n_lines, ok3 = lb + 3 < n_lines;
+      const long long base = lb * nt + i0;
 #pragma unroll
-    for (int m = 0; m < R; ++m) {
-      const int n = i0 + (m << k);
-      if (kFromGlobal) {
-        const long long l0 = line0 + 2 * c, l1 = l0 + 1;
-        float re = 0.0f, im = 0.0f;
+      for (int m = 0; m < R; ++m) {
+        const int n = i0 + (m << k);
+        float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
         if (n < nt) {
-          if (l0 < n_lines) re = x[l0 * nt + n];
-          if (l1 < n_lines) im = x[l1 * nt + n];
+          const long long o = base + (m << k);
+          if (ok0) e0 = x[o];
+          if (ok1) e1 = x[o + nt];
+          if (ok2) e2 = x[o + 2 * (long long)nt];
+          if (ok3) e3 = x[o + 3 * (long long)nt];
         }
-        v[m] = make_float2(re, im);
-      } else {
-        v[m] = a[slot<KC>(n, c)];
+        v[m] = Cx2{f2_pack(e0, e2), f2_pack(e1, e3)};
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const ulonglong2 u = a[s0 + m * ds];
+        v[m] = Cx2{u.x, u.y};
       }
     }
     float2 pw[r];  // pw[j] = W_2^(k+j+1)^q
@@ -129,34 +186,39 @@ __device__ __forceinline__ void dif_pass(float2 *a, int NF, int k, const float *
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         if (m & S) continue;
-        const float2 u = v[m], w = v[m + S];
-        v[m] = cadd(u, w);
+        const Cx2 u = v[m], w = v[m + S];
+        v[m] = x_add(u, w);
         const int um = m & (S - 1);
         const float2 tw = um == 0 ? pw[j] : cmul(pw[j], w_small(2 * S, um));
-        v[m + S] = cmul(csub(u, w), tw);
+        v[m + S] = x_mul(x_sub(u, w), tw);
       }
     }
 #pragma unroll
-    for (int m = 0; m < R; ++m) a[slot<KC>(i0 + (m << k), c)] = v[m];
+    for (int m = 0; m < R; ++m) a[s0 + m * ds] = make_ulonglong2(v[m].re, v[m].im);
   }
 }
 
 // The matching decimation-in-time inverse pass (spans 2^k up to 2^(k+r-1)):
-// (u, w) at (p, p + S) go to (u + w conj(W), u - w conj(W)), W as above.
-// Results go to global memory (points below nt only) when kToGlobal, else
-// back to shared memory.
-template <int KC, int r, bool kToGlobal>
-__device__ __forceinline__ void dit_pass(float2 *a, int NF, int k, float *y, long long line0, long long n_lines,
+// (u, w) at (n, n + S) go to (u + w conj(W), u - w conj(W)), W as above.  With
+// kToGlobal the results go to the A-lines in global memory (points below nt
+// and lines below n_lines only), else back to shared memory.
+template <int KP, int r, bool kToGlobal>
+__device__ __forceinline__ void dit_pass(ulonglong2 *a, int NF, int k, float *y, long long line0, long long n_lines,
                                          int nt) {
   constexpr int R = 1 << r;
   const int groups = NF >> r;
-  for (int id = threadIdx.x; id < groups * KC; id += blockDim.x) {
-    const int c = id % KC, t = id / KC;
+  const int ds = (KP << k) + (1 << (k - 3));
+  for (int id = threadIdx.x; id < groups * KP; id += blockDim.x) {
+    const int p = id % KP, t = id / KP;
     const int q = t & ((1 << k) - 1), blk = t >> k;
     const int i0 = (blk << (k + r)) | q;
-    float2 v[R];
+    const int s0 = slot<KP>(i0, p);
+    Cx2 v[R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = a[slot<KC>(i0 + (m << k), c)];
+    for (int m = 0; m < R; ++m) {
+      const ulonglong2 u = a[s0 + m * ds];
+      v[m] = Cx2{u.x, u.y};
+    }
     float2 pw[r];
     sincospif(-2.0f * (float)q / (float)(1 << (k + r)), &pw[r - 1].y, &pw[r - 1].x);
 #pragma unroll
@@ -169,148 +231,167 @@ __device__ __forceinline__ void dit_pass(float2 *a, int NF, int k, float *y, lon
         if (m & S) continue;
         const int um = m & (S - 1);
         const float2 tw = um == 0 ? pw[j] : cmul(pw[j], w_small(2 * S, um));
-        const float2 u = v[m], w = cmul(v[m + S], cconj(tw));
-        v[m] = cadd(u, w);
-        v[m + S] = csub(u, w);
+        const Cx2 u = v[m], w = x_mul(v[m + S], make_float2(tw.x, -tw.y));
+        v[m] = x_add(u, w);
+        v[m + S] = x_sub(u, w);
       }
     }
     if (kToGlobal) {
-      const long long l0 = line0 + 2 * c, l1 = l0 + 1;
+      const long long lb = line0 + 4 * p;
+      const bool ok0 = lb < n_lines, ok1 = lb + 1 < n_lines, ok2 = lb + 2 < n_lines, ok3 = lb + 3 < n_lines;
+      const long long base = lb * nt + i0;
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int n = i0 + (m << k);
         if (n < nt) {
-          if (l0 < n_lines) y[l0 * nt + n] = v[m].x;
-          if (l1 < n_lines) y[l1 * nt + n] = v[m].y;
+          const long long o = base + (m << k);
+          const float2 re = f2_unpack(v[m].re), im = f2_unpack(v[m].im);
+          if (ok0) y[o] = re.x;
+          if (ok1) y[o + nt] = im.x;
+          if (ok2) y[o + 2 * (long long)nt] = re.y;
+          if (ok3) y[o + 3 * (long long)nt] = im.y;
         }
       }
     } else {
 #pragma unroll
-      for (int m = 0; m < R; ++m) a[slot<KC>(i0 + (m << k), c)] = v[m];
+      for (int m = 0; m < R; ++m) a[s0 + m * ds] = make_ulonglong2(v[m].re, v[m].im);
     }
   }
 }
 
-// The middle of the convolution for one 8-point group g of line c, in
+// The middle of the convolution for one 8-point group g of line pair p, in
 // registers: forward stages of spans 4, 2, 1 (the group then holds spectrum
 // entries in bit-reversed order), the product with the filter's spectrum in
-// the same order, inverse stages of spans 1, 2, 4.
-template <int KC>
-__device__ __forceinline__ void mid_group(float2 *a, int g, int c, const float4 *__restrict__ hb4) {
-  float2 v[8];
+// the same order, inverse stages of spans 1, 2, 4.  Products with +-i are
+// folded into the additions.
+template <int KP>
+__device__ __forceinline__ void mid_group(ulonglong2 *a, int g, int p, const float4 *__restrict__ hb4) {
+  const int base = slot<KP>(8 * g, p);
+  Cx2 v[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) v[j] = a[slot<KC>(8 * g + j, c)];
+  for (int j = 0; j < 8; ++j) {
+    const ulonglong2 u = a[base + j * KP];
+    v[j] = Cx2{u.x, u.y};
+  }
+  const uint64_t R2 = f2_splat(kRsqrt2), NR2 = f2_splat(-kRsqrt2);
   // forward span 4: W_8^j = (1, (1-i)/sqrt2, -i, (-1-i)/sqrt2)
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float2 u = v[j], w = v[j + 4];
-    v[j] = make_float2(u.x + w.x, u.y + w.y);
-    const float2 d = make_float2(u.x - w.x, u.y - w.y);
-    if (j == 0) v[4] = d;
-    if (j == 1) v[5] = make_float2(kRsqrt2 * (d.x + d.y), kRsqrt2 * (d.y - d.x));
-    if (j == 2) v[6] = make_float2(d.y, -d.x);
-    if (j == 3) v[7] = make_float2(kRsqrt2 * (d.y - d.x), -kRsqrt2 * (d.x + d.y));
+  {
+    const Cx2 u0 = v[0], w0 = v[4], u1 = v[1], w1 = v[5], u2 = v[2], w2 = v[6], u3 = v[3], w3 = v[7];
+    v[0] = x_add(u0, w0);
+    v[4] = x_sub(u0, w0);
+    v[1] = x_add(u1, w1);
+    const Cx2 d1 = x_sub(u1, w1);
+    v[5] = Cx2{f2_mul(R2, f2_add(d1.re, d1.im)), f2_mul(R2, f2_sub(d1.im, d1.re))};
+    v[2] = x_add(u2, w2);
+    v[6] = Cx2{f2_sub(u2.im, w2.im), f2_sub(w2.re, u2.re)};
+    v[3] = x_add(u3, w3);
+    const Cx2 d3 = x_sub(u3, w3);
+    v[7] = Cx2{f2_mul(R2, f2_sub(d3.im, d3.re)), f2_mul(NR2, f2_add(d3.re, d3.im))};
   }
   // forward span 2: W_4^j = (1, -i)
 #pragma unroll
   for (int b = 0; b < 8; b += 4) {
-    const float2 u0 = v[b], w0 = v[b + 2], u1 = v[b + 1], w1 = v[b + 3];
-    v[b] = make_float2(u0.x + w0.x, u0.y + w0.y);
-    v[b + 2] = make_float2(u0.x - w0.x, u0.y - w0.y);
-    v[b + 1] = make_float2(u1.x + w1.x, u1.y + w1.y);
-    v[b + 3] = make_float2(u1.y - w1.y, w1.x - u1.x);
+    const Cx2 u0 = v[b], w0 = v[b + 2], u1 = v[b + 1], w1 = v[b + 3];
+    v[b] = x_add(u0, w0);
+    v[b + 2] = x_sub(u0, w0);
+    v[b + 1] = x_add(u1, w1);
+    v[b + 3] = Cx2{f2_sub(u1.im, w1.im), f2_sub(w1.re, u1.re)};
   }
   // forward span 1, product, inverse span 1
   const float4 h0 = hb4[2 * g], h1 = hb4[2 * g + 1];
   const float hs[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
 #pragma unroll
   for (int b = 0; b < 8; b += 2) {
-    const float2 u = v[b], w = v[b + 1];
-    const float2 p = make_float2((u.x + w.x) * hs[b], (u.y + w.y) * hs[b]);
-    const float2 m = make_float2((u.x - w.x) * hs[b + 1], (u.y - w.y) * hs[b + 1]);
-    v[b] = make_float2(p.x + m.x, p.y + m.y);
-    v[b + 1] = make_float2(p.x - m.x, p.y - m.y);
+    const uint64_t ha = f2_splat(hs[b]), hc = f2_splat(hs[b + 1]);
+    const Cx2 u = v[b], w = v[b + 1];
+    const Cx2 P = Cx2{f2_mul(f2_add(u.re, w.re), ha), f2_mul(f2_add(u.im, w.im), ha)};
+    const Cx2 M = Cx2{f2_mul(f2_sub(u.re, w.re), hc), f2_mul(f2_sub(u.im, w.im), hc)};
+    v[b] = x_add(P, M);
+    v[b + 1] = x_sub(P, M);
   }
-  // inverse span 2: conj W_4^j = (1, i)
+  // inverse span 2: conj W_4^j = (1, i); w i = (-w.im, w.re)
 #pragma unroll
   for (int b = 0; b < 8; b += 4) {
-    const float2 u0 = v[b], w0 = v[b + 2], u1 = v[b + 1];
-    const float2 w1 = make_float2(-v[b + 3].y, v[b + 3].x);
-    v[b] = make_float2(u0.x + w0.x, u0.y + w0.y);
-    v[b + 2] = make_float2(u0.x - w0.x, u0.y - w0.y);
-    v[b + 1] = make_float2(u1.x + w1.x, u1.y + w1.y);
-    v[b + 3] = make_float2(u1.x - w1.x, u1.y - w1.y);
+    const Cx2 u0 = v[b], w0 = v[b + 2], u1 = v[b + 1], w1 = v[b + 3];
+    v[b] = x_add(u0, w0);
+    v[b + 2] = x_sub(u0, w0);
+    v[b + 1] = Cx2{f2_sub(u1.re, w1.im), f2_add(u1.im, w1.re)};
+    v[b + 3] = Cx2{f2_add(u1.re, w1.im), f2_sub(u1.im, w1.re)};
   }
   // inverse span 4: conj W_8^j = (1, (1+i)/sqrt2, i, (-1+i)/sqrt2)
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float2 u = v[j], x = v[j + 4];
-    float2 w = x;
-    if (j == 1) w = make_float2(kRsqrt2 * (x.x - x.y), kRsqrt2 * (x.x + x.y));
-    if (j == 2) w = make_float2(-x.y, x.x);
-    if (j == 3) w = make_float2(-kRsqrt2 * (x.x + x.y), kRsqrt2 * (x.x - x.y));
-    v[j] = make_float2(u.x + w.x, u.y + w.y);
-    v[j + 4] = make_float2(u.x - w.x, u.y - w.y);
+  {
+    const Cx2 u0 = v[0], x0 = v[4], u1 = v[1], x1 = v[5], u2 = v[2], x2 = v[6], u3 = v[3], x3 = v[7];
+    v[0] = x_add(u0, x0);
+    v[4] = x_sub(u0, x0);
+    const uint64_t d1 = f2_sub(x1.re, x1.im), s1 = f2_add(x1.re, x1.im);  // x1 conj W_8 = r (d1, s1)
+    v[1] = Cx2{f2_fma(R2, d1, u1.re), f2_fma(R2, s1, u1.im)};
+    v[5] = Cx2{f2_fma(NR2, d1, u1.re), f2_fma(NR2, s1, u1.im)};
+    v[2] = Cx2{f2_sub(u2.re, x2.im), f2_add(u2.im, x2.re)};
+    v[6] = Cx2{f2_add(u2.re, x2.im), f2_sub(u2.im, x2.re)};
+    const uint64_t s3 = f2_add(x3.re, x3.im), d3 = f2_sub(x3.re, x3.im);  // x3 conj W_8^3 = r (-s3, d3)
+    v[3] = Cx2{f2_fma(NR2, s3, u3.re), f2_fma(R2, d3, u3.im)};
+    v[7] = Cx2{f2_fma(R2, s3, u3.re), f2_fma(NR2, d3, u3.im)};
   }
 #pragma unroll
-  for (int j = 0; j < 8; ++j) a[slot<KC>(8 * g + j, c)] = v[j];
+  for (int j = 0; j < 8; ++j) a[base + j * KP] = make_ulonglong2(v[j].re, v[j].im);
 }
 
 // First forward pass (from global memory) and last inverse pass (to global
 // memory) with r0 = ((log2 NF - 3) mod 4, or 4) stages at k = log2 NF - r0.
-template <int KC, bool kForward>
-__device__ __forceinline__ void edge_pass(int r0, float2 *a, int NF, int k, const float *x, float *y, long long line0,
-                                          long long n_lines, int nt) {
+template <int KP, bool kForward>
+__device__ __forceinline__ void edge_pass(int r0, ulonglong2 *a, int NF, int k, const float *x, float *y,
+                                          long long line0, long long n_lines, int nt) {
   switch (r0) {
     case 1:
-      if (kForward) dif_pass<KC, 1, true>(a, NF, k, x, line0, n_lines, nt);
-      else dit_pass<KC, 1, true>(a, NF, k, y, line0, n_lines, nt);
+      if (kForward) dif_pass<KP, 1, true>(a, NF, k, x, line0, n_lines, nt);
+      else dit_pass<KP, 1, true>(a, NF, k, y, line0, n_lines, nt);
       break;
     case 2:
-      if (kForward) dif_pass<KC, 2, true>(a, NF, k, x, line0, n_lines, nt);
-      else dit_pass<KC, 2, true>(a, NF, k, y, line0, n_lines, nt);
+      if (kForward) dif_pass<KP, 2, true>(a, NF, k, x, line0, n_lines, nt);
+      else dit_pass<KP, 2, true>(a, NF, k, y, line0, n_lines, nt);
       break;
     case 3:
-      if (kForward) dif_pass<KC, 3, true>(a, NF, k, x, line0, n_lines, nt);
-      else dit_pass<KC, 3, true>(a, NF, k, y, line0, n_lines, nt);
+      if (kForward) dif_pass<KP, 3, true>(a, NF, k, x, line0, n_lines, nt);
+      else dit_pass<KP, 3, true>(a, NF, k, y, line0, n_lines, nt);
       break;
     default:
-      if (kForward) dif_pass<KC, 4, true>(a, NF, k, x, line0, n_lines, nt);
-      else dit_pass<KC, 4, true>(a, NF, k, y, line0, n_lines, nt);
+      if (kForward) dif_pass<KP, 4, true>(a, NF, k, x, line0, n_lines, nt);
+      else dit_pass<KP, 4, true>(a, NF, k, y, line0, n_lines, nt);
       break;
   }
 }
 
 // y = F x for n_lines A-lines of nt samples (x and y may alias: a block reads
 // all of its lines before it writes any).  Block b holds real lines
-// 2 KC b .. 2 KC b + 2 KC - 1; complex line c carries real lines 2c (real
-// part) and 2c + 1 (imaginary part).  NF >= 16.  hb: the filter's spectrum
-// over NF, in bit-reversed order (NF floats, 16-byte aligned).  Forward
-// stages: spans NF/2 .. 2^k0 straight from global memory, then passes of four
-// down to span 8, then the register middle (spans 4, 2, 1, the product and
-// back); the inverse mirrors them and its last pass writes to global memory.
-template <int KC>
-__global__ void __launch_bounds__(kFirThreads) k_fir_lines(const float *x, float *y, long long n_lines, int nt,
-                                                           int NF, int lgNF, const float *__restrict__ hb) {
-  extern __shared__ float2 a[];
-  const long long line0 = (long long)blockIdx.x * (2 * KC);
+// 4 KP b .. 4 KP b + 4 KP - 1 as 2 KP complex lines (real and imaginary part
+// from consecutive real lines), processed in line pairs.  NF >= 16.  hb: the
+// filter's spectrum over NF, in bit-reversed order (NF floats, 16-byte
+// aligned).  Forward stages: spans NF/2 .. 2^k0 straight from global memory,
+// then passes of four down to span 8, then the register middle (spans 4, 2, 1,
+// the product and back); the inverse mirrors them and its last pass writes to
+// global memory.
+template <int KP>
+__global__ void __launch_bounds__(kFirThreads, 2) k_fir_lines(const float *x, float *y, long long n_lines, int nt,
+                                                              int NF, int lgNF, const float *__restrict__ hb) {
+  extern __shared__ ulonglong2 a[];
+  const long long line0 = (long long)blockIdx.x * (4 * KP);
   const int r0 = ((lgNF - 3) & 3) ? ((lgNF - 3) & 3) : 4;
   const int k0 = lgNF - r0;
-  edge_pass<KC, true>(r0, a, NF, k0, x, nullptr, line0, n_lines, nt);
+  edge_pass<KP, true>(r0, a, NF, k0, x, nullptr, line0, n_lines, nt);
   __syncthreads();
   for (int k = k0 - 4; k >= 3; k -= 4) {
-    dif_pass<KC, 4, false>(a, NF, k, nullptr, 0, 0, 0);
+    dif_pass<KP, 4, false>(a, NF, k, nullptr, 0, 0, 0);
     __syncthreads();
   }
   const int groups = NF >> 3;
-  for (int id = threadIdx.x; id < groups * KC; id += blockDim.x)
-    mid_group<KC>(a, id % groups, id / groups, reinterpret_cast<const float4 *>(hb));
+  for (int id = threadIdx.x; id < groups * KP; id += blockDim.x)
+    mid_group<KP>(a, id % groups, id / groups, reinterpret_cast<const float4 *>(hb));
   __syncthreads();
   for (int k = 3; k + 4 <= k0; k += 4) {
-    dit_pass<KC, 4, false>(a, NF, k, nullptr, 0, 0, 0);
+    dit_pass<KP, 4, false>(a, NF, k, nullptr, 0, 0, 0);
     __syncthreads();
   }
-  edge_pass<KC, false>(r0, a, NF, k0, nullptr, y, line0, n_lines, nt);
+  edge_pass<KP, false>(r0, a, NF, k0, nullptr, y, line0, n_lines, nt);
 }
 
 oam_status set_smem(const void *fn, size_t bytes) {
@@ -319,20 +400,20 @@ oam_status set_smem(const void *fn, size_t bytes) {
   return OAM_OK;
 }
 
-template <int KC>
+template <int KP>
 oam_status launch_fir(const FirLayout *F, const float *x, float *y, long long n_lines, int nt, cudaStream_t st) {
-  const size_t smem = fir_smem(F->NF, KC);
-  oam_status rc = set_smem((const void *)k_fir_lines<KC>, smem);
+  const size_t smem = fir_smem(F->NF, KP);
+  oam_status rc = set_smem((const void *)k_fir_lines<KP>, smem);
   if (rc) return rc;
-  const long long blocks = (n_lines + 2 * KC - 1) / (2 * KC);
+  const long long blocks = (n_lines + 4 * KP - 1) / (4 * KP);
   if (blocks <= 0) return OAM_OK;
-  k_fir_lines<KC><<<(unsigned)blocks, kFirThreads, smem, st>>>(x, y, n_lines, nt, F->NF, F->lgNF, F->d_hb);
+  k_fir_lines<KP><<<(unsigned)blocks, kFirThreads, smem, st>>>(x, y, n_lines, nt, F->NF, F->lgNF, F->d_hb);
   OAM_LAUNCHED();
   return OAM_OK;
 }
 
-// Complex lines per block: about 64 KB of lines in shared memory.
-int fir_lines_per_block(int NF) { return std::max(1, std::min(16, 8192 / NF)); }
+// Line pairs per block: about 64 KB of points in shared memory.
+int fir_pairs_per_block(int NF) { return std::max(1, std::min(8, 4096 / NF)); }
 
 double sinc(double x) { return x == 0.0 ? 1.0 : std::sin(M_PI * x) / (M_PI * x); }
 
@@ -352,8 +433,7 @@ oam_status oam::fir_apply(const oam_model *m, const float *x, float *y, cudaStre
   const FirLayout *F = m->fir;
   if (!F) return OAM_ERR_INVALID_ARG;
   const long long lines = (long long)m->grid.py * m->grid.px;
-  switch (F->KC) {
-    case 16: return launch_fir<16>(F, x, y, lines, m->grid.nt, st);
+  switch (F->KP) {
     case 8: return launch_fir<8>(F, x, y, lines, m->grid.nt, st);
     case 4: return launch_fir<4>(F, x, y, lines, m->grid.nt, st);
     case 2: return launch_fir<2>(F, x, y, lines, m->grid.nt, st);
@@ -418,7 +498,7 @@ oam_status oam_model_set_filter(oam_model *m, const double *taps, int32_t half_l
   F->L = half_len;
   F->NF = NF;
   F->lgNF = lg;
-  F->KC = fir_lines_per_block(NF);
+  F->KP = fir_pairs_per_block(NF);
   const size_t hbytes = sizeof(float) * hh.size(), sbytes = sizeof(float) * sig_elems(m);
   if (cudaMallocAsync((void **)&F->d_hb, hbytes, st) != cudaSuccess ||
       cudaMallocAsync((void **)&F->d_stage, sbytes, st) != cudaSuccess) {
