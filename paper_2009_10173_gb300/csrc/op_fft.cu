@@ -173,6 +173,258 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_c2r(const float2 *__re
   }
 }
 
+// ---- transforms in register passes (P >= 16) ------------------------------
+// The kernels above move every point through shared memory once per two
+// radix-2 stages and scatter it to its bit-reversed slot first.  The kernels
+// below run up to four stages per pass in registers: a forward transform is
+// decimation in frequency (natural order in, bit-reversed out: the point at
+// position i ends as frequency bitrev(i), which goes to global row bitrev(i)),
+// an inverse transform decimation in time (position i loads frequency
+// bitrev(i), natural order out), so no permutation pass is needed, the first
+// pass reads global memory and the last writes it.  Passes cover stages
+// k .. k + r - 1 (spans 2^k .. 2^(k+r-1)) with k a multiple of 4: the first
+// forward pass has r0 = log2 P - 4 (ceil(log2 P / 4) - 1) stages, every other
+// pass four.
+
+// Shared-memory slot of point i of line l among KL lines: lines fastest, and
+// for KL < 16 a pad of KL slots after every 16 points, so that the 16 lines x
+// points a half-warp touches in a pass fall in distinct banks.
+template <int KL>
+__device__ __forceinline__ int xslot(int i, int l) {
+  return i * KL + l + (KL < 16 ? (i >> 4) * KL : 0);
+}
+template <int KL>
+__host__ __device__ constexpr size_t xslots(int P) {
+  return (size_t)P * KL + (KL < 16 ? (size_t)(P >> 4) * KL : 0);
+}
+
+constexpr float kXRsqrt2 = 0.70710678118654752f;  // cos(pi/4) = sin(pi/4)
+constexpr float kXCos8 = 0.92387953251128676f;    // cos(pi/8)
+constexpr float kXSin8 = 0.38268343236508977f;    // sin(pi/8)
+
+// W_N^u = exp(-2 pi i u / N) for N <= 16 (u < N/2).
+__device__ __forceinline__ float2 xw_small(int N, int u) {
+  switch (u * (16 / N)) {
+    case 0: return make_float2(1.0f, 0.0f);
+    case 1: return make_float2(kXCos8, -kXSin8);
+    case 2: return make_float2(kXRsqrt2, -kXRsqrt2);
+    case 3: return make_float2(kXSin8, -kXCos8);
+    case 4: return make_float2(0.0f, -1.0f);
+    case 5: return make_float2(-kXSin8, -kXCos8);
+    case 6: return make_float2(-kXRsqrt2, -kXRsqrt2);
+    default: return make_float2(-kXCos8, -kXSin8);
+  }
+}
+
+// One pass of r stages over the points i0 + m 2^k (m < 2^r) of each group
+// (line l, q < 2^k, block blk; i0 = blk 2^(k+r) + q).  Forward (decimation in
+// frequency, spans from large to small): span S = 2^(k+j) maps (u, w) at
+// (n, n + S) to (u + w, (u - w) W_2S^(n mod S)), n mod S = q + (m mod 2^j) 2^k,
+// twiddle W_2S^q W_2^(j+1)^(m mod 2^j), the first factor a power of
+// b = W_2^(k+r)^q (one sincospif, then squarings).  Inverse (decimation in
+// time, spans from small to large, sign +1): (u, w) go to (u + w conj(W),
+// u - w conj(W)).  src(i, l) yields point i before the pass, dst(i, l, v)
+// takes it after.
+template <int KL, int r, bool kForward, class Src, class Dst>
+__device__ __forceinline__ void xpass(int P, int k, Src src, Dst dst) {
+  constexpr int R = 1 << r;
+  const int groups = P >> r;
+  for (int id = threadIdx.x; id < groups * KL; id += blockDim.x) {
+    const int l = id % KL, t = id / KL;
+    const int q = t & ((1 << k) - 1), blk = t >> k;
+    const int i0 = (blk << (k + r)) | q;
+    float2 v[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = src(i0 + (m << k), l);
+    float2 pw[r];
+    sincospif(-2.0f * (float)q / (float)(1 << (k + r)), &pw[r - 1].y, &pw[r - 1].x);
+#pragma unroll
+    for (int j = r - 2; j >= 0; --j) pw[j] = cmul(pw[j + 1], pw[j + 1]);
+    if (kForward) {
+#pragma unroll
+      for (int j = r - 1; j >= 0; --j) {
+        const int S = 1 << j;
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          if (m & S) continue;
+          const float2 u = v[m], w = v[m + S];
+          v[m] = make_float2(u.x + w.x, u.y + w.y);
+          const int um = m & (S - 1);
+          const float2 tw = um == 0 ? pw[j] : cmul(pw[j], xw_small(2 * S, um));
+          v[m + S] = cmul(make_float2(u.x - w.x, u.y - w.y), tw);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < r; ++j) {
+        const int S = 1 << j;
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          if (m & S) continue;
+          const int um = m & (S - 1);
+          const float2 tw = um == 0 ? pw[j] : cmul(pw[j], xw_small(2 * S, um));
+          const float2 u = v[m], w = cmul(v[m + S], make_float2(tw.x, -tw.y));
+          v[m] = make_float2(u.x + w.x, u.y + w.y);
+          v[m + S] = make_float2(u.x - w.x, u.y - w.y);
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) dst(i0 + (m << k), l, v[m]);
+  }
+}
+
+// A whole transform of KL lines of P = 2^lgP points (lgP >= 4) through the
+// shared slots `a`: `first` reads the input (forward: natural point i;
+// inverse: the point at position i, i.e. frequency bitrev(i)), `last` takes
+// position i's result (forward: frequency bitrev(i); inverse: point i).  With
+// kLastToSmem the last pass writes the slots too (followed by a barrier) and
+// `last` is not called.
+template <int KL, bool kForward, bool kLastToSmem, class First, class Last>
+__device__ __forceinline__ void xtransform(float2 *a, int P, int lgP, First first, Last last) {
+  const int np = (lgP + 3) / 4, r0 = lgP - 4 * (np - 1);
+  auto from_smem = [&](int i, int l) { return a[xslot<KL>(i, l)]; };
+  auto to_smem = [&](int i, int l, float2 v) { a[xslot<KL>(i, l)] = v; };
+  // pass p covers stages [kf, kf + rr): forward passes run p = 0 .. np-1 with
+  // kf = 4 (np-1-p) (the first has r0 stages), inverse passes the reverse
+  for (int pi = 0; pi < np; ++pi) {
+    const int pp = kForward ? pi : np - 1 - pi;  // which stage block
+    const int kf = 4 * (np - 1 - pp), rr = pp == 0 ? r0 : 4;
+    const bool is_first = pi == 0, is_last = pi == np - 1;
+    if (is_first && is_last) {
+      if (kLastToSmem) {
+        switch (rr) {
+          case 1: xpass<KL, 1, kForward>(P, kf, first, to_smem); break;
+          case 2: xpass<KL, 2, kForward>(P, kf, first, to_smem); break;
+          case 3: xpass<KL, 3, kForward>(P, kf, first, to_smem); break;
+          default: xpass<KL, 4, kForward>(P, kf, first, to_smem); break;
+        }
+      } else {
+        switch (rr) {
+          case 1: xpass<KL, 1, kForward>(P, kf, first, last); break;
+          case 2: xpass<KL, 2, kForward>(P, kf, first, last); break;
+          case 3: xpass<KL, 3, kForward>(P, kf, first, last); break;
+          default: xpass<KL, 4, kForward>(P, kf, first, last); break;
+        }
+      }
+    } else if (is_first) {
+      switch (rr) {
+        case 1: xpass<KL, 1, kForward>(P, kf, first, to_smem); break;
+        case 2: xpass<KL, 2, kForward>(P, kf, first, to_smem); break;
+        case 3: xpass<KL, 3, kForward>(P, kf, first, to_smem); break;
+        default: xpass<KL, 4, kForward>(P, kf, first, to_smem); break;
+      }
+    } else if (is_last && !kLastToSmem) {
+      switch (rr) {
+        case 1: xpass<KL, 1, kForward>(P, kf, from_smem, last); break;
+        case 2: xpass<KL, 2, kForward>(P, kf, from_smem, last); break;
+        case 3: xpass<KL, 3, kForward>(P, kf, from_smem, last); break;
+        default: xpass<KL, 4, kForward>(P, kf, from_smem, last); break;
+      }
+    } else {
+      switch (rr) {
+        case 1: xpass<KL, 1, kForward>(P, kf, from_smem, to_smem); break;
+        case 2: xpass<KL, 2, kForward>(P, kf, from_smem, to_smem); break;
+        case 3: xpass<KL, 3, kForward>(P, kf, from_smem, to_smem); break;
+        default: xpass<KL, 4, kForward>(P, kf, from_smem, to_smem); break;
+      }
+    }
+    if (!is_last || kLastToSmem) __syncthreads();
+  }
+}
+
+// k_fft_rows_r2c in register passes (P >= 16): same arguments and results.
+template <int KC>
+__global__ void __launch_bounds__(kFftThreads) k_xfft_rows_r2c(const float *__restrict__ X, int py, int px, int Ctot,
+                                                               int c0, int C, int P, int lgP, int Q,
+                                                               float2 *__restrict__ Y) {
+  constexpr int KH = KC / 2;
+  extern __shared__ float2 sm[];
+  float2 *a = sm;
+  const int y = blockIdx.x, cb = blockIdx.y * KC;
+  const float *row = X + (size_t)y * px * Ctot + c0 + cb;
+  auto load = [&](int x, int l) {
+    float re = 0.0f, im = 0.0f;
+    if (x < px) {
+      const float *p = row + (size_t)x * Ctot;
+      if (cb + l < C) re = p[l];
+      if (cb + l + KH < C) im = p[l + KH];
+    }
+    return make_float2(re, im);
+  };
+  auto none = [](int, int, float2) {};
+  xtransform<KH, true, true>(a, P, lgP, load, none);
+  for (int i = threadIdx.x; i < Q * KC; i += blockDim.x) {
+    const int u = i / KC, c = i % KC, l = c % KH;
+    if (cb + c >= C) continue;
+    const float2 z = a[xslot<KH>(bitrev(u, lgP), l)], w = a[xslot<KH>(bitrev((P - u) & (P - 1), lgP), l)];
+    Y[((size_t)u * py + y) * C + cb + c] = c < KH ? make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y))
+                                                  : make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
+  }
+}
+
+// k_fft_cols in register passes (P >= 16): same arguments and results.
+template <int KC, bool kInverse>
+__global__ void __launch_bounds__(kFftThreads) k_xfft_cols(const float2 *__restrict__ Z, int nin, int nout, int C,
+                                                           int P, int lgP, float2 *__restrict__ W) {
+  extern __shared__ float2 sm[];
+  const int u = blockIdx.x, cb = blockIdx.y * KC;
+  const float2 *zin = Z + (size_t)u * nin * C + cb;
+  float2 *wout = W + (size_t)u * nout * C + cb;
+  auto load = [&](int i, int l) {
+    const int row = kInverse ? bitrev(i, lgP) : i;
+    return (row < nin && cb + l < C) ? zin[(size_t)row * C + l] : make_float2(0.0f, 0.0f);
+  };
+  auto store = [&](int i, int l, float2 v) {
+    const int row = kInverse ? i : bitrev(i, lgP);
+    if (row < nout && cb + l < C) wout[(size_t)row * C + l] = v;
+  };
+  xtransform<KC, !kInverse, false>(sm, P, lgP, load, store);
+}
+
+// k_fft_rows_c2r in register passes (P >= 16): same arguments and results.
+template <int KC>
+__global__ void __launch_bounds__(kFftThreads) k_xfft_rows_c2r(const float2 *__restrict__ Z, int py, int px, int Ctot,
+                                                               int c0, int C, int P, int lgP, int Q, float scale,
+                                                               float *__restrict__ X) {
+  constexpr int KH = KC / 2;
+  extern __shared__ float2 sm[];
+  const int y = blockIdx.x, ob = blockIdx.y * KC;
+  if (ob >= c0 + C || ob + KC <= c0) {  // block entirely outside the band: zeros
+    for (int i = threadIdx.x; i < px * KC; i += blockDim.x) {
+      const int x = i / KC, c = i % KC;
+      if (ob + c < Ctot) X[((size_t)y * px + x) * Ctot + ob + c] = 0.0f;
+    }
+    return;
+  }
+  // position i takes frequency f = bitrev(i) of W = X + i Y, the two real
+  // channels' Hermitian-extended spectra (imaginary parts of f = 0, P/2 dropped)
+  auto load = [&](int i, int l) {
+    const int f = bitrev(i, lgP);
+    const int fh = f < Q ? f : P - f;
+    float2 xs = make_float2(0.0f, 0.0f), ys = make_float2(0.0f, 0.0f);
+    const int zx = ob + l - c0, zy = ob + l + KH - c0;
+    if (zx >= 0 && zx < C) xs = Z[((size_t)fh * py + y) * C + zx];
+    if (zy >= 0 && zy < C) ys = Z[((size_t)fh * py + y) * C + zy];
+    if (f == 0 || f == (P >> 1)) {
+      xs.y = 0.0f;
+      ys.y = 0.0f;
+    } else if (f >= Q) {
+      xs.y = -xs.y;
+      ys.y = -ys.y;
+    }
+    return make_float2(xs.x - ys.y, xs.y + ys.x);
+  };
+  auto store = [&](int x, int l, float2 v) {
+    if (x >= px) return;
+    float *p = X + ((size_t)y * px + x) * Ctot;
+    const int o0 = ob + l, o1 = ob + l + KH;
+    if (o0 < Ctot) p[o0] = (o0 - c0 >= 0 && o0 - c0 < C) ? v.x * scale : 0.0f;
+    if (o1 < Ctot) p[o1] = (o1 - c0 >= 0 && o1 - c0 < C) ? v.y * scale : 0.0f;
+  };
+  xtransform<KH, false, false>(sm, P, lgP, load, store);
+}
+
 // Forward, per frequency orbit r: s^_f[j] = sum_k S^_r[k][n - klo_k] H^_f[k]
 // for the orbit's member frequencies f, n = n_lo + j; thread j visits the
 // depths [kr_j.x, kr_j.y) whose band holds n.  Block per orbit.
@@ -609,20 +861,77 @@ oam_status set_smem(const void *fn, size_t bytes) {
 
 namespace {
 
+// Threads for a register-pass transform block: one per group of the
+// four-stage passes (KL lines x P/16 groups), 64 to 256.
+int xthreads(int P, int KL) { return std::max(64, std::min(kFftThreads, (((P >> 4) * KL + 31) / 32) * 32)); }
+
+// The transforms of one application in register passes (P >= 16); the
+// spectral products are launched by run_fft between them.
 template <int KC>
+struct XKernels {
+  static oam_status prepare(int P) {
+    oam_status rc;
+    const size_t sr = sizeof(float2) * xslots<KC / 2>(P), sc = sizeof(float2) * xslots<KC>(P);
+    if ((rc = set_smem((const void *)k_xfft_rows_r2c<KC>, sr)) || (rc = set_smem((const void *)k_xfft_rows_c2r<KC>, sr)) ||
+        (rc = set_smem((const void *)k_xfft_cols<KC, false>, sc)) || (rc = set_smem((const void *)k_xfft_cols<KC, true>, sc)))
+      return rc;
+    return OAM_OK;
+  }
+  static void rows_r2c(dim3 g, cudaStream_t st, const float *X, int py, int px, int Ctot, int c0, int C, int P, int lgP,
+                       int Q, float2 *Y) {
+    k_xfft_rows_r2c<KC><<<g, xthreads(P, KC / 2), sizeof(float2) * xslots<KC / 2>(P), st>>>(X, py, px, Ctot, c0, C, P,
+                                                                                           lgP, Q, Y);
+  }
+  static void cols(dim3 g, cudaStream_t st, const float2 *Z, int nin, int nout, int C, int P, int lgP, int inverse,
+                   float2 *W) {
+    if (inverse)
+      k_xfft_cols<KC, true><<<g, xthreads(P, KC), sizeof(float2) * xslots<KC>(P), st>>>(Z, nin, nout, C, P, lgP, W);
+    else
+      k_xfft_cols<KC, false><<<g, xthreads(P, KC), sizeof(float2) * xslots<KC>(P), st>>>(Z, nin, nout, C, P, lgP, W);
+  }
+  static void rows_c2r(dim3 g, cudaStream_t st, const float2 *Z, int py, int px, int Ctot, int c0, int C, int P,
+                       int lgP, int Q, float scale, float *X) {
+    k_xfft_rows_c2r<KC><<<g, xthreads(P, KC / 2), sizeof(float2) * xslots<KC / 2>(P), st>>>(Z, py, px, Ctot, c0, C,
+                                                                                           P, lgP, Q, scale, X);
+  }
+};
+
+// The same in the radix-2 kernels (any P).
+template <int KC>
+struct RKernels {
+  static oam_status prepare(int P) {
+    oam_status rc;
+    const size_t sm = fft_smem(P, KC), smr = fft_smem(P, KC / 2);  // row kernels: two channels per line
+    if ((rc = set_smem((const void *)k_fft_rows_r2c<KC>, smr)) || (rc = set_smem((const void *)k_fft_cols<KC>, sm)) ||
+        (rc = set_smem((const void *)k_fft_rows_c2r<KC>, smr)))
+      return rc;
+    return OAM_OK;
+  }
+  static void rows_r2c(dim3 g, cudaStream_t st, const float *X, int py, int px, int Ctot, int c0, int C, int P, int lgP,
+                       int Q, float2 *Y) {
+    k_fft_rows_r2c<KC><<<g, kFftThreads, fft_smem(P, KC / 2), st>>>(X, py, px, Ctot, c0, C, P, lgP, Q, Y);
+  }
+  static void cols(dim3 g, cudaStream_t st, const float2 *Z, int nin, int nout, int C, int P, int lgP, int inverse,
+                   float2 *W) {
+    k_fft_cols<KC><<<g, kFftThreads, fft_smem(P, KC), st>>>(Z, nin, nout, C, P, lgP, inverse, W);
+  }
+  static void rows_c2r(dim3 g, cudaStream_t st, const float2 *Z, int py, int px, int Ctot, int c0, int C, int P,
+                       int lgP, int Q, float scale, float *X) {
+    k_fft_rows_c2r<KC><<<g, kFftThreads, fft_smem(P, KC / 2), st>>>(Z, py, px, Ctot, c0, C, P, lgP, Q, scale, X);
+  }
+};
+
+template <int KC, class K>
 oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float *in, float *out, cudaStream_t st) {
   const int P = L->P, Q = L->Q, lgP = L->lgP, nz = m->grid.nz, py = m->grid.py, px = m->grid.px, NS = L->NS;
-  const size_t sm = fft_smem(P, KC), smr = fft_smem(P, KC / 2);  // row kernels: two channels per line
-  oam_status rc;
-  if ((rc = set_smem((const void *)k_fft_rows_r2c<KC>, smr)) || (rc = set_smem((const void *)k_fft_cols<KC>, sm)) ||
-      (rc = set_smem((const void *)k_fft_rows_c2r<KC>, smr)))
-    return rc;
+  oam_status rc = K::prepare(P);
+  if (rc) return rc;
   const unsigned cbz = (unsigned)((nz + KC - 1) / KC), cbs = (unsigned)((NS + KC - 1) / KC);
   const float scale = 1.0f / ((float)P * (float)P);
   if (fwd) {
-    k_fft_rows_r2c<KC><<<dim3(py, cbz), kFftThreads, smr, st>>>(in, py, px, nz, 0, nz, P, lgP, Q, L->d_w2);
+    K::rows_r2c(dim3(py, cbz), st, in, py, px, nz, 0, nz, P, lgP, Q, L->d_w2);
     OAM_LAUNCHED();
-    k_fft_cols<KC><<<dim3(Q, cbz), kFftThreads, sm, st>>>(L->d_w2, py, P, nz, P, lgP, 0, L->d_w1);
+    K::cols(dim3(Q, cbz), st, L->d_w2, py, P, nz, P, lgP, 0, L->d_w1);
     OAM_LAUNCHED();
     const size_t sa = sizeof(float4) * 2 * nz + sizeof(int) * (2 * nz + 2) + sizeof(long long) * nz;
     if ((rc = set_smem((const void *)k_fft_apply_fwd, sa))) return rc;
@@ -632,17 +941,15 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     k_fft_apply_fwd<<<fblocks, fwd_threads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
                                                       L->d_koff, L->d_krange, nz, m->n_lo, NS, L->d_w1, L->d_w2);
     OAM_LAUNCHED();
-    k_fft_cols<KC><<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, P, py, NS, P, lgP, 1, L->d_w1);
+    K::cols(dim3(Q, cbs), st, L->d_w2, P, py, NS, P, lgP, 1, L->d_w1);
     OAM_LAUNCHED();
     const unsigned cbt = (unsigned)((m->grid.nt + KC - 1) / KC);
-    k_fft_rows_c2r<KC><<<dim3(py, cbt), kFftThreads, smr, st>>>(L->d_w1, py, px, m->grid.nt, m->n_lo, NS, P, lgP, Q,
-                                                               scale, out);
+    K::rows_c2r(dim3(py, cbt), st, L->d_w1, py, px, m->grid.nt, m->n_lo, NS, P, lgP, Q, scale, out);
     OAM_LAUNCHED();
   } else {
-    k_fft_rows_r2c<KC><<<dim3(py, cbs), kFftThreads, smr, st>>>(in, py, px, m->grid.nt, m->n_lo, NS, P, lgP, Q,
-                                                               L->d_w2);
+    K::rows_r2c(dim3(py, cbs), st, in, py, px, m->grid.nt, m->n_lo, NS, P, lgP, Q, L->d_w2);
     OAM_LAUNCHED();
-    k_fft_cols<KC><<<dim3(Q, cbs), kFftThreads, sm, st>>>(L->d_w2, py, P, NS, P, lgP, 0, L->d_w1);
+    K::cols(dim3(Q, cbs), st, L->d_w2, py, P, NS, P, lgP, 0, L->d_w1);
     OAM_LAUNCHED();
     const size_t sa = (sizeof(float4) * 2 + sizeof(int2) + sizeof(long long)) * NS;
     if ((rc = set_smem((const void *)k_fft_apply_adj, sa))) return rc;
@@ -652,9 +959,9 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     k_fft_apply_adj<<<ablocks, adj_threads, sa, st>>>(L->d_shat_t, L->row_len_t, L->d_members, L->d_klo, L->d_klen,
                                                       L->d_krange, L->d_noff, nz, m->n_lo, NS, L->d_w1, L->d_w2);
     OAM_LAUNCHED();
-    k_fft_cols<KC><<<dim3(Q, cbz), kFftThreads, sm, st>>>(L->d_w2, P, py, nz, P, lgP, 1, L->d_w1);
+    K::cols(dim3(Q, cbz), st, L->d_w2, P, py, nz, P, lgP, 1, L->d_w1);
     OAM_LAUNCHED();
-    k_fft_rows_c2r<KC><<<dim3(py, cbz), kFftThreads, smr, st>>>(L->d_w1, py, px, nz, 0, nz, P, lgP, Q, scale, out);
+    K::rows_c2r(dim3(py, cbz), st, L->d_w1, py, px, nz, 0, nz, P, lgP, Q, scale, out);
     OAM_LAUNCHED();
   }
   return OAM_OK;
@@ -664,11 +971,12 @@ oam_status run_fft_any(const oam_model *m, bool fwd, const float *in, float *out
   const FftLayout *L = m->fft;
   if (!L) return OAM_ERR_UNSUPPORTED;
   ProfScope prof(m, st, fwd);
+  const bool x = L->P >= 16;  // register-pass transforms need a four-stage pass
   switch (L->KC) {
-    case 16: return run_fft<16>(m, L, fwd, in, out, st);
-    case 8: return run_fft<8>(m, L, fwd, in, out, st);
-    case 4: return run_fft<4>(m, L, fwd, in, out, st);
-    default: return run_fft<2>(m, L, fwd, in, out, st);
+    case 16: return x ? run_fft<16, XKernels<16>>(m, L, fwd, in, out, st) : run_fft<16, RKernels<16>>(m, L, fwd, in, out, st);
+    case 8: return x ? run_fft<8, XKernels<8>>(m, L, fwd, in, out, st) : run_fft<8, RKernels<8>>(m, L, fwd, in, out, st);
+    case 4: return x ? run_fft<4, XKernels<4>>(m, L, fwd, in, out, st) : run_fft<4, RKernels<4>>(m, L, fwd, in, out, st);
+    default: return x ? run_fft<2, XKernels<2>>(m, L, fwd, in, out, st) : run_fft<2, RKernels<2>>(m, L, fwd, in, out, st);
   }
 }
 
