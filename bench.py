@@ -37,9 +37,9 @@ FP32_LANES_PER_SM = 128
 TC_TRAFFIC_BYTES = 440.8e6 * 11160 / 2945
 # DRAM bytes per application of the lateral-FFT form on this workload:
 # dram__bytes_read.sum + dram__bytes_write.sum over the five launches of one
-# forward, from an ncu capture of the full 200x200x300 workload (1.189 GB read,
-# 0.243 GB written).  Set to None when those kernels change.
-FFT_TRAFFIC_BYTES = 1.4327e9
+# forward, from an ncu capture of the full 200x200x300 workload (1.191 GB read,
+# 0.250 GB written).  Set to None when those kernels change.
+FFT_TRAFFIC_BYTES = 1.4414e9
 # Band-pass filter along time: half length of the 0.5-80 MHz FIR, and the DRAM
 # bytes of one application (ncu, profiles/k_fir_lines_200x200x1024_L511.md).
 FIR_HALF = 511
