@@ -1,0 +1,182 @@
+"""Index arithmetic of the shared-memory FFT kernels, checked on the CPU.
+
+The band-pass filter kernel (``k_fir_lines`` in ``csrc/op_filter.cu``) and the
+lateral-FFT form's register-pass transforms (``k_xfft_*`` in
+``csrc/op_fft.cu``) address shared memory and global memory through a few
+formulas.  This test restates those formulas and checks, for every transform
+length the kernels accept:
+
+* the passes cover every transform stage exactly once, largest span first for
+  forward (decimation in frequency) and smallest first for inverse (decimation
+  in time);
+* every pass visits each (point, line) once, its slots are distinct and lie
+  inside the shared memory the launch allocates, and the kernels' linear slot
+  steps equal the slot formula;
+* accesses of 16 consecutive work items (a half-warp of 8-byte accesses, or a
+  quarter-warp of 16-byte ones) hit distinct banks where the padding is meant
+  to ensure it;
+* global offsets of loads and stores stay inside the arrays for ragged line
+  counts.
+
+It checks no arithmetic: the GPU parity tests do.
+"""
+import pytest
+
+
+# ------------------------------------------------------------------ k_fir_lines
+def fir_slot(KP, i, p):
+    return i * KP + p + (i >> 3)
+
+
+def fir_nslots(KP, NF):  # fir_smem / 16 bytes
+    return KP * NF + NF // 8
+
+
+def fir_pairs_per_block(NF):
+    return max(1, min(8, 4096 // NF))
+
+
+def fir_schedule(lgNF):
+    """(k, r) of the forward outer passes, the middle's spans, the inverse passes."""
+    r0 = ((lgNF - 3) & 3) or 4
+    k0 = lgNF - r0
+    fwd = [(k0, r0)] + [(k, 4) for k in range(k0 - 4, 2, -4)]
+    inv = [(k, 4) for k in range(3, k0 - 3, 4) if k + 4 <= k0] + [(k0, r0)]
+    return fwd, inv
+
+
+def fir_pass_items(KP, NF, k, r):
+    """(pair, i0, slots of the group's points) per work item, as dif_pass / dit_pass."""
+    groups = NF >> r
+    ds = (KP << k) + (1 << (k - 3))
+    for idx in range(groups * KP):
+        p, t = idx % KP, idx // KP
+        q, blk = t & ((1 << k) - 1), t >> k
+        i0 = (blk << (k + r)) | q
+        s0 = fir_slot(KP, i0, p)
+        yield p, i0, [s0 + m * ds for m in range(1 << r)], [i0 + (m << k) for m in range(1 << r)]
+
+
+@pytest.mark.parametrize("lgNF", range(4, 14))
+def test_fir_schedule_covers_every_stage_once(lgNF):
+    fwd, inv = fir_schedule(lgNF)
+    spans_f = [k + j for k, r in fwd for j in reversed(range(r))]
+    assert spans_f == list(range(lgNF - 1, 2, -1))   # spans NF/2 .. 8, largest first; the middle does 4, 2, 1
+    spans_i = [k + j for k, r in inv for j in range(r)]
+    assert spans_i == list(range(3, lgNF))            # spans 8 .. NF/2 after the middle
+    assert all(k >= 3 for k, _ in fwd + inv)          # point steps 2^k are multiples of 8 (linear slot steps)
+
+
+@pytest.mark.parametrize("lgNF", range(4, 14))
+def test_fir_passes_visit_every_point_once_inside_shared_memory(lgNF):
+    NF = 1 << lgNF
+    assert 16 * fir_nslots(fir_pairs_per_block(NF), NF) <= 227 * 1024  # the launched shape fits a block
+    for KP in sorted({1, 2, fir_pairs_per_block(NF)}):
+        n = fir_nslots(KP, NF)
+        every = {fir_slot(KP, i, p) for i in range(NF) for p in range(KP)}
+        assert len(every) == NF * KP and max(every) < n
+        fwd, inv = fir_schedule(lgNF)
+        for k, r in set(fwd + inv):
+            seen = set()
+            for p, _, slots, points in fir_pass_items(KP, NF, k, r):
+                assert slots == [fir_slot(KP, i, p) for i in points]
+                seen.update((i, p) for i in points)
+            assert len(seen) == NF * KP
+        # the middle: 8-point groups at base + j KP
+        for g in range(NF >> 3):
+            for p in range(KP):
+                base = fir_slot(KP, 8 * g, p)
+                assert [base + j * KP for j in range(8)] == [fir_slot(KP, 8 * g + j, p) for j in range(8)]
+
+
+@pytest.mark.parametrize("KP", [1, 2, 4, 8])
+def test_fir_middle_pass_is_bank_conflict_free(KP):
+    """16-byte slots: 8 consecutive groups (one quarter-warp) fall in 8 distinct
+    16-byte bank groups for every point j of the group."""
+    NF = 2048
+    groups = NF >> 3
+    for g0 in range(0, groups, 8):
+        for j in range(8):
+            banks = {(fir_slot(KP, 8 * g + j, 0)) % 8 for g in range(g0, g0 + 8)}
+            assert len(banks) == 8
+
+
+@pytest.mark.parametrize("nt,n_lines", [(1024, 40000), (192, 1023), (4, 3), (1000, 7)])
+def test_fir_global_offsets_stay_inside(nt, n_lines):
+    L = 511 if nt > 511 else nt - 1
+    lgNF = 4
+    while (1 << lgNF) < nt + min(L, nt - 1):
+        lgNF += 1
+    NF = 1 << lgNF
+    KP = fir_pairs_per_block(NF)
+    blocks = (n_lines + 4 * KP - 1) // (4 * KP)
+    fwd, _ = fir_schedule(lgNF)
+    k0, r0 = fwd[0]
+    for b in sorted({0, blocks - 1}):
+        line0 = b * 4 * KP
+        for p, _, _, points in fir_pass_items(KP, NF, k0, r0):
+            for n in points:
+                if n >= nt:
+                    continue
+                for role in range(4):
+                    if line0 + 4 * p + role < n_lines:
+                        assert 0 <= (line0 + 4 * p + role) * nt + n < n_lines * nt
+
+
+# ------------------------------------------------------------------ k_xfft_*
+def x_slot(KL, i, l):
+    return i * KL + l + ((i >> 4) * KL if KL < 16 else 0)
+
+
+def x_nslots(KL, P):
+    return P * KL + ((P >> 4) * KL if KL < 16 else 0)
+
+
+def x_schedule(lgP, forward):
+    """(kf, r) of each pass in execution order, as xtransform."""
+    npass = (lgP + 3) // 4
+    r0 = lgP - 4 * (npass - 1)
+    out = []
+    for pi in range(npass):
+        pp = pi if forward else npass - 1 - pi
+        out.append((4 * (npass - 1 - pp), r0 if pp == 0 else 4))
+    return out
+
+
+def x_pass_points(KL, P, k, r):
+    groups = P >> r
+    for idx in range(groups * KL):
+        l, t = idx % KL, idx // KL
+        q, blk = t & ((1 << k) - 1), t >> k
+        i0 = (blk << (k + r)) | q
+        yield idx, l, [i0 + (m << k) for m in range(1 << r)]
+
+
+@pytest.mark.parametrize("lgP", range(4, 12))
+def test_xfft_schedule_covers_every_stage_once(lgP):
+    f = x_schedule(lgP, True)
+    assert [k + j for k, r in f for j in reversed(range(r))] == list(range(lgP - 1, -1, -1))
+    i = x_schedule(lgP, False)
+    assert [k + j for k, r in i for j in range(r)] == list(range(lgP))
+    assert all(k % 4 == 0 for k, _ in f)
+
+
+@pytest.mark.parametrize("lgP", range(4, 12))
+@pytest.mark.parametrize("KL", [1, 2, 4, 8, 16])
+def test_xfft_passes_visit_every_point_once_without_bank_conflicts(lgP, KL):
+    P = 1 << lgP
+    n = x_nslots(KL, P)
+    assert 8 * n <= 48 * 1024 or KL * P > 4096  # the shapes the form launches fit the default 48 KB
+    every = {x_slot(KL, i, l) for i in range(P) for l in range(KL)}
+    assert len(every) == P * KL and max(every) < n
+    for k, r in set(x_schedule(lgP, True)):
+        items = list(x_pass_points(KL, P, k, r))
+        assert len({(i, l) for _, l, pts in items for i in pts}) == P * KL
+        # 16 consecutive items (one half-warp of 8-byte accesses): distinct banks per point m
+        for h in range(0, len(items) - 15, 16):
+            for m in range(1 << r):
+                pairs = set()
+                for idx, l, pts in items[h:h + 16]:
+                    s = x_slot(KL, pts[m], l)
+                    pairs.add((2 * s) % 32)
+                assert len(pairs) == 16, (k, r, h, m)
