@@ -171,7 +171,7 @@ oam_status oam_bandpass_taps(double f_lo_hz, double f_hi_hz, double fs_hz, int32
  * NF > 8192 is rejected (OAM_ERR_INVALID_ARG), as are non-finite taps.
  * Allocates the filter's spectrum and one signal-sized staging buffer (owned
  * by the model, counted in device_bytes) on `stream` and synchronises it.
- * Set the filter before recording batches that use the model. */
+ * A batch that uses the model records its graph again on its next run. */
 oam_status oam_model_set_filter(oam_model *model, const double *taps, int32_t half_len, void *stream);
 
 /* d_out = F d_in over py*px A-lines of nt samples with the model's filter

@@ -87,6 +87,7 @@ struct oam_model {
 
   oam::FftLayout *fft = nullptr;  // lateral-FFT form (OAM_PREC_FFT)
   oam::FirLayout *fir = nullptr;  // band-pass filter: forward is F A, adjoint A^T F (none: nullptr)
+  unsigned generation = 0;        // bumped when the operators' buffers change (filter set or removed)
 
   int *d_status = nullptr;  // device error word (bounded waits that ran out)
   cudaStream_t alloc_stream = nullptr;  // stream of the stream-ordered allocations (the build stream)

@@ -466,6 +466,7 @@ oam_status oam_model_set_filter(oam_model *m, const double *taps, int32_t half_l
   if (!m) return OAM_ERR_INVALID_ARG;
   cudaStream_t st = as_stream(stream);
   if (!taps || half_len < 0) {  // remove
+    if (m->fir) ++m->generation;
     fir_free(m, st);
     OAM_CUDA_TRY(cudaStreamSynchronize(st));
     return OAM_OK;
@@ -521,6 +522,7 @@ oam_status oam_model_set_filter(oam_model *m, const double *taps, int32_t half_l
   fir_free(m, st);
   m->fir = F;
   m->bytes += F->bytes;
+  ++m->generation;
   OAM_CUDA_TRY(cudaStreamSynchronize(st));
   return OAM_OK;
 }

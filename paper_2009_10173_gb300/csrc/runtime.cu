@@ -42,6 +42,7 @@ struct oam_batch {
     void *work = nullptr;
     size_t work_bytes = 0;
     bool set = false;
+    unsigned generation = 0;  // the model's generation when the graph was recorded
   };
   std::vector<Job> jobs;
   cudaStream_t origin = nullptr;
@@ -102,6 +103,7 @@ oam_status batch_capture(oam_batch *b) {
     batch_release_graph(b);
     return OAM_ERR_CUDA;
   }
+  for (auto &J : b->jobs) J.generation = J.model->generation;
   b->dirty = false;
   return OAM_OK;
 }
@@ -161,8 +163,10 @@ extern "C" oam_status oam_batch_set_job(oam_batch *b, int32_t j, const oam_model
 
 extern "C" oam_status oam_batch_run(oam_batch *b, void *stream) {
   if (!b) return OAM_ERR_INVALID_ARG;
-  for (const auto &J : b->jobs)
+  for (const auto &J : b->jobs) {
     if (!J.set) return OAM_ERR_INVALID_ARG;
+    if (J.generation != J.model->generation) b->dirty = true;  // a model's buffers changed: record again
+  }
   if (b->dirty) {
     oam_status rc = batch_capture(b);
     if (rc) return rc;

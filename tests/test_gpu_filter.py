@@ -161,6 +161,26 @@ def test_filtered_model_in_a_batch_matches_standalone():
         B.oam_batch_free(batch)
 
 
+def test_batch_records_again_after_the_filter_changes():
+    """A recorded graph holds the filter's buffers: setting another filter (or
+    removing it) makes the next run record the graph again."""
+    m = model("c0", B.OAM_PREC_FP32)
+    s = dev(inputs.gaussian(m.sig_shape, 71))
+    work = m.workspace(0)
+    batch = B.oam_batch_create(1)
+    try:
+        x = m.empty_volume()
+        B.oam_batch_set_job(batch, 0, m.handle, s, x, None, B.OamLsqrOpts(4, 0.0),
+                            B.OamFistaOpts(0, 0, 1, 0, -1.0, 1e-3, 0.0, None), work)
+        for taps in (list(bp.bandpass_taps(0.5e6, 80e6, FS, 40)), list(bp.bandpass_taps(2e6, 60e6, FS, 12)), None):
+            m.set_filter(taps)
+            ref = host(m.lsqr(s, 4)[0])
+            B.oam_batch_run(batch)
+            assert np.array_equal(host(x), ref)
+    finally:
+        B.oam_batch_free(batch)
+
+
 # ------------------------------------------------------------------ Tikhonov sweep
 DAMPS = [0.0, 0.3, 3.0, 30.0]
 
