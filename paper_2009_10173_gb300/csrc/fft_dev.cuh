@@ -1,4 +1,5 @@
-// Shared-memory radix-2 FFT of interleaved complex lines, used by the
+// Shared-memory radix-2 FFT of interleaved complex lines and the small
+// twiddle constants, used by the
 // lateral-FFT operator form and by the band-pass filter along time.
 #pragma once
 
@@ -72,6 +73,24 @@ __device__ void fft_lines(float2 *a, const float2 *tw, int P, int lgP, bool inve
 }
 
 __device__ __forceinline__ int bitrev(int x, int lg) { return (int)(__brev((unsigned)x) >> (32 - lg)); }
+
+constexpr float kRsqrt2 = 0.70710678118654752f;  // cos(pi/4) = sin(pi/4)
+constexpr float kCosPi8 = 0.92387953251128676f;  // cos(pi/8)
+constexpr float kSinPi8 = 0.38268343236508977f;  // sin(pi/8)
+
+// W_N^u = exp(-2 pi i u / N) for N <= 16 (u < N/2), from the constants above.
+__device__ __forceinline__ float2 w16(int N, int u) {
+  switch (u * (16 / N)) {  // in sixteenths of a turn
+    case 0: return make_float2(1.0f, 0.0f);
+    case 1: return make_float2(kCosPi8, -kSinPi8);
+    case 2: return make_float2(kRsqrt2, -kRsqrt2);
+    case 3: return make_float2(kSinPi8, -kCosPi8);
+    case 4: return make_float2(0.0f, -1.0f);
+    case 5: return make_float2(-kSinPi8, -kCosPi8);
+    case 6: return make_float2(-kRsqrt2, -kRsqrt2);
+    default: return make_float2(-kCosPi8, -kSinPi8);  // 7
+  }
+}
 
 }  // namespace fftdev
 }  // namespace oam

@@ -198,24 +198,6 @@ __host__ __device__ constexpr size_t xslots(int P) {
   return (size_t)P * KL + (KL < 16 ? (size_t)(P >> 4) * KL : 0);
 }
 
-constexpr float kXRsqrt2 = 0.70710678118654752f;  // cos(pi/4) = sin(pi/4)
-constexpr float kXCos8 = 0.92387953251128676f;    // cos(pi/8)
-constexpr float kXSin8 = 0.38268343236508977f;    // sin(pi/8)
-
-// W_N^u = exp(-2 pi i u / N) for N <= 16 (u < N/2).
-__device__ __forceinline__ float2 xw_small(int N, int u) {
-  switch (u * (16 / N)) {
-    case 0: return make_float2(1.0f, 0.0f);
-    case 1: return make_float2(kXCos8, -kXSin8);
-    case 2: return make_float2(kXRsqrt2, -kXRsqrt2);
-    case 3: return make_float2(kXSin8, -kXCos8);
-    case 4: return make_float2(0.0f, -1.0f);
-    case 5: return make_float2(-kXSin8, -kXCos8);
-    case 6: return make_float2(-kXRsqrt2, -kXRsqrt2);
-    default: return make_float2(-kXCos8, -kXSin8);
-  }
-}
-
 // One pass of r stages over the points i0 + m 2^k (m < 2^r) of each group
 // (line l, q < 2^k, block blk; i0 = blk 2^(k+r) + q).  Forward (decimation in
 // frequency, spans from large to small): span S = 2^(k+j) maps (u, w) at
@@ -250,7 +232,7 @@ __device__ __forceinline__ void xpass(int P, int k, Src src, Dst dst) {
           const float2 u = v[m], w = v[m + S];
           v[m] = make_float2(u.x + w.x, u.y + w.y);
           const int um = m & (S - 1);
-          const float2 tw = um == 0 ? pw[j] : cmul(pw[j], xw_small(2 * S, um));
+          const float2 tw = um == 0 ? pw[j] : cmul(pw[j], w16(2 * S, um));
           v[m + S] = cmul(make_float2(u.x - w.x, u.y - w.y), tw);
         }
       }
@@ -262,7 +244,7 @@ __device__ __forceinline__ void xpass(int P, int k, Src src, Dst dst) {
         for (int m = 0; m < R; ++m) {
           if (m & S) continue;
           const int um = m & (S - 1);
-          const float2 tw = um == 0 ? pw[j] : cmul(pw[j], xw_small(2 * S, um));
+          const float2 tw = um == 0 ? pw[j] : cmul(pw[j], w16(2 * S, um));
           const float2 u = v[m], w = cmul(v[m + S], make_float2(tw.x, -tw.y));
           v[m] = make_float2(u.x + w.x, u.y + w.y);
           v[m + S] = make_float2(u.x - w.x, u.y - w.y);

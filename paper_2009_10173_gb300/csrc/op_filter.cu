@@ -57,25 +57,6 @@ constexpr int kFirMaxSize = 8192;  // largest transform: 132 KB of shared memory
 
 size_t fir_smem(int NF, int KP) { return sizeof(ulonglong2) * ((size_t)KP * NF + NF / 8); }
 
-constexpr float kRsqrt2 = 0.70710678118654752f;  // cos(pi/4) = sin(pi/4)
-constexpr float kCos8 = 0.92387953251128676f;    // cos(pi/8)
-constexpr float kSin8 = 0.38268343236508977f;    // sin(pi/8)
-
-// W_N^u = exp(-2 pi i u / N) for N <= 16 (u < N/2), from the constants above.
-__device__ __forceinline__ float2 w_small(int N, int u) {
-  const int e = u * (16 / N);  // in sixteenths
-  switch (e) {
-    case 0: return make_float2(1.0f, 0.0f);
-    case 1: return make_float2(kCos8, -kSin8);
-    case 2: return make_float2(kRsqrt2, -kRsqrt2);
-    case 3: return make_float2(kSin8, -kCos8);
-    case 4: return make_float2(0.0f, -1.0f);
-    case 5: return make_float2(-kSin8, -kCos8);
-    case 6: return make_float2(-kRsqrt2, -kRsqrt2);
-    default: return make_float2(-kCos8, -kSin8);  // 7
-  }
-}
-
 // Packed FP32 pairs (two lanes of one 64-bit register) and their arithmetic.
 __device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
   uint64_t r;
@@ -189,7 +170,7 @@ __device__ __forceinline__ void dif_pass(ulonglong2 *a, int NF, int k, const flo
         const Cx2 u = v[m], w = v[m + S];
         v[m] = x_add(u, w);
         const int um = m & (S - 1);
-        const float2 tw = um == 0 ? pw[j] : cmul(pw[j], w_small(2 * S, um));
+        const float2 tw = um == 0 ? pw[j] : cmul(pw[j], w16(2 * S, um));
         v[m + S] = x_mul(x_sub(u, w), tw);
       }
     }
@@ -230,7 +211,7 @@ __device__ __forceinline__ void dit_pass(ulonglong2 *a, int NF, int k, float *y,
       for (int m = 0; m < R; ++m) {
         if (m & S) continue;
         const int um = m & (S - 1);
-        const float2 tw = um == 0 ? pw[j] : cmul(pw[j], w_small(2 * S, um));
+        const float2 tw = um == 0 ? pw[j] : cmul(pw[j], w16(2 * S, um));
         const Cx2 u = v[m], w = x_mul(v[m + S], make_float2(tw.x, -tw.y));
         v[m] = x_add(u, w);
         v[m + S] = x_sub(u, w);
