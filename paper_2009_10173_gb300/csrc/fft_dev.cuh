@@ -1,6 +1,6 @@
-// Shared-memory radix-2 FFT of interleaved complex lines and the small
-// twiddle constants, used by the
-// lateral-FFT operator form and by the band-pass filter along time.
+// Shared-memory radix-2 FFT of interleaved complex lines and the 16-point
+// twiddle constants, used by the lateral-FFT operator form and by the
+// band-pass filter along time.
 #pragma once
 
 #include <cuda_runtime.h>
