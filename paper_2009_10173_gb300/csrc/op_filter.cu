@@ -24,8 +24,10 @@
 // over shared memory: the first forward pass reads the A-lines from global
 // memory, the three smallest spans of both transforms and the product share
 // one pass on 8-point groups, and the last inverse pass writes the filtered
-// A-lines to global memory.  Each sample is read from and written to HBM once
-// and goes through shared memory four times each way at NF = 2048.
+// A-lines to global memory.  A thread carries the same points of two complex
+// lines as packed FP32 pairs, so each twiddle serves both.  Each sample is read
+// from and written to HBM once and goes through shared memory four times each
+// way at NF = 2048.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -53,7 +55,7 @@ namespace {
 using namespace oam::fftdev;
 
 constexpr int kFirThreads = 256;
-constexpr int kFirMaxSize = 8192;  // largest transform: 132 KB of shared memory per line pair
+constexpr int kFirMaxSize = 8192;  // largest transform: 144 KiB of shared memory for one line pair
 
 size_t fir_smem(int NF, int KP) { return sizeof(ulonglong2) * ((size_t)KP * NF + NF / 8); }
 
