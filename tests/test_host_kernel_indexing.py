@@ -16,10 +16,13 @@ length the kernels accept:
   quarter-warp of 16-byte ones) hit distinct banks where the padding is meant
   to ensure it;
 * global offsets of loads and stores stay inside the arrays for ragged line
-  counts.
+  counts;
+* float64 models of the stage arithmetic, run through the same schedules on
+  small sizes, give numpy's DFT and the direct convolution.
 
-It checks no arithmetic: the GPU parity tests do.
+The kernels' own arithmetic is checked by the GPU parity tests.
 """
+import numpy as np
 import pytest
 
 
@@ -180,3 +183,92 @@ def test_xfft_passes_visit_every_point_once_without_bank_conflicts(lgP, KL):
                     s = x_slot(KL, pts[m], l)
                     pairs.add((2 * s) % 32)
                 assert len(pairs) == 16, (k, r, h, m)
+
+
+# ------------------------------------------------------------------ the schedules carry out the transforms
+# Float64 models of the two kernels' stage arithmetic (the twiddle of span S at
+# point n is W_2S^(n mod S), factored as W_2S^q times a 16-point constant, the
+# q factor from one base twiddle by squaring), run through the schedules above
+# and compared with numpy's FFT.  Small sizes only; the GPU tests check the
+# kernels themselves.
+
+def _w16(N, u):
+    return np.exp(-2j * np.pi * u / N)
+
+
+def _pass(P, k, r, forward, v_of, put):
+    """One pass of r stages over the groups of all lines, as xpass / dif_pass / dit_pass."""
+    R = 1 << r
+    for t in range(P >> r):
+        q, blk = t & ((1 << k) - 1), t >> k
+        i0 = (blk << (k + r)) | q
+        v = [v_of(i0 + (m << k)) for m in range(R)]
+        pw = [None] * r
+        pw[r - 1] = np.exp(-2j * np.pi * q / (1 << (k + r)))
+        for j in range(r - 2, -1, -1):
+            pw[j] = pw[j + 1] ** 2
+        order = range(r - 1, -1, -1) if forward else range(r)
+        for j in order:
+            S = 1 << j
+            for m in range(R):
+                if m & S:
+                    continue
+                um = m & (S - 1)
+                tw = pw[j] if um == 0 else pw[j] * _w16(2 * S, um)
+                u, w = v[m], v[m + S]
+                if forward:
+                    v[m], v[m + S] = u + w, (u - w) * tw
+                else:
+                    w = w * np.conj(tw)
+                    v[m], v[m + S] = u + w, u - w
+        for m in range(R):
+            put(i0 + (m << k), v[m])
+
+
+def _bitrev(x, lg):
+    return int(format(x, "0%db" % lg)[::-1], 2) if lg else 0
+
+
+@pytest.mark.parametrize("lgP", [4, 5, 6, 7, 8, 9])
+def test_xfft_schedules_compute_the_dft(lgP):
+    P = 1 << lgP
+    rng = np.random.Generator(np.random.PCG64(lgP))
+    x = rng.standard_normal(P) + 1j * rng.standard_normal(P)
+    a = x.copy()
+    for k, r in x_schedule(lgP, True):
+        _pass(P, k, r, True, lambda i: a[i], a.__setitem__)
+    X = np.fft.fft(x)
+    assert np.allclose([a[_bitrev(f, lgP)] for f in range(P)], X, atol=1e-10 * np.abs(X).max())
+    b = np.array([X[_bitrev(i, lgP)] for i in range(P)])  # inverse input: frequency bitrev(i) at position i
+    for k, r in x_schedule(lgP, False):
+        _pass(P, k, r, False, lambda i: b[i], b.__setitem__)
+    assert np.allclose(b / P, x, atol=1e-12 * np.abs(x).max())
+
+
+@pytest.mark.parametrize("lgNF,L", [(4, 3), (5, 10), (7, 40), (8, 100), (9, 200)])
+def test_fir_schedule_computes_the_convolution(lgNF, L):
+    """Forward outer passes, the 8-point middle (spans 4, 2, 1, product,
+    spans 1, 2, 4), inverse outer passes: a circular convolution with the even
+    taps, equal to the direct sum on the first NF - L points."""
+    NF = 1 << lgNF
+    nt = NF - L
+    rng = np.random.Generator(np.random.PCG64(100 + lgNF))
+    x = rng.standard_normal(nt) + 1j * rng.standard_normal(nt)
+    h = rng.standard_normal(L + 1)
+    f = np.arange(NF)
+    H = h[0] + 2 * sum((h[m] * np.cos(2 * np.pi * f * m / NF) for m in range(1, L + 1)), np.zeros(NF))
+    hb = np.array([H[_bitrev(i, lgNF)] for i in range(NF)]) / NF
+    a = np.zeros(NF, complex)
+    a[:nt] = x
+    fwd, inv = fir_schedule(lgNF)
+    for k, r in fwd:
+        _pass(NF, k, r, True, lambda i: a[i], a.__setitem__)
+    for g in range(NF >> 3):  # the middle: forward spans 4, 2, 1 on 8-point groups, product, inverse spans 1, 2, 4
+        _pass(8, 0, 3, True, lambda i: a[8 * g + i], lambda i, v: a.__setitem__(8 * g + i, v))
+        a[8 * g: 8 * g + 8] *= hb[8 * g: 8 * g + 8]
+        _pass(8, 0, 3, False, lambda i: a[8 * g + i], lambda i, v: a.__setitem__(8 * g + i, v))
+    for k, r in inv:
+        _pass(NF, k, r, False, lambda i: a[i], a.__setitem__)
+    full = np.concatenate([h[:0:-1], h])
+    want = np.convolve(x, full)[L:L + nt]
+    assert np.allclose(a[:nt], want, atol=1e-10 * np.abs(want).max())
