@@ -334,7 +334,8 @@ oam_status oam_server_stop(oam_server *server);
 /* ---------------------------------------------------------------- timing */
 /* Device time of the operator kernels, measured with CUDA events recorded on
  * the caller's stream around the main kernel of every forward / adjoint
- * (including those inside the solvers). */
+ * (including those inside the solvers).  The band-pass filter of a filtered
+ * model runs outside these events. */
 typedef struct {
   int64_t forward_calls, adjoint_calls;
   double forward_ms, adjoint_ms; /* summed event-to-event durations */
