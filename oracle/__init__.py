@@ -13,7 +13,10 @@ benchmark's CPU-baseline leg import this package; the product path
 * ``forward_fft`` / ``adjoint_fft``: the same operators restated exactly
   through the 2-D correlation theorem over the zero-padded scan grid, with a
   project-written radix-2 FFT (``fft``); ``slab_dft`` is the transform of one
-  slab slice.
+  slab slice.  ``Spectral`` keeps the slab's half spectrum per (depth,
+  sample) so that large grids (200 x 200 positions, 61 x 61 taps) can be
+  applied hundreds of times; ``Spectral.forward`` / ``Spectral.adjoint`` are
+  the same two operators.
 * ``oracle.solvers``: LSQR for Eq. 5 with Eq. 6 (MB-L2) and FISTA for Eq. 5
   with Eq. 7 (MB-L1), written from the published algorithms the paper names.
 * ``oracle.bandpass``: the band-pass filtering of signals and model along
@@ -67,10 +70,16 @@ def lib():
         L.orc_slab_dft.argtypes = [dp, i32, i32, i32, i32, i32, i32, dp, dp]
         L.orc_forward_fft.argtypes = [dp, i32, i32, i32, i32, i32, i32, dp, dp]
         L.orc_adjoint_fft.argtypes = [dp, i32, i32, i32, i32, i32, i32, dp, dp]
+        lp = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+        L.orc_depth_band.argtypes = [P, f64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.orc_spectrum_depth.argtypes = [P, f64, i32, i32, i32, i32, i32, dp, dp]
+        L.orc_forward_spec.argtypes = [dp, dp, ip, ip, lp, i32, i32, i32, i32, i32, i32, dp, dp]
+        L.orc_adjoint_spec.argtypes = [dp, dp, ip, ip, lp, i32, i32, i32, i32, i32, i32, dp, dp]
         for f in ("orc_patch_count_rings", "orc_patches", "orc_distance_range", "orc_t0",
                   "orc_slab_column", "orc_slab", "orc_slab_time_slice", "orc_forward",
                   "orc_adjoint", "orc_forward_at", "orc_fft", "orc_slab_dft", "orc_forward_fft",
-                  "orc_adjoint_fft"):
+                  "orc_adjoint_fft", "orc_depth_band", "orc_spectrum_depth", "orc_forward_spec",
+                  "orc_adjoint_spec"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -255,3 +264,97 @@ def adjoint_fft(S, s, P=None):
     H = np.zeros((py, px, nz))
     _check(lib().orc_adjoint_fft(S, win, nz, nt, py, px, P, s, H))
     return H
+
+
+class Spectral:
+    """A and A^T of a configuration through the lateral correlation theorem,
+    with the slab's spectrum computed once.
+
+    For every depth k the band [klo[k], klo[k] + klen[k]) holds all samples
+    any patch's EIR window reaches at that depth (the slab is exactly zero
+    elsewhere); for each (k, n) in it the 2-D DFT of the slice S[:, :, k, n]
+    placed at (b mod P, a mod P) is stored for columns u = 0 .. P/2 (the
+    slab is real, so the other half follows by Hermitian symmetry).  Memory:
+    16 * sum(klen) * P * (P/2 + 1) bytes.  Building evaluates every slab
+    column once (Eqs. 3-4); each application then costs the 2-D transforms
+    of the input and output and the spectral sums.
+    """
+
+    def __init__(self, cfg, t0_s=None, P=None, symmetric=False):
+        """``symmetric``: evaluate Eq. 3 for one tap per orbit of the patch
+        set's mirror (and, for dx == dy, x <-> y) symmetry and copy it to
+        the orbit's other taps (same terms, summed in another order)."""
+        p = params(cfg)
+        self.t0 = t0(cfg) if t0_s is None else float(t0_s)
+        self.win, self.nz, self.nt, self.py, self.px = p.win, p.nz, p.nt, p.py, p.px
+        self.R = (p.win - 1) // 2
+        self.P = fft_size(p.py, p.px, p.win) if P is None else int(P)
+        Q = self.P // 2 + 1
+        L = lib()
+        self.klo = np.zeros(p.nz, np.int32)
+        self.klen = np.zeros(p.nz, np.int32)
+        lo, ln = ctypes.c_int32(), ctypes.c_int32()
+        for k in range(p.nz):
+            _check(L.orc_depth_band(ctypes.byref(p), self.t0, k, ctypes.byref(lo), ctypes.byref(ln)))
+            self.klo[k], self.klen[k] = lo.value, ln.value
+        self.koff = np.zeros(p.nz, np.int64)
+        self.koff[1:] = np.cumsum(self.klen.astype(np.int64))[:-1]
+        total = int(self.klen.sum())
+        self.re = np.zeros((max(total, 1), self.P, Q))
+        self.im = np.zeros((max(total, 1), self.P, Q))
+        for k in range(p.nz):
+            if self.klen[k] == 0:
+                continue
+            a, b = int(self.koff[k]), int(self.koff[k] + self.klen[k])
+            _check(L.orc_spectrum_depth(ctypes.byref(p), self.t0, k, self.P, int(self.klo[k]),
+                                        int(self.klen[k]), int(bool(symmetric)), self.re[a:b], self.im[a:b]))
+
+    @classmethod
+    def from_dense(cls, S, py, px, P=None):
+        """The same operators for a given dense slab S[win][win][nz][nt]
+        (any values, no symmetry assumed): depth k's band is the union of its
+        nonzero samples over taps, each slice transformed by ``slab_dft``."""
+        S = np.ascontiguousarray(S, np.float64)
+        self = cls.__new__(cls)
+        self.win, _, self.nz, self.nt = S.shape
+        self.py, self.px = py, px
+        self.R = (self.win - 1) // 2
+        self.P = fft_size(py, px, self.win) if P is None else int(P)
+        Q = self.P // 2 + 1
+        nzmask = (S != 0).any(axis=(0, 1))  # [nz][nt]
+        self.klo = np.zeros(self.nz, np.int32)
+        self.klen = np.zeros(self.nz, np.int32)
+        for k in range(self.nz):
+            idx = np.flatnonzero(nzmask[k])
+            if len(idx):
+                self.klo[k], self.klen[k] = idx[0], idx[-1] - idx[0] + 1
+        self.koff = np.zeros(self.nz, np.int64)
+        self.koff[1:] = np.cumsum(self.klen.astype(np.int64))[:-1]
+        total = int(self.klen.sum())
+        self.re = np.zeros((max(total, 1), self.P, Q))
+        self.im = np.zeros((max(total, 1), self.P, Q))
+        self.t0 = float("nan")
+        for k in range(self.nz):
+            for i in range(int(self.klen[k])):
+                X = slab_dft(S, k, int(self.klo[k]) + i, self.P)
+                self.re[self.koff[k] + i] = X.real[:, :Q]
+                self.im[self.koff[k] + i] = X.imag[:, :Q]
+        return self
+
+    def forward(self, H):
+        """A H (Eq. 4 over the scan grid), H[py][px][nz] -> s[py][px][nt]."""
+        H = np.ascontiguousarray(H, np.float64)
+        assert H.shape == (self.py, self.px, self.nz)
+        s = np.zeros((self.py, self.px, self.nt))
+        _check(lib().orc_forward_spec(self.re, self.im, self.klo, self.klen, self.koff, self.nz, self.nt,
+                                      self.P, self.R, self.py, self.px, H, s))
+        return s
+
+    def adjoint(self, s):
+        """A^T s, s[py][px][nt] -> H[py][px][nz]."""
+        s = np.ascontiguousarray(s, np.float64)
+        assert s.shape == (self.py, self.px, self.nt)
+        H = np.zeros((self.py, self.px, self.nz))
+        _check(lib().orc_adjoint_spec(self.re, self.im, self.klo, self.klen, self.koff, self.nz, self.nt,
+                                      self.P, self.R, self.py, self.px, s, H))
+        return H

@@ -540,3 +540,253 @@ int orc_adjoint_fft(const double *S, int win, int nz, int nt, int py, int px, in
   free(Sr); free(Si);
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Lateral-FFT restatement with the slab's spectrum computed once.          */
+/* Same correlation-theorem identities as above; the spectrum of every     */
+/* slab slice (k, n) inside depth k's band is transformed once per model    */
+/* and kept, so an application costs the input and output transforms and  */
+/* the spectral sums only.  Depth k's band [klo, klo + klen) is the union,  */
+/* over taps and patches, of the samples each patch's EIR window can reach */
+/* (all other samples of depth k are exactly zero).  The slab is real, so  */
+/* its spectrum is Hermitian: only columns u = 0 .. P/2 are stored, and    */
+/* an output spectrum (also of real data) is completed from those columns  */
+/* by X(v, u) = conj(X(-v, -u)) before the inverse transform.               */
+/* ------------------------------------------------------------------------ */
+
+/* Depth k's band: the union over taps and patches of the patch's EIR      */
+/* window [ceil(D_j - cut), floor(D_j + cut)], clipped to [0, nt).         */
+int orc_depth_band(const orc_params *p, double t0, int k, int *klo, int *klen) {
+  patchset ps;
+  int rc = load_patches(p, &ps);
+  if (rc) return rc;
+  int R = (p->win - 1) / 2;
+  double s, w, cut;
+  eir_consts(p, &s, &w, &cut);
+  int lo = p->nt, hi = -1, W = p->win;
+#pragma omp parallel for reduction(min : lo) reduction(max : hi) schedule(static)
+  for (int t = 0; t < W * W; ++t) {
+    int b = t / W - R, a = t % W - R;
+    for (int j = 0; j < ps.M; ++j) {
+        double d = dist(p, a * p->dx_m, b * p->dy_m, p->z0_rel_m + k * p->dz_m, ps.nx[j], ps.ny[j], ps.nz[j]);
+        double Dj = p->fs_hz * (d / p->c_mps - t0);
+        int n0 = (int)ceil(Dj - cut), n1 = (int)floor(Dj + cut);
+        if (n0 < 0) n0 = 0;
+        if (n1 > p->nt - 1) n1 = p->nt - 1;
+        if (n0 > n1) continue;
+        if (n0 < lo) lo = n0;
+        if (n1 > hi) hi = n1;
+    }
+  }
+  free(ps.nx);
+  if (hi < lo) { *klo = 0; *klen = 0; } else { *klo = lo; *klen = hi - lo + 1; }
+  return ORC_OK;
+}
+
+/* Half spectra of the slab slices (k, n), n in [klo, klo + klen):          */
+/* re/im[(n - klo)][v][u], v in [0, P), u in [0, P/2], of the 2-D DFT of    */
+/* S[.][.][k][n] placed at (b mod P, a mod P) (sign -1, unscaled).          */
+/* symmetric != 0 evaluates Eq. 3 only for one tap per orbit of the patch   */
+/* set's symmetries -- (b, a) ~ (+-b, +-a), and (a, b) when dx == dy         */
+/* (axial symmetry, Results) -- and copies that column to the orbit's other */
+/* taps; the direct evaluation of those taps sums the same terms in another */
+/* order, so the two agree to rounding.                                     */
+int orc_spectrum_depth(const orc_params *p, double t0, int k, int P, int klo, int klen, int symmetric,
+                       double *re, double *im) {
+  int R = (p->win - 1) / 2, W = p->win;
+  if (!is_pow2(P) || P < W || klo < 0 || klen < 0 || klo + klen > p->nt) return ORC_EINVAL;
+  patchset ps;
+  int rc = load_patches(p, &ps);
+  if (rc) return rc;
+  const size_t nt = p->nt, PP = (size_t)P * P, Q = P / 2 + 1;
+  double *cols = calloc((size_t)W * W * nt, sizeof(double)); /* S[b][a][k][0..nt) */
+  if (!cols) { free(ps.nx); return ORC_ENOMEM; }
+  const int swap = symmetric && p->dx_m == p->dy_m;
+#pragma omp parallel for schedule(dynamic)
+  for (int t = 0; t < W * W; ++t) {
+    int b = t / W - R, a = t % W - R;
+    if (symmetric && (b < 0 || a < 0 || (swap && a > b))) continue; /* not an orbit representative */
+    voxel_signal(p, &ps, t0, a * p->dx_m, b * p->dy_m, p->z0_rel_m + k * p->dz_m, cols + (size_t)t * nt);
+  }
+  free(ps.nx);
+  if (symmetric)
+    for (int t = 0; t < W * W; ++t) {
+      int b = abs(t / W - R), a = abs(t % W - R);
+      if (swap && a > b) { int x = a; a = b; b = x; }
+      int rep = (b + R) * W + (a + R);
+      if (rep != t) memcpy(cols + (size_t)t * nt, cols + (size_t)rep * nt, sizeof(double) * nt);
+    }
+#pragma omp parallel
+  {
+    double *tr = malloc(sizeof(double) * PP), *ti = malloc(sizeof(double) * PP);
+    if (!tr || !ti) {
+#pragma omp atomic write
+      rc = ORC_ENOMEM;
+    } else {
+#pragma omp for schedule(dynamic)
+      for (int i = 0; i < klen; ++i) {
+        int n = klo + i;
+        memset(tr, 0, sizeof(double) * PP);
+        memset(ti, 0, sizeof(double) * PP);
+        for (int b = -R; b <= R; ++b)
+          for (int a = -R; a <= R; ++a)
+            tr[(size_t)((b + P) % P) * P + (a + P) % P] = cols[((size_t)(b + R) * W + (a + R)) * nt + n];
+        fft2(tr, ti, P, -1);
+        double *dr = re + (size_t)i * P * Q, *di = im + (size_t)i * P * Q;
+        for (int v = 0; v < P; ++v)
+          for (size_t u = 0; u < Q; ++u) {
+            dr[(size_t)v * Q + u] = tr[(size_t)v * P + u];
+            di[(size_t)v * Q + u] = ti[(size_t)v * P + u];
+          }
+      }
+    }
+    free(tr); free(ti);
+  }
+  free(cols);
+  return rc;
+}
+
+/* Complete a half spectrum (columns 0..P/2) of real data to all P columns  */
+/* and transform back (sign +1); out[y][x] = Re / P^2 for y < py, x < px.    */
+static void half_inverse(const double *hr, const double *hi, int P, double *tr, double *ti) {
+  const size_t Q = P / 2 + 1;
+  for (int v = 0; v < P; ++v)
+    for (int u = 0; u < P; ++u) {
+      size_t d = (size_t)v * P + u;
+      if ((size_t)u < Q) {
+        tr[d] = hr[(size_t)v * Q + u];
+        ti[d] = hi[(size_t)v * Q + u];
+      } else { /* X(v, u) = conj(X(-v, -u)) */
+        size_t sidx = (size_t)((P - v) % P) * Q + (size_t)(P - u);
+        tr[d] = hr[sidx];
+        ti[d] = -hi[sidx];
+      }
+    }
+  fft2(tr, ti, P, +1);
+}
+
+/* A H from the stored half spectra.  klo/klen: per-depth bands; koff[k]:   */
+/* index of depth k's first slice in re/im (slices of P x (P/2+1)).         */
+int orc_forward_spec(const double *re, const double *im, const int *klo, const int *klen, const long long *koff,
+                     int nz, int nt, int P, int R, int py, int px, const double *H, double *s) {
+  const size_t PP = (size_t)P * P, Q = P / 2 + 1, PQ = (size_t)P * Q;
+  if (!fft_pad_ok(P, R, py, px)) return ORC_EINVAL;
+  double *Hr = malloc(sizeof(double) * PQ * nz), *Hi = malloc(sizeof(double) * PQ * nz);
+  if (!Hr || !Hi) { free(Hr); free(Hi); return ORC_ENOMEM; }
+  int rc = ORC_OK;
+#pragma omp parallel
+  {
+    double *tr = malloc(sizeof(double) * PP), *ti = malloc(sizeof(double) * PP);
+    double *ar = malloc(sizeof(double) * PQ), *ai = malloc(sizeof(double) * PQ);
+    if (!tr || !ti || !ar || !ai) {
+#pragma omp atomic write
+      rc = ORC_ENOMEM;
+    } else {
+#pragma omp for schedule(dynamic)
+      for (int k = 0; k < nz; ++k) { /* H^_k, half spectrum */
+        memset(tr, 0, sizeof(double) * PP);
+        memset(ti, 0, sizeof(double) * PP);
+        for (int y = 0; y < py; ++y)
+          for (int x = 0; x < px; ++x) tr[(size_t)y * P + x] = H[((size_t)y * px + x) * nz + k];
+        fft2(tr, ti, P, -1);
+        for (int v = 0; v < P; ++v)
+          for (size_t u = 0; u < Q; ++u) {
+            Hr[k * PQ + (size_t)v * Q + u] = tr[(size_t)v * P + u];
+            Hi[k * PQ + (size_t)v * Q + u] = ti[(size_t)v * P + u];
+          }
+      }
+#pragma omp for schedule(dynamic)
+      for (int n = 0; n < nt; ++n) {
+        int any = 0;
+        memset(ar, 0, sizeof(double) * PQ);
+        memset(ai, 0, sizeof(double) * PQ);
+        for (int k = 0; k < nz; ++k) {
+          if (n < klo[k] || n >= klo[k] + klen[k]) continue;
+          any = 1;
+          const double *sr = re + (size_t)(koff[k] + (n - klo[k])) * PQ, *si = im + (size_t)(koff[k] + (n - klo[k])) * PQ;
+          const double *hr = Hr + k * PQ, *hi = Hi + k * PQ;
+          for (size_t f = 0; f < PQ; ++f) { /* conj(S^) * H^ */
+            ar[f] += sr[f] * hr[f] + si[f] * hi[f];
+            ai[f] += sr[f] * hi[f] - si[f] * hr[f];
+          }
+        }
+        if (!any) {
+          for (int y = 0; y < py; ++y)
+            for (int x = 0; x < px; ++x) s[((size_t)y * px + x) * nt + n] = 0.0;
+          continue;
+        }
+        half_inverse(ar, ai, P, tr, ti);
+        for (int y = 0; y < py; ++y)
+          for (int x = 0; x < px; ++x) s[((size_t)y * px + x) * nt + n] = tr[(size_t)y * P + x] / (double)PP;
+      }
+    }
+    free(tr); free(ti); free(ar); free(ai);
+  }
+  free(Hr); free(Hi);
+  return rc;
+}
+
+/* A^T s from the stored half spectra. */
+int orc_adjoint_spec(const double *re, const double *im, const int *klo, const int *klen, const long long *koff,
+                     int nz, int nt, int P, int R, int py, int px, const double *s, double *H) {
+  const size_t PP = (size_t)P * P, Q = P / 2 + 1, PQ = (size_t)P * Q;
+  if (!fft_pad_ok(P, R, py, px)) return ORC_EINVAL;
+  int nlo = nt, nhi = 0; /* samples some band reaches */
+  for (int k = 0; k < nz; ++k)
+    if (klen[k] > 0) {
+      if (klo[k] < nlo) nlo = klo[k];
+      if (klo[k] + klen[k] > nhi) nhi = klo[k] + klen[k];
+    }
+  const int NS = nhi > nlo ? nhi - nlo : 0;
+  double *Sr = malloc(sizeof(double) * PQ * (NS ? NS : 1)), *Si = malloc(sizeof(double) * PQ * (NS ? NS : 1));
+  if (!Sr || !Si) { free(Sr); free(Si); return ORC_ENOMEM; }
+  int rc = ORC_OK;
+#pragma omp parallel
+  {
+    double *tr = malloc(sizeof(double) * PP), *ti = malloc(sizeof(double) * PP);
+    double *ar = malloc(sizeof(double) * PQ), *ai = malloc(sizeof(double) * PQ);
+    if (!tr || !ti || !ar || !ai) {
+#pragma omp atomic write
+      rc = ORC_ENOMEM;
+    } else {
+#pragma omp for schedule(dynamic)
+      for (int i = 0; i < NS; ++i) { /* s^_n, half spectrum */
+        int n = nlo + i;
+        memset(tr, 0, sizeof(double) * PP);
+        memset(ti, 0, sizeof(double) * PP);
+        for (int y = 0; y < py; ++y)
+          for (int x = 0; x < px; ++x) tr[(size_t)y * P + x] = s[((size_t)y * px + x) * nt + n];
+        fft2(tr, ti, P, -1);
+        for (int v = 0; v < P; ++v)
+          for (size_t u = 0; u < Q; ++u) {
+            Sr[i * PQ + (size_t)v * Q + u] = tr[(size_t)v * P + u];
+            Si[i * PQ + (size_t)v * Q + u] = ti[(size_t)v * P + u];
+          }
+      }
+#pragma omp for schedule(dynamic)
+      for (int k = 0; k < nz; ++k) {
+        if (klen[k] == 0) {
+          for (int y = 0; y < py; ++y)
+            for (int x = 0; x < px; ++x) H[((size_t)y * px + x) * nz + k] = 0.0;
+          continue;
+        }
+        memset(ar, 0, sizeof(double) * PQ);
+        memset(ai, 0, sizeof(double) * PQ);
+        for (int n = klo[k]; n < klo[k] + klen[k]; ++n) {
+          const double *sr = re + (size_t)(koff[k] + (n - klo[k])) * PQ, *si = im + (size_t)(koff[k] + (n - klo[k])) * PQ;
+          const double *xr = Sr + (size_t)(n - nlo) * PQ, *xi = Si + (size_t)(n - nlo) * PQ;
+          for (size_t f = 0; f < PQ; ++f) { /* S^ * s^ */
+            ar[f] += sr[f] * xr[f] - si[f] * xi[f];
+            ai[f] += sr[f] * xi[f] + si[f] * xr[f];
+          }
+        }
+        half_inverse(ar, ai, P, tr, ti);
+        for (int y = 0; y < py; ++y)
+          for (int x = 0; x < px; ++x) H[((size_t)y * px + x) * nz + k] = tr[(size_t)y * P + x] / (double)PP;
+      }
+    }
+    free(tr); free(ti); free(ar); free(ai);
+  }
+  free(Sr); free(Si);
+  return rc;
+}

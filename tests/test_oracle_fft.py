@@ -11,6 +11,10 @@ them exactly.  What pins the restatement:
   on the 32x32x48 workload and on a 64x64x64 case, and on a random slab with
   no symmetry at all (so a missing conjugate, a flipped index or a wrong pad
   cannot hide behind the slab's mirror symmetry);
+* the cached-spectrum form (``oracle.Spectral``, the slab's half spectrum
+  computed once, used for the full-size reference reconstructions) equals
+  the direct correlations to <= 1e-12 on both cases and on a random slab
+  with no symmetry, and its per-depth bands hold every nonzero slab sample;
 * the DFT of a slab slice is real and symmetric under (v, u) -> (u, v) when
   dx = dy, the properties the GPU form relies on (mirror symmetry of the
   patch set, Results, axial symmetry).
@@ -101,3 +105,49 @@ def test_slab_dft_is_real_and_d4_symmetric():
     assert np.abs(Sh.imag).max() <= 1e-13 * scale
     assert np.abs(Sh.real - Sh.real.T).max() <= 1e-13 * scale           # (v, u) <-> (u, v), dx = dy
     assert np.abs(Sh.real - np.roll(Sh.real[::-1], 1, axis=0)).max() <= 1e-13 * scale  # v -> -v
+
+
+@pytest.mark.parametrize("name", ["tiny_32x32x48", "mid_64x64x64"])
+def test_cached_spectrum_form_equals_direct_form(name):
+    cfg = _cases()[name]
+    S = oracle.slab(cfg)
+    sp = oracle.Spectral(cfg)
+    H = inputs.gaussian((cfg["py"], cfg["px"], cfg["nz"]), 41)
+    s = inputs.gaussian((cfg["py"], cfg["px"], cfg["nt"]), 42)
+    assert rel(sp.forward(H), oracle.forward(S, H)) <= 1e-12
+    assert rel(sp.adjoint(s), oracle.adjoint(S, s)) <= 1e-12
+    # every nonzero sample of depth k lies in depth k's band
+    nz_samples = (S != 0).any(axis=(0, 1))
+    for k in range(cfg["nz"]):
+        idx = np.flatnonzero(nz_samples[k])
+        assert idx.size == 0 or (sp.klo[k] <= idx[0] and idx[-1] < sp.klo[k] + sp.klen[k])
+
+
+@pytest.mark.parametrize("shape", [(5, 4, 16, 9, 13), (3, 3, 12, 6, 5)])
+def test_cached_spectrum_form_on_a_slab_without_symmetry(shape):
+    """A random slab has a complex, non-Hermitian-in-(v) spectrum: a missing
+    conjugate, a wrong Hermitian completion or a dropped column fails here."""
+    win, nz, nt, py, px = shape
+    rng = np.random.Generator(np.random.PCG64(sum(shape)))
+    S = rng.standard_normal((win, win, nz, nt))
+    S[:, :, :, :3] = 0.0
+    S[:, :, 1, 9:] = 0.0  # uneven bands
+    H = rng.standard_normal((py, px, nz))
+    s = rng.standard_normal((py, px, nt))
+    for pad in (None, 32):
+        sp = oracle.Spectral.from_dense(S, py, px, pad)
+        assert rel(sp.forward(H), oracle.forward(S, H)) <= 1e-12
+        assert rel(sp.adjoint(s), oracle.adjoint(S, s)) <= 1e-12
+
+
+@pytest.mark.parametrize("over", [{}, dict(dy_m=15e-6, px=40, py=24)])
+def test_cached_spectrum_symmetric_build_matches_plain_build(over):
+    """Evaluating one tap per symmetry orbit and copying it gives the same
+    spectrum as evaluating every tap (mirror orbits only when dx != dy)."""
+    cfg = configs.scaled(configs.TINY_32, **over)
+    a = oracle.Spectral(cfg)
+    b = oracle.Spectral(cfg, symmetric=True)
+    assert np.array_equal(a.klo, b.klo) and np.array_equal(a.klen, b.klen)
+    scale = np.abs(a.re).max()
+    assert np.abs(a.re - b.re).max() <= 1e-14 * scale
+    assert np.abs(a.im - b.im).max() <= 1e-14 * scale

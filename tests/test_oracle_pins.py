@@ -102,13 +102,54 @@ def test_eir_derivative_matches_difference_quotient():
 
 
 # ------------------------------------------------------------------ Eqs. 1-4
+def brute_distance_range(cfg, y0=3, x0=5):
+    """Shortest and longest voxel-patch distance over the slab window, from
+    absolute coordinates: the sensor sits over scan point (y0, x0) (focus at
+    (x0 dx, y0 dy, 0), surface points focus - F n_j), the voxels of the
+    win x win x nz window around it sit at their absolute positions."""
+    nx, ny, nz, _ = oracle.patches(cfg)
+    F = cfg["focal_m"]
+    R = (cfg["win"] - 1) // 2
+    fx, fy = x0 * cfg["dx_m"], y0 * cfg["dy_m"]
+    q = np.stack([fx - F * nx, fy - F * ny, -F * nz], 1)                  # (M, 3)
+    yy, xx, kk = np.meshgrid(np.arange(y0 - R, y0 + R + 1), np.arange(x0 - R, x0 + R + 1),
+                             np.arange(cfg["nz"]), indexing="ij")
+    v = np.stack([xx.ravel() * cfg["dx_m"], yy.ravel() * cfg["dy_m"],
+                  cfg["z0_rel_m"] + kk.ravel() * cfg["dz_m"]], 1)          # (voxels, 3)
+    d = np.sqrt(((v[:, None, :] - q[None, :, :]) ** 2).sum(-1))
+    return float(d.min()), float(d.max())
+
+
+@pytest.mark.parametrize("over", [{}, dict(win=5, nz=8, z0_rel_m=40e-6, dx_m=30e-6, dy_m=10e-6)])
+def test_distance_range_matches_brute_force(over):
+    """The oracle's distance range equals a numpy min / max over every
+    (voxel, patch) pair of the window, taken in absolute coordinates."""
+    cfg = dict(C0, **over)
+    dmin, dmax = oracle.distance_range(cfg)
+    bmin, bmax = brute_distance_range(cfg)
+    assert abs(dmin - bmin) <= 1e-15 * bmin and abs(dmax - bmax) <= 1e-15 * bmax
+    if not over:  # the tiny workload's window holds the focal voxel: dmin <= F <= dmax
+        assert dmin <= C0["focal_m"] <= dmax
+
+
 def test_time_origin_rule_and_window():
+    """Reading of the unstated time origin: the earliest arrival minus the
+    EIR half-width falls in [2, 3) samples after t0, and the window check
+    passes exactly when the latest arrival plus the half-width is below nt.
+    dmin / dmax come from the brute-force range, not from the oracle."""
     t0 = oracle.t0(C0)
-    dmin, dmax = oracle.distance_range(C0)
+    dmin, dmax = brute_distance_range(C0)
+    fs, c = C0["fs_hz"], C0["c_mps"]
     cut = 5 * GOLD["eir_sigma_samples"]["value"]
-    n_first = C0["fs_hz"] * (dmin / C0["c_mps"] - t0) - cut
+    n_first = fs * (dmin / c - t0) - cut
     assert 2.0 <= n_first < 3.0 + 1e-9
-    assert C0["fs_hz"] * (dmax / C0["c_mps"] - t0) + cut < C0["nt"]
+    assert abs(t0 * fs - round(t0 * fs)) < 1e-6          # t0 on the sample grid
+    n_last = fs * (dmax / c - t0) + cut
+    assert n_last < C0["nt"]
+    nt_edge = int(math.floor(n_last))                    # n_last >= nt_edge: rejected
+    with pytest.raises(oracle.OracleError):
+        oracle.t0(dict(C0, nt=nt_edge))
+    assert oracle.t0(dict(C0, nt=nt_edge + 1)) == t0     # t0 does not depend on nt
     with pytest.raises(oracle.OracleError):
         oracle.t0(dict(C0, nt=100))
 
