@@ -54,7 +54,17 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16x3", "fft"],
                    help="operator form: auto = split-BF16 tensor cores when built; fft = FP32 lateral-FFT form")
-    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true",
+                   help="skip the oracle leg: the timed FP64 CPU baseline and the FP64 accuracy references")
+    p.add_argument("--no-accuracy", action="store_true",
+                   help="skip the per-result error against the FP64 oracle (A, A^T, LSQR and FISTA images)")
+    p.add_argument("--serve", action="store_true",
+                   help="instead of the volume benchmark, run the served workload: Poisson arrivals at --rates, "
+                        "--requests per rate, with the small requests' images checked against the FP64 oracle")
+    p.add_argument("--rates", type=float, nargs="+", default=[2.0, 20.0])
+    p.add_argument("--requests", type=int, default=500)
+    p.add_argument("--pool", type=int, default=32)
+    p.add_argument("--slots", type=int, default=8)
     p.add_argument("--no-forms", action="store_true",
                    help="skip the short measurements of the other operator form, the band-pass filter and "
                         "the Tikhonov sweep in the default run")
@@ -186,6 +196,261 @@ def cpu_baseline_entry(flops_per_op):
             "seconds_per_volume": per_volume}
 
 
+# ---------------------------------------------------------------- oracle leg: FP64 references
+# The oracle leg runs the FP64 oracle on the host cores: the timed CPU
+# baseline above, and the FP64 references of this workload's results (A H,
+# A^T s, the LSQR and FISTA images) that every operator form is compared with.
+# The references take minutes of host time, so they run in a spawned process
+# (started before the first CUDA call) while the GPU legs are timed; the
+# CPU baseline is timed afterwards, on idle cores.
+def _reference_proc(workdir, threads):
+    os.environ["OMP_NUM_THREADS"] = str(threads)  # read when the oracle library loads
+    import numpy as np
+
+    from oracle import headline
+    from paper_2009_10173_gb300 import configs
+
+    def on_signals(s32, H32):
+        np.save(os.path.join(workdir, "s32.npy"), s32)
+        np.save(os.path.join(workdir, "H32.npy"), H32)
+        os.replace(os.path.join(workdir, "s32.npy"), os.path.join(workdir, "signals.npy"))
+
+    try:
+        r = headline.reference(configs.VOLUME_200, seed=1, n_spheres=50, snr_db=20.0, lsqr_iters=LSQR_ITERS,
+                               fista_iters=FISTA_ITERS, power_iters=POWER_ITERS, lambda_rel=LAMBDA_REL,
+                               v0_seed=7, on_signals=on_signals)
+        np.savez(os.path.join(workdir, "ref_tmp.npz"), AH=r["AH"], ATs=r["ATs"], x_l2=r["x_l2"], x_l1=r["x_l1"],
+                 L=r["L"], lam=r["lam"], seconds=json.dumps(r["seconds"]), threads=threads)
+        os.replace(os.path.join(workdir, "ref_tmp.npz"), os.path.join(workdir, "ref.npz"))
+    except Exception as e:  # reported in the bench line
+        with open(os.path.join(workdir, "error.txt"), "w") as f:
+            f.write(repr(e))
+
+
+class AccuracyLeg:
+    """FP64 references in a spawned process; device results compared at the end."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        import tempfile
+        self.dir = tempfile.mkdtemp(prefix="oam_ref_")
+        self.threads = max(1, cpu_cores() - 2)  # two cores stay with the GPU process
+        self.proc = mp.get_context("spawn").Process(target=_reference_proc, args=(self.dir, self.threads),
+                                                    daemon=True)
+        self.t0 = time.perf_counter()
+        self.proc.start()
+        self.results = {}
+
+    def _wait_for(self, name, timeout_s):
+        path = os.path.join(self.dir, name)
+        t = time.perf_counter()
+        while not os.path.exists(path):
+            if os.path.exists(os.path.join(self.dir, "error.txt")) or not self.proc.is_alive() and \
+                    not os.path.exists(path):
+                return None
+            if time.perf_counter() - t > timeout_s:
+                return None
+            time.sleep(0.5)
+        return path
+
+    def run_device(self, forms, make_model):
+        """Device results of each form on the oracle's signals (FP32 in, FP32 out)."""
+        import numpy as np
+        import torch
+        if self._wait_for("signals.npy", 1800) is None:
+            return
+        s32 = np.load(os.path.join(self.dir, "signals.npy"))
+        H32 = np.load(os.path.join(self.dir, "H32.npy"))
+        s = torch.from_numpy(s32).cuda()
+        H = torch.from_numpy(H32).cuda()
+        from paper_2009_10173_gb300 import inputs
+        v0 = torch.from_numpy(inputs.gaussian(H32.shape, 7).astype(np.float32)).cuda()
+        for name, prec in forms:
+            m = make_model(prec)
+            out = {"A": m.forward(H).cpu().numpy(), "AT": m.adjoint(s).cpu().numpy()}
+            x2, _ = m.lsqr(s, LSQR_ITERS)
+            out["lsqr_image"] = x2.cpu().numpy()
+            x1, inf = m.fista(s, FISTA_ITERS, power_iters=POWER_ITERS, lambda_rel=LAMBDA_REL, nonneg=True, v0=v0)
+            out["fista_image"] = x1.cpu().numpy()
+            out["L"], out["lambda"] = inf.L, inf.lambda_
+            m.close()
+            self.results[name] = out
+
+    def finish(self):
+        import numpy as np
+        path = self._wait_for("ref.npz", 3600)
+        self.proc.join(timeout=60)
+        if path is None:
+            err = "reference process failed"
+            ep = os.path.join(self.dir, "error.txt")
+            if os.path.exists(ep):
+                err = open(ep).read().strip()
+            return {"error": err}
+        ref = np.load(path)
+
+        def rel(a, b):
+            a = np.asarray(a, np.float64)
+            return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+        out = {"reference": "FP64 oracle (lateral-FFT restatement with the slab spectrum computed once, pinned to "
+                            "the direct form at 1e-12) on the host cores, same seeded FP32 signals",
+               "oracle_threads": int(ref["threads"]), "oracle_seconds": json.loads(str(ref["seconds"])),
+               "wall_s": time.perf_counter() - self.t0, "tolerance": {"A, A^T fp32/fft": 1e-5,
+                                                                       "A, A^T bf16x3": 1e-4, "images": 1e-3}}
+        for name, r in self.results.items():
+            out[name] = {"A": rel(r["A"], ref["AH"]), "AT": rel(r["AT"], ref["ATs"]),
+                         "lsqr_image": rel(r["lsqr_image"], ref["x_l2"]),
+                         "fista_image": rel(r["fista_image"], ref["x_l1"]),
+                         "L": abs(r["L"] - float(ref["L"])) / float(ref["L"]),
+                         "lambda": abs(r["lambda"] - float(ref["lam"])) / float(ref["lam"])}
+        import shutil
+        shutil.rmtree(self.dir, ignore_errors=True)
+        return out
+
+
+# ---------------------------------------------------------------- served workload
+SERVE_ITERS = (30, 50, 20)  # LSQR, FISTA, power iterations per served request
+
+
+def _serve_reference_proc(workdir, threads, cfgs):
+    """Oracle leg of the served workload: for each small prepared request, the
+    signals (FP64 oracle's A on the request's phantom, 20 dB noise) and its
+    FP64 LSQR and FISTA images."""
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    import numpy as np
+
+    import oracle
+    from oracle import solvers
+    from paper_2009_10173_gb300 import configs, inputs
+    try:
+        sps = {}
+        for j, cfg in cfgs:
+            while True:  # the same sample-count fallback as the library's window check
+                try:
+                    oracle.t0(cfg)
+                    break
+                except oracle.OracleError:
+                    cfg = configs.next_nt(cfg)
+                    if cfg is None:
+                        raise
+            sp = oracle.Spectral(cfg, symmetric=True)
+            H = inputs.phantom(cfg, cfg.get("seed", 0), kind="vessels", count=10)
+            s32 = inputs.add_noise(sp.forward(H.astype(np.float32).astype(np.float64)), 20.0,
+                                   cfg.get("seed", 0) + 10 ** 6).astype(np.float32)
+            np.save(os.path.join(workdir, f"sig{j}_tmp.npy"), s32)
+            os.replace(os.path.join(workdir, f"sig{j}_tmp.npy"), os.path.join(workdir, f"sig{j}.npy"))
+            with open(os.path.join(workdir, f"nt{j}.txt"), "w") as f:
+                f.write(str(cfg["nt"]))
+            sps[j] = (sp, s32)
+        for j, (sp, s32) in sps.items():
+            sd = s32.astype(np.float64)
+            x2, _ = solvers.lsqr(sp.forward, sp.adjoint, sd, SERVE_ITERS[0])
+            x1, _ = solvers.mb_l1(sp.forward, sp.adjoint, sd, SERVE_ITERS[1], SERVE_ITERS[2],
+                                  np.ones(x2.shape), lambda_rel=LAMBDA_REL, nonneg=True)
+            np.savez(os.path.join(workdir, f"ref{j}_tmp.npz"), x2=x2, x1=x1)
+            os.replace(os.path.join(workdir, f"ref{j}_tmp.npz"), os.path.join(workdir, f"ref{j}.npz"))
+    except Exception as e:
+        with open(os.path.join(workdir, "error.txt"), "w") as f:
+            f.write(repr(e))
+
+
+def run_serve(args):
+    """Served workload: requests drawn from a pool of prepared
+    instances (sizes as the batched workload plus occasional 200x200x300
+    volumes), submitted at Poisson arrival times to one request server with a
+    150 GB device-memory budget.  Requests on small instances (64x64 scans,
+    <= 192 depths) carry signals made by the FP64 oracle and every one of
+    them is compared with the oracle's FP64 LSQR and FISTA images."""
+    import multiprocessing as mp
+    import tempfile
+
+    import numpy as np
+
+    from paper_2009_10173_gb300 import configs
+    cfgs = [configs.served_request(2000 + j) for j in range(args.pool)]
+    from paper_2009_10173_gb300.serve import is_small
+    small = [(j, c) for j, c in enumerate(cfgs) if is_small(c)]
+    workdir = tempfile.mkdtemp(prefix="oam_serve_ref_")
+    proc = None
+    if small and not args.no_cpu_baseline:
+        proc = mp.get_context("spawn").Process(target=_serve_reference_proc,
+                                               args=(workdir, max(1, cpu_cores() - 2), small), daemon=True)
+        proc.start()
+
+    import torch
+
+    from paper_2009_10173_gb300 import binding as B
+    from paper_2009_10173_gb300 import serve
+    torch.cuda.set_device(0)
+    prec = {"auto": B.OAM_PREC_BF16X3, "bf16x3": B.OAM_PREC_BF16X3, "fft": B.OAM_PREC_FFT,
+            "fp32": B.OAM_PREC_FP32}[args.prec]
+
+    def wait_file(name, timeout_s=3600):
+        t = time.perf_counter()
+        path = os.path.join(workdir, name)
+        while not os.path.exists(path):
+            if os.path.exists(os.path.join(workdir, "error.txt")) or time.perf_counter() - t > timeout_s or \
+                    (proc is not None and not proc.is_alive() and not os.path.exists(path)):
+                return None
+            time.sleep(0.5)
+        return path
+
+    pool, checked_pool = [], set()
+    for j, cfg in enumerate(cfgs):
+        sig = None
+        if proc is not None and is_small(cfg):
+            pth = wait_file(f"sig{j}.npy")
+            final = serve.final_config(cfg, prec)
+            if pth is not None and open(os.path.join(workdir, f"nt{j}.txt")).read().strip() == str(final["nt"]):
+                sig = np.load(pth)
+                checked_pool.add(j)
+        pool.append(serve.Instance(cfg, prec, signals=sig))
+
+    refs = {}
+
+    def check(j, x2, x1):
+        if j not in checked_pool:
+            return None
+        if j not in refs:
+            pth = wait_file(f"ref{j}.npz")
+            if pth is None:
+                return None
+            refs[j] = np.load(pth)
+        r = refs[j]
+
+        def rel(a, b):
+            a = np.asarray(a, np.float64)
+            return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+        return {"rel_err_lsqr": rel(x2.numpy(), r["x2"]), "rel_err_fista": rel(x1.numpy(), r["x1"])}
+
+    results = []
+    for k, rate in enumerate(args.rates):
+        server = serve.make_server(150e9, args.slots, precision=prec, lsqr_iters=SERVE_ITERS[0],
+                                   fista_iters=SERVE_ITERS[1], power_iters=SERVE_ITERS[2], lambda_rel=LAMBDA_REL)
+        res, _ = serve.run_rate(server, pool, rate, args.requests, seed=3000 + k, check=check)
+        B.oam_server_stop(server)
+        results.append(res)
+    err = None
+    if os.path.exists(os.path.join(workdir, "error.txt")):
+        err = open(os.path.join(workdir, "error.txt")).read().strip()
+    import shutil
+    shutil.rmtree(workdir, ignore_errors=True)
+    line = {"metric": "served reconstructions: volumes/s and p50/p99 latency", "unit": "volumes/s",
+            "value": max(r["volumes_per_s"] for r in results), "n_gpus": 1, "higher_is_better": True,
+            "dtype": "bf16" if prec == B.OAM_PREC_BF16X3 else "f32", "data": "synthetic",
+            "config": {"workload": "served: Poisson arrivals, sizes as the batched workload (scan 64-256^2, "
+                                   "128-384 depths, 512-1024 samples, seeded sensors) plus 5 % 200x200x300 "
+                                   "volumes; 30 LSQR + 50 FISTA (+20 power) each",
+                       "pool_instances": args.pool, "slots": args.slots, "budget_gb": 150,
+                       "oracle_checked_instances": sorted(checked_pool),
+                       "check": "every request on a small instance (64x64 scan, <= 192 depths) against the "
+                                "FP64 oracle's LSQR and FISTA images of the same oracle-made signals"},
+            "rates": results}
+    if err:
+        line["oracle_error"] = err
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank):
     if rank != 0:
@@ -233,7 +498,7 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- our arm
-def run_ours(args, rank, world):
+def run_ours(args, rank, world, acc=None):
     import numpy as np
     import torch
 
@@ -488,6 +753,12 @@ def run_ours(args, rank, world):
         line["forms"] = {"lateral_fft": other_form(B.OAM_PREC_FFT)}
     if world == 1 and not args.no_forms:
         line["extensions"] = extensions()
+    if acc is not None:
+        forms = [("bf16x3", B.OAM_PREC_BF16X3), ("fft", B.OAM_PREC_FFT), ("fp32", B.OAM_PREC_FP32)]
+        if prec != B.OAM_PREC_BF16X3:
+            forms = [f for f in forms if f[1] != B.OAM_PREC_BF16X3]
+        acc.run_device(forms, make_model)
+        line["accuracy_vs_fp64"] = acc.finish()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_entry(info.flops_per_op)
     print(json.dumps(line), flush=True)
@@ -500,12 +771,18 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
+    if args.serve:
+        if rank == 0:
+            run_serve(args)
+        return
+    # the oracle leg's references start before the first CUDA call (spawned process)
+    acc = AccuracyLeg() if world == 1 and not args.no_cpu_baseline and not args.no_accuracy else None
     if world > 1:
         import torch
         import torch.distributed as tdist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         tdist.init_process_group("nccl")
-    run_ours(args, rank, world)
+    run_ours(args, rank, world, acc)
     if world > 1:
         import torch.distributed as tdist
         tdist.destroy_process_group()

@@ -23,15 +23,36 @@ from . import configs, inputs
 from .batch import build_model
 
 
-class Instance:
-    """A prepared request: configuration, pinned host signals and image buffers."""
+def is_small(cfg):
+    """Requests whose FP64 reference a host can compute in well under a minute
+    (64 x 64 scans with at most 192 depths)."""
+    return cfg["py"] <= 64 and cfg["px"] <= 64 and cfg["nz"] <= 192
 
-    def __init__(self, cfg, precision):
+
+def final_config(cfg, precision):
+    """The request's configuration after the sample-count fallback of build_model."""
+    cfg, m = build_model(cfg, precision)
+    m.close()
+    return cfg
+
+
+class Instance:
+    """A prepared request: configuration, pinned host signals and image buffers.
+
+    The noisy signals are seeded noise (20 dB) on clean signals A H of the
+    request's vessel phantom; A is the library's FP32 operator unless the
+    caller passes the noisy signals (``signals``, e.g. made by a reference
+    implementation for requests whose results it checks)."""
+
+    def __init__(self, cfg, precision, signals=None):
         cfg, m = build_model(cfg, precision)
-        H = inputs.phantom(cfg, cfg.get("seed", 0), kind="vessels", count=10)
-        clean = m.forward(torch.from_numpy(H.astype(np.float32)).cuda()).cpu().numpy()
+        if signals is None:
+            H = inputs.phantom(cfg, cfg.get("seed", 0), kind="vessels", count=10)
+            clean = m.forward(torch.from_numpy(H.astype(np.float32)).cuda()).cpu().numpy()
+            noisy = inputs.add_noise(clean, 20.0, cfg.get("seed", 0) + 10 ** 6).astype(np.float32)
+        else:
+            noisy = np.ascontiguousarray(signals, np.float32)
         m.close()
-        noisy = inputs.add_noise(clean, 20.0, cfg.get("seed", 0) + 10 ** 6).astype(np.float32)
         self.cfg = cfg
         self.structs = B.structs_from_config(cfg)
         self.h_s = torch.from_numpy(noisy).pin_memory()
@@ -49,8 +70,12 @@ def make_server(budget_bytes=150 * 10 ** 9, slots=8, precision=B.OAM_PREC_BF16X3
     return B.oam_server_create(opts)
 
 
-def run_rate(server, pool, rate, n_requests, seed, timeout_s=3600.0):
-    """Submit n_requests at Poisson arrival times (rate per second), wait for all."""
+def run_rate(server, pool, rate, n_requests, seed, timeout_s=3600.0, check=None):
+    """Submit n_requests at Poisson arrival times (rate per second), wait for all.
+
+    ``check(index_in_pool, x_l2, x_l1)``, if given, is called for every
+    completed request; it returns None (not checked) or a dict of errors,
+    which are summarised in the result."""
     rng = np.random.Generator(np.random.PCG64(seed))
     gaps = rng.exponential(1.0 / rate, n_requests)
     picks = rng.integers(0, len(pool), n_requests)
@@ -66,22 +91,32 @@ def run_rate(server, pool, rate, n_requests, seed, timeout_s=3600.0):
         x2, x1 = inst.new_outputs()
         s, g, e = inst.structs
         rid = B.oam_server_submit(server, s, g, e, inst.h_s, x2, x1)
-        keep.append((rid, inst, x2, x1))
-    lat, failed = [], 0
-    for rid, inst, x2, x1 in keep:
+        keep.append((rid, int(picks[i]), x2, x1))
+    t_last_submit = time.perf_counter() - t0
+    lat, failed, done = [], 0, []
+    for rid, pick, x2, x1 in keep:
         rc = B.oam_server_wait(server, rid, timeout_s)
         info = B.oam_server_poll(server, rid)
         if rc != B.OAM_OK or info.state != 2:
             failed += 1
         else:
             lat.append(info.latency_s)
+            done.append((pick, x2, x1))
     makespan = time.perf_counter() - t0
     stats = B.oam_server_stats(server)
-    return {"rate_offered_per_s": rate, "requests": n_requests, "completed": len(lat), "failed": failed,
-            "makespan_s": makespan, "volumes_per_s": len(lat) / makespan,
-            "p50_latency_s": float(np.percentile(lat, 50)) if lat else None,
-            "p99_latency_s": float(np.percentile(lat, 99)) if lat else None,
-            "peak_running": stats.peak_running, "peak_reserved_gb": stats.peak_reserved_bytes / 1e9}, keep
+    out = {"rate_offered_per_s": rate, "rate_achieved_submit_per_s": n_requests / t_last_submit,
+           "requests": n_requests, "completed": len(lat), "failed": failed, "makespan_s": makespan,
+           "volumes_per_s": len(lat) / makespan,
+           "p50_latency_s": float(np.percentile(lat, 50)) if lat else None,
+           "p99_latency_s": float(np.percentile(lat, 99)) if lat else None,
+           "peak_running": stats.peak_running, "peak_reserved_gb": stats.peak_reserved_bytes / 1e9}
+    if check is not None:
+        errs = [e for e in (check(p, x2, x1) for p, x2, x1 in done) if e is not None]
+        out["checked"] = len(errs)
+        if errs:
+            for key in errs[0]:
+                out[f"max_{key}"] = max(float(e[key]) for e in errs)
+    return out, keep
 
 
 def main():
