@@ -737,19 +737,28 @@ constexpr int kMaxDevices = 64;
 void *g_static_ptr[kMaxDevices] = {};
 std::mutex g_static_mu;
 
-// Device address of g_static_work on the current device (looked up once per device).
-oam_status static_work_ptr(void **out) {
+// Device address of g_static_work in the current device's context.  Outside
+// stream capture it is looked up on every call (cudaGetSymbolAddress, no
+// allocation), so a context that was torn down and created again never gets
+// a stale address; during capture the address from the last uncaptured call
+// on this device is used, so the first call on a device must come before any
+// capture (OAM_ERR_INVALID_ARG otherwise).
+oam_status static_work_ptr(cudaStream_t st, void **out) {
   int dev = 0;
   OAM_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return OAM_ERR_UNSUPPORTED;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  OAM_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_static_work) != cudaSuccess || !p) {
       cudaGetLastError();
       return OAM_ERR_CUDA;
     }
     g_static_ptr[dev] = p;
+  } else if (!g_static_ptr[dev]) {
+    return OAM_ERR_INVALID_ARG;
   }
   *out = g_static_ptr[dev];
   return OAM_OK;
@@ -763,7 +772,7 @@ extern "C" oam_status oam_lsqr_noalloc(const oam_model *m, const float *d_s, flo
   const size_t need = layout(m).total(0);
   if (need > kStaticWorkBytes) return OAM_ERR_INVALID_ARG;
   void *work = nullptr;
-  oam_status rc = static_work_ptr(&work);
+  oam_status rc = static_work_ptr(as_stream(stream), &work);
   if (rc) return rc;
   return oam_lsqr(m, d_s, d_x, opts, info, work, kStaticWorkBytes, stream);
 }
