@@ -10,6 +10,11 @@
 //   of the shifted volume row and the packed slab rows in shared memory.
 // adjoint: block = (row y, 64 positions, 16-depth tile); it walks every tap and
 //   the samples of the tile's band union, 64 samples at a time.
+//
+// Each output sums up to win^2 x band products (about 3e5 at 61 x 61 taps).
+// One FP32 accumulator for all of them loses about sqrt(n) units in the last
+// place, 2e-5 relative at that size, so both kernels sum in three levels: the
+// products of one tap, then the taps of one tap row, then the rows.
 #include "internal.cuh"
 
 using namespace oam;
@@ -27,16 +32,24 @@ __global__ void __launch_bounds__(256) k_fwd_fp32(const float *__restrict__ H, f
   const int W = 2 * R + 1;
   __shared__ float Hs[kPos][kDepthTile + 1];
   __shared__ float4 Ps[kDepthTile][kTimeTile / 4];
-  float acc[4][4] = {};
+  float acc[4][4] = {}, row_acc[4][4], tap_acc[4][4];
   for (int b = -R; b <= R; ++b) {
     const int yy = y + b;
     if (yy < 0 || yy >= py) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) row_acc[i][j] = 0.0f;
     for (int a = -R; a <= R; ++a) {
       const int xs = x0 + a;
       if (xs + kPos <= 0 || xs >= px) continue;
       const int oi = tap_orbit[(b + R) * W + (a + R)] * n_tt + T;
       const int klo = krange[2 * oi], khi = krange[2 * oi + 1];
       if (klo >= khi) continue;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tap_acc[i][j] = 0.0f;
       const float4 *P4 = reinterpret_cast<const float4 *>(P + off[oi]);
       for (int kc = klo; kc < khi; kc += kDepthTile) {
 #pragma unroll
@@ -57,15 +70,23 @@ __global__ void __launch_bounds__(256) k_fwd_fp32(const float *__restrict__ H, f
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const float h = Hs[4 * ty + i][kk];
-            acc[i][0] = fmaf(h, p.x, acc[i][0]);
-            acc[i][1] = fmaf(h, p.y, acc[i][1]);
-            acc[i][2] = fmaf(h, p.z, acc[i][2]);
-            acc[i][3] = fmaf(h, p.w, acc[i][3]);
+            tap_acc[i][0] = fmaf(h, p.x, tap_acc[i][0]);
+            tap_acc[i][1] = fmaf(h, p.y, tap_acc[i][1]);
+            tap_acc[i][2] = fmaf(h, p.z, tap_acc[i][2]);
+            tap_acc[i][3] = fmaf(h, p.w, tap_acc[i][3]);
           }
         }
         __syncthreads();
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) row_acc[i][j] += tap_acc[i][j];
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += row_acc[i][j];
   }
   const int n = T * kTimeTile + 4 * tx;
   if (n >= nt) return;
@@ -87,16 +108,20 @@ __global__ void __launch_bounds__(256) k_adj_fp32(const float *__restrict__ s, f
   const int W = 2 * R + 1;
   __shared__ float4 Ss[kPos][kTimeTile / 4 + 1];
   __shared__ float4 Qs[kDepthTile][kTimeTile / 4];
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float acc[4] = {0.f, 0.f, 0.f, 0.f}, row_acc[4], tap_acc[4];
   for (int b = -R; b <= R; ++b) {
     const int yy = y - b;
     if (yy < 0 || yy >= py) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) row_acc[i] = 0.0f;
     for (int a = -R; a <= R; ++a) {
       const int xs = x0 - a;
       if (xs + kPos <= 0 || xs >= px) continue;
       const int oi = tap_orbit[(b + R) * W + (a + R)] * n_kt + K;
       const int nlo = nrange[2 * oi], nlen = nrange[2 * oi + 1];
       if (nlen <= 0) continue;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) tap_acc[i] = 0.0f;
       const float4 *Q4 = reinterpret_cast<const float4 *>(Q + off[oi]);
       for (int nc = 0; nc < nlen; nc += kTimeTile) {
 #pragma unroll
@@ -118,15 +143,19 @@ __global__ void __launch_bounds__(256) k_adj_fp32(const float *__restrict__ s, f
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const float4 q = Qs[4 * kq + i][j4];
-            acc[i] = fmaf(v.x, q.x, acc[i]);
-            acc[i] = fmaf(v.y, q.y, acc[i]);
-            acc[i] = fmaf(v.z, q.z, acc[i]);
-            acc[i] = fmaf(v.w, q.w, acc[i]);
+            tap_acc[i] = fmaf(v.x, q.x, tap_acc[i]);
+            tap_acc[i] = fmaf(v.y, q.y, tap_acc[i]);
+            tap_acc[i] = fmaf(v.z, q.z, tap_acc[i]);
+            tap_acc[i] = fmaf(v.w, q.w, tap_acc[i]);
           }
         }
         __syncthreads();
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) row_acc[i] += tap_acc[i];
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] += row_acc[i];
   }
   const int x = x0 + p;
   if (x >= px) return;

@@ -23,12 +23,29 @@ extern "C" oam_status oam_model_autotune(oam_model *m, int32_t reps, void *strea
                                          int32_t *ring_adjoint) {
   if (!m || reps < 1) return OAM_ERR_INVALID_ARG;
   if (m->precision != OAM_PREC_BF16X3) return OAM_OK;  // nothing to tune on the FP32 path
-  int f = 0, a = 0;
-  oam_status rc = tc_autotune(m, reps, as_stream(stream), &f, &a);
+  int f = 0, a = 0, wf = 0, wa = 0;
+  oam_status rc = tc_autotune(m, reps, as_stream(stream), &f, &a, &wf, &wa);
   if (rc) return rc;
   if (ring_forward) *ring_forward = f;
   if (ring_adjoint) *ring_adjoint = a;
   return OAM_OK;
+}
+
+extern "C" oam_status oam_model_get_tiles(const oam_model *m, int32_t direction, int32_t *fold_warps,
+                                          int32_t *ring) {
+  if (!m || (direction != 0 && direction != 1) || !fold_warps || !ring) return OAM_ERR_INVALID_ARG;
+  if (m->precision != OAM_PREC_BF16X3) return OAM_ERR_UNSUPPORTED;
+  int w = 0, r = 0;
+  tc_get_tiles(m, direction, &w, &r);
+  *fold_warps = w;
+  *ring = r;
+  return OAM_OK;
+}
+
+extern "C" oam_status oam_model_set_tiles(oam_model *m, int32_t direction, int32_t fold_warps, int32_t ring) {
+  if (!m || (direction != 0 && direction != 1)) return OAM_ERR_INVALID_ARG;
+  if (m->precision != OAM_PREC_BF16X3) return OAM_ERR_UNSUPPORTED;
+  return tc_set_tiles(m, direction, fold_warps, ring);
 }
 
 // ---------------------------------------------------------------- batch
@@ -72,23 +89,58 @@ void batch_destroy(oam_batch *b) {
   delete b;
 }
 
-// Record every job (LSQR, then FISTA) on its own branch of one graph.
+// Do two jobs touch the same model-owned buffers or overlapping workspaces?
+// A model's internal staging buffers serve one stream at a time, so such
+// jobs must run one after the other.
+bool jobs_conflict(const oam_batch::Job &x, const oam_batch::Job &y) {
+  if (x.model == y.model) return true;
+  const uintptr_t x0 = reinterpret_cast<uintptr_t>(x.work), y0 = reinterpret_cast<uintptr_t>(y.work);
+  return x0 < y0 + y.work_bytes && y0 < x0 + x.work_bytes;
+}
+
+// Branch of each job: jobs that conflict (directly or through other jobs)
+// share the branch of the first of them and run in job order; all others get
+// their own branch.
+std::vector<int> batch_branches(const oam_batch *b) {
+  const int n = (int)b->jobs.size();
+  std::vector<int> br(n);
+  for (int j = 0; j < n; ++j) br[j] = j;
+  for (bool changed = true; changed;) {  // connected components, smallest index as label
+    changed = false;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j)
+        if (br[j] != br[i] && jobs_conflict(b->jobs[i], b->jobs[j])) {
+          const int lo = std::min(br[i], br[j]);
+          br[i] = br[j] = lo;
+          changed = true;
+        }
+  }
+  return br;
+}
+
+// Record every job (LSQR, then FISTA) on its branch of one graph.
 oam_status batch_capture(oam_batch *b) {
   batch_release_graph(b);
+  const std::vector<int> br = batch_branches(b);
   OAM_CUDA_TRY(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed));
   oam_status rc = OAM_OK;
   if (cudaEventRecord(b->fork, b->origin) != cudaSuccess) rc = OAM_ERR_CUDA;
-  for (size_t j = 0; j < b->jobs.size() && !rc; ++j) {
-    const oam_batch::Job &J = b->jobs[j];
-    cudaStream_t st = b->streams[j];
+  for (size_t g = 0; g < b->jobs.size() && !rc; ++g) {
+    if (br[g] != (int)g) continue;  // not the first job of a branch
+    cudaStream_t st = b->streams[g];
     if (cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess) {
       rc = OAM_ERR_CUDA;
       break;
     }
-    if (J.lsqr.iters > 0) rc = oam_lsqr(J.model, J.s, J.x_l2, &J.lsqr, nullptr, J.work, J.work_bytes, st);
-    if (!rc && J.fista.iters > 0) rc = oam_l1_fista(J.model, J.s, J.x_l1, &J.fista, nullptr, J.work, J.work_bytes, st);
-    if (!rc && cudaEventRecord(b->joins[j], st) != cudaSuccess) rc = OAM_ERR_CUDA;
-    if (!rc && cudaStreamWaitEvent(b->origin, b->joins[j], 0) != cudaSuccess) rc = OAM_ERR_CUDA;
+    for (size_t j = g; j < b->jobs.size() && !rc; ++j) {
+      if (br[j] != (int)g) continue;
+      const oam_batch::Job &J = b->jobs[j];
+      if (J.lsqr.iters > 0) rc = oam_lsqr(J.model, J.s, J.x_l2, &J.lsqr, nullptr, J.work, J.work_bytes, st);
+      if (!rc && J.fista.iters > 0)
+        rc = oam_l1_fista(J.model, J.s, J.x_l1, &J.fista, nullptr, J.work, J.work_bytes, st);
+    }
+    if (!rc && cudaEventRecord(b->joins[g], st) != cudaSuccess) rc = OAM_ERR_CUDA;
+    if (!rc && cudaStreamWaitEvent(b->origin, b->joins[g], 0) != cudaSuccess) rc = OAM_ERR_CUDA;
   }
   cudaGraph_t g = nullptr;
   const cudaError_t end = cudaStreamEndCapture(b->origin, &g);

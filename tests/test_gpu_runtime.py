@@ -1,13 +1,16 @@
 """Batched and served reconstructions on the GPU (through the C ABI).
 
 * A batch of uneven jobs in one CUDA-graph launch gives exactly the images of
-  each job run on its own (the kernels are deterministic), and one small job
-  agrees with the FP64 oracle's LSQR and FISTA.
+  each job run on its own (the kernels are deterministic), also when jobs
+  share a model, and one small job agrees with the FP64 oracle's LSQR and
+  FISTA.
 * The request server returns, for every request in a mix of concurrent
-  requests, exactly the images of the same request served alone; it respects
-  its device-memory budget, reports invalid requests as failed without
-  disturbing the others, and its bounded waits time out.
-* The ring-depth autotuner keeps results unchanged.
+  requests, exactly the images of the same request served alone, and served
+  requests agree with the oracle's images; it respects its device-memory
+  budget, reports invalid requests as failed without disturbing the others,
+  and its bounded waits time out.
+* The autotuner's tile shapes (fold warps, ring depth) keep results unchanged
+  to the bit.
 """
 import numpy as np
 import pytest
@@ -69,6 +72,40 @@ def test_batch_graph_equals_standalone_runs(prec):
     batch.close()
 
 
+@pytest.mark.parametrize("prec", [B.OAM_PREC_BF16X3, B.OAM_PREC_FFT])
+def test_batch_jobs_sharing_a_model_run_in_order(prec):
+    """Two jobs on one model (its staging buffers serve one stream at a time)
+    and a third on its own: the batch serialises the two on one branch, so
+    every image equals the job run alone."""
+    cfg = JOBS[0]
+    m = Model(cfg, precision=prec)
+    other = Model(JOBS[1], precision=prec)
+    sigs = [signals_for(cfg, m), signals_for(configs.scaled(cfg, seed=31), m), signals_for(JOBS[1], other)]
+    models = [m, m, other]
+    cfgs = [cfg, cfg, JOBS[1]]
+    ref = [standalone(c, mm, s) for c, mm, s in zip(cfgs, models, sigs)]
+    h = B.oam_batch_create(3)
+    outs = []
+    for j, (c, mm, s) in enumerate(zip(cfgs, models, sigs)):
+        x2, x1 = mm.empty_volume(), mm.empty_volume()
+        nbytes = max(B.oam_solver_work_bytes(mm.handle, 0), B.oam_solver_work_bytes(mm.handle, 1))
+        raw = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        work = raw[(-raw.data_ptr()) % 256:][:nbytes]
+        B.oam_batch_set_job(h, j, mm.handle, s, x2, x1, B.OamLsqrOpts(c["lsqr_iters"], 0.0),
+                            B.OamFistaOpts(c["fista_iters"], c["power_iters"], 1, 0, -1.0, c["lambda_rel"], 0.0,
+                                           None), work)
+        outs.append((x2, x1, raw))
+    for _ in range(2):
+        B.oam_batch_run(h)
+        torch.cuda.synchronize()
+        for (x2, x1, _), (r2, r1) in zip(outs, ref):
+            assert np.array_equal(x2.cpu().numpy(), r2)
+            assert np.array_equal(x1.cpu().numpy(), r1)
+    B.oam_batch_free(h)
+    m.close()
+    other.close()
+
+
 def test_batch_job_matches_oracle():
     cfg = dict(JOBS[0])
     S = oracle.slab(cfg)
@@ -92,11 +129,40 @@ def test_autotune_keeps_results():
     cfg = JOBS[1]
     m = Model(cfg, precision=B.OAM_PREC_BF16X3)
     H = torch.from_numpy(inputs.gaussian(m.vol_shape, 5).astype(np.float32)).cuda()
-    before = m.forward(H).cpu().numpy()
+    s = torch.from_numpy(inputs.gaussian(m.sig_shape, 6).astype(np.float32)).cuda()
+    before, before_t = m.forward(H).cpu().numpy(), m.adjoint(s).cpu().numpy()
     f, a = B.oam_model_autotune(m.handle, 2)
     assert f >= 2 and a >= 2
-    after = m.forward(H).cpu().numpy()
-    assert np.array_equal(before, after)
+    for d, ring in ((0, f), (1, a)):
+        w, r = B.oam_model_get_tiles(m.handle, d)
+        assert w in (4, 8, 16) and r == ring
+    assert np.array_equal(before, m.forward(H).cpu().numpy())
+    assert np.array_equal(before_t, m.adjoint(s).cpu().numpy())
+    m.close()
+
+
+@pytest.mark.parametrize("name", ["job", "ragged"])
+def test_every_tile_shape_gives_the_same_bits(name):
+    """Fold-warp count and ring depth change how the work is spread over the
+    block, not the order of any sum: results are bit-identical."""
+    cfg = JOBS[2] if name == "job" else configs.scaled(configs.TINY_32, px=70, py=37, nz=52, nt=200, win=15,
+                                                        n_patches=800, dz_m=8e-6, z0_rel_m=-200e-6)
+    m = Model(cfg, precision=B.OAM_PREC_BF16X3)
+    H = torch.from_numpy(inputs.gaussian(m.vol_shape, 15).astype(np.float32)).cuda()
+    s = torch.from_numpy(inputs.gaussian(m.sig_shape, 16).astype(np.float32)).cuda()
+    ref_f, ref_a = None, None
+    for w in (4, 8, 16):
+        for ring in (0, 2, 3):
+            for d in (0, 1):
+                B.oam_model_set_tiles(m.handle, d, w, ring)
+                assert B.oam_model_get_tiles(m.handle, d)[0] == w
+            f, a = m.forward(H).cpu().numpy(), m.adjoint(s).cpu().numpy()
+            if ref_f is None:
+                ref_f, ref_a = f, a
+            assert np.array_equal(f, ref_f) and np.array_equal(a, ref_a), (w, ring)
+    with pytest.raises(B.OamError):
+        B.oam_model_set_tiles(m.handle, 0, 6, 0)
+    assert B.oam_model_get_tiles(m.handle, 0)[0] == 16  # a refused shape changes nothing
     m.close()
 
 
@@ -188,3 +254,28 @@ def test_server_with_fft_form_models_matches_standalone():
         m.close()
         assert np.array_equal(x2.numpy(), ref2)
         assert np.array_equal(x1.numpy(), ref1)
+
+
+@pytest.mark.parametrize("prec", [B.OAM_PREC_BF16X3, B.OAM_PREC_FFT])
+def test_served_requests_match_oracle(prec):
+    """Two requests served together (split-BF16 or lateral-FFT models) give
+    the FP64 oracle's LSQR (MB-L2) and FISTA (MB-L1) images of the same
+    signals, made by the oracle's A, within the image tolerance."""
+    reqs, refs = [], []
+    for cfg in (JOBS[0], JOBS[1]):
+        S = oracle.slab(cfg)
+        H = inputs.phantom(cfg, cfg["seed"], count=4)
+        s32 = inputs.add_noise(oracle.forward(S, H), 20.0, cfg["seed"] + 10 ** 6).astype(np.float32)
+        s64 = s32.astype(np.float64)
+        A, AT = (lambda v, S=S: oracle.forward(S, v)), (lambda v, S=S: oracle.adjoint(S, v))
+        x2, _ = solvers.lsqr(A, AT, s64, cfg["lsqr_iters"])
+        x1, _ = solvers.mb_l1(A, AT, s64, cfg["fista_iters"], cfg["power_iters"], np.ones(H.shape),
+                              lambda_rel=cfg["lambda_rel"], nonneg=True)
+        reqs.append((cfg, torch.from_numpy(s32).pin_memory()))
+        refs.append((x2, x1))
+    srv = _server(slots=2, prec=prec)
+    outs = _serve(srv, reqs)
+    B.oam_server_stop(srv)
+    for (rid, x2, x1), (r2, r1) in zip(outs, refs):
+        assert rel(x2.numpy(), r2) < 1e-3
+        assert rel(x1.numpy(), r1) < 1e-3
