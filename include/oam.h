@@ -233,9 +233,13 @@ oam_status oam_l1_fista(const oam_model *model, const float *d_s, float *d_x, co
  * is a 32 MiB array in this library's static device memory (every GPU that
  * loads the library holds it until the process exits), so problems whose
  * oam_solver_work_bytes(model, 0) exceeds 32 MiB are rejected with
- * OAM_ERR_INVALID_ARG.  The first call on each device looks the array's
- * device address up (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every call on a device shares the one array, which keeps
+ * OAM_ERR_INVALID_ARG.  Each call outside stream capture looks the array's
+ * device address up in the current context (cudaGetSymbolAddress, which does
+ * not allocate); a call made while `stream` is capturing reuses the address
+ * of the last uncaptured call on that device, so the first call on a device
+ * must come before any capture (else OAM_ERR_INVALID_ARG), and a context that
+ * is reset must see an uncaptured call again before the next capture.
+ * Every call on a device shares the one array, which keeps
  * the previous call's contents (each call initialises what it reads); calls
  * that overlap on the GPU race and give wrong results.  No cudaMalloc,
  * cudaFree or allocating library routine is called. */
@@ -263,22 +267,37 @@ oam_status oam_lsqr_sweep_work_bytes(const oam_model *model, int32_t n_damps, si
 oam_status oam_solver_work_bytes(const oam_model *model, int32_t solver, size_t *bytes);
 
 /* ------------------------------------------------------------- autotuning */
-/* Pick the tensor-core kernels' item-ring depth for this model's shapes by
- * timing each candidate (CUDA events on `stream`, `reps` runs each after one
- * warm-up); the choice is kept in the model.  Allocates and frees a scratch
- * volume and signal buffer; synchronises `stream`.  No-op for
- * OAM_PREC_FP32.  The paper has no counterpart (tuning of this implementation). */
+/* Pick the tensor-core kernels' tile shape for this model's shapes by timing
+ * each candidate (CUDA events on `stream`, `reps` runs each after one
+ * warm-up): per direction, the number of fold warps (4, 8 or 16 warps that
+ * build the folded split-BF16 operand, each folding 32, 16 or 8 of a stage's
+ * 32 K elements per item) and the item-ring depth (slab tiles in shared
+ * memory and folded operands in tensor memory, 2 up to the deepest that
+ * fits).  The choice is kept in the model (read it with oam_model_get_tiles).
+ * Allocates and frees a scratch volume and signal buffer; synchronises
+ * `stream`.  No-op for the other precisions.  The paper has no counterpart
+ * (tuning of this implementation). */
 oam_status oam_model_autotune(oam_model *model, int32_t reps, void *stream, int32_t *ring_forward,
                               int32_t *ring_adjoint);
+/* Tile shape of the split-BF16 kernels, direction 0 = forward, 1 = adjoint:
+ * fold warps and the ring depth in use.  OAM_ERR_UNSUPPORTED for the other
+ * precisions. */
+oam_status oam_model_get_tiles(const oam_model *model, int32_t direction, int32_t *fold_warps, int32_t *ring);
+/* Set that shape (fold_warps 4, 8 or 16; ring 0 = deepest that fits, else
+ * 2 .. deepest); OAM_ERR_INVALID_ARG leaves the model unchanged.  Results do
+ * not depend on the shape (fixed summation order per accumulator). */
+oam_status oam_model_set_tiles(oam_model *model, int32_t direction, int32_t fold_warps, int32_t ring);
 
 /* --------------------------------------------------------------- batching */
 /* Many uneven reconstructions in one CUDA-graph launch (the paper reconstructs
  * one volume at a time; this is a serving feature).  Each job is LSQR (MB-L2)
- * and/or FISTA (MB-L1) on its own model, signals, images and workspace (at
- * least the larger of oam_solver_work_bytes(model, 0/1)); the jobs run on
- * separate branches of one graph, so their kernels overlap on the GPU.  The
- * graph is recorded on the first oam_batch_run after any oam_batch_set_job
- * and replayed afterwards.  Buffers must stay valid until the run completes. */
+ * and/or FISTA (MB-L1) on a model, signals, images and a workspace (at least
+ * the larger of oam_solver_work_bytes(model, 0/1)); jobs run on separate
+ * branches of one graph, so their kernels overlap on the GPU.  Jobs that use
+ * the same model (whose staging buffers serve one stream at a time) or
+ * overlapping workspaces share one branch and run in job order.  The graph
+ * is recorded on the first oam_batch_run after any oam_batch_set_job and
+ * replayed afterwards.  Buffers must stay valid until the run completes. */
 typedef struct oam_batch oam_batch;
 oam_status oam_batch_create(int32_t n_jobs, oam_batch **out);
 /* d_x_l2 / d_x_l1 may be NULL when the matching iteration count is 0. */

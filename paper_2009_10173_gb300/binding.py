@@ -22,7 +22,8 @@ EXPORTED = ("oam_build_model", "oam_model_free", "oam_model_get_info", "oam_mode
             "oam_model_autotune", "oam_batch_create", "oam_batch_set_job", "oam_batch_run", "oam_batch_free",
             "oam_server_create", "oam_server_submit", "oam_server_poll", "oam_server_wait", "oam_server_stats",
             "oam_server_stop", "oam_request_footprint", "oam_bandpass_taps", "oam_model_set_filter",
-            "oam_filter_signals", "oam_lsqr_sweep", "oam_lsqr_sweep_work_bytes")
+            "oam_filter_signals", "oam_lsqr_sweep", "oam_lsqr_sweep_work_bytes", "oam_model_get_tiles",
+            "oam_model_set_tiles")
 
 OAM_MAX_FIR_HALF = 8191
 OAM_MAX_SWEEP = 32
@@ -127,6 +128,8 @@ def lib():
         L.oam_profile_read.argtypes = [vp, P(OamProfile)]
         L.oam_launch_count.restype = ctypes.c_int64
         L.oam_model_autotune.argtypes = [vp, i32, vp, P(i32), P(i32)]
+        L.oam_model_get_tiles.argtypes = [vp, i32, P(i32), P(i32)]
+        L.oam_model_set_tiles.argtypes = [vp, i32, i32, i32]
         L.oam_batch_create.argtypes = [i32, P(vp)]
         L.oam_batch_set_job.argtypes = [vp, i32, vp, vp, vp, vp, P(OamLsqrOpts), P(OamFistaOpts), vp, sz]
         L.oam_batch_run.argtypes = [vp, vp]
@@ -308,6 +311,17 @@ def oam_model_autotune(model, reps=3, stream=None):
     _check("oam_model_autotune", lib().oam_model_autotune(model, int(reps), _stream(stream), ctypes.byref(f),
                                                           ctypes.byref(a)))
     return f.value, a.value
+
+
+def oam_model_get_tiles(model, direction):
+    """(fold warps, ring depth) of the split-BF16 kernel of one direction (0 forward, 1 adjoint)."""
+    w, r = ctypes.c_int32(), ctypes.c_int32()
+    _check("oam_model_get_tiles", lib().oam_model_get_tiles(model, int(direction), ctypes.byref(w), ctypes.byref(r)))
+    return w.value, r.value
+
+
+def oam_model_set_tiles(model, direction, fold_warps, ring=0):
+    _check("oam_model_set_tiles", lib().oam_model_set_tiles(model, int(direction), int(fold_warps), int(ring)))
 
 
 def oam_batch_create(n_jobs):

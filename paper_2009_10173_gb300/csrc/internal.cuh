@@ -153,7 +153,10 @@ void tc_free(oam_model *m, cudaStream_t st);
 oam_status forward_tc(const oam_model *m, const float *H, float *s, cudaStream_t st);
 oam_status adjoint_tc(const oam_model *m, const float *s, float *H, cudaStream_t st);
 double tc_exec_flops(const oam_model *m, int dir);
-oam_status tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_fwd, int *best_adj);
+oam_status tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_fwd, int *best_adj, int *warps_fwd,
+                       int *warps_adj);
+oam_status tc_set_tiles(oam_model *m, int dir, int fold_warps, int ring);
+void tc_get_tiles(const oam_model *m, int dir, int *fold_warps, int *ring);
 
 // op_fft.cu
 oam_status fft_build(oam_model *m, cudaStream_t st);

@@ -48,8 +48,8 @@ namespace oam {
 
 constexpr int kStageK = 32;        // K elements per stage (two 16-deep MMA chunks)
 constexpr int kTileM = 128;        // positions per block
-constexpr int kFoldWarps = 16;     // warps that build the folded operand (then run the epilogue)
-constexpr int kThreads = 64 + 32 * kFoldWarps;
+constexpr int kFoldWarpChoices[] = {4, 8, 16};  // warps that build the folded operand (then run the epilogue)
+constexpr int kDefaultFoldWarps = 8;
 constexpr int kMaxItems = 8;       // item ring depth (slab tile + folded operand)
 constexpr int kFoldCols = 32;      // tensor-memory columns per folded operand: 2 chunks x (hi, lo) x 8
 constexpr int kSmemLimit = 227 * 1024;
@@ -76,6 +76,7 @@ struct TcLayout {
   int in_elems = 0;       // packed elements per position (32 * stages)
   int slot_bytes = 0;     // shared-memory slot per item
   int ring_pref = 0;      // item-ring depth chosen by oam_model_autotune (0 = deepest that fits)
+  int fold_warps = kDefaultFoldWarps;  // fold-warp count chosen by oam_model_autotune (4, 8 or 16)
   TcItem *d_items = nullptr;
   uint8_t *d_data = nullptr;
   size_t data_bytes = 0;
@@ -178,8 +179,59 @@ __device__ __forceinline__ void split_bf16(const uint64_t (&v)[4], uint32_t (&hv
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// Fold one item: F = P[m + R + a] + P[m + R - a] (P[m + R] alone for a = 0)
+// for this thread's row m and its E of the stage's 32 K elements (8-element
+// quarters q0 .. q0 + E/8 - 1), split into BF16 hi/lo words in the order the
+// tensor-memory store takes them: E = 8: hi[4], lo[4]; E >= 16: per 16-deep
+// chunk, hi[8] then lo[8].
+template <int E>
+__device__ __forceinline__ void fold_item(const float *X1, int m, int R, int a, int q0, uint32_t (&w)[E]) {
+  constexpr int NQ = E / 8;
+  uint64_t f[NQ][4];
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) load_row(X1, m + R + a, q0 + i, f[i]);
+  if (a > 0) {
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) add_row(X1, m + R - a, q0 + i, f[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    uint32_t hv[4], lv[4];
+    split_bf16(f[i], hv, lv);
+    const int hb = E == 8 ? 0 : 16 * (i >> 1) + 4 * (i & 1);  // word of the quarter's first hi pair
+    const int lb = E == 8 ? 4 : hb + 8;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      w[hb + e] = hv[e];
+      w[lb + e] = lv[e];
+    }
+  }
+}
+
+// Store one folded item into its tensor-memory slot (slot column 0 = chunk 0
+// hi, 8 = chunk 0 lo, 16 = chunk 1 hi, 24 = chunk 1 lo; a column holds two
+// BF16 K elements).
+template <int E>
+__device__ __forceinline__ void store_item(uint32_t slot_addr, int q0, const uint32_t (&w)[E]) {
+  if constexpr (E == 8) {
+    const uint32_t col = (uint32_t)(16 * (q0 >> 1) + 4 * (q0 & 1));
+    uint32_t h[4] = {w[0], w[1], w[2], w[3]}, l[4] = {w[4], w[5], w[6], w[7]};
+    ptx::tmem_st4(slot_addr + col, h);
+    ptx::tmem_st4(slot_addr + col + 8u, l);
+  } else if constexpr (E == 16) {
+    ptx::tmem_st16(slot_addr + (uint32_t)(8 * q0), w);  // q0 = 2 * chunk
+  } else {
+    ptx::tmem_st32(slot_addr, w);
+  }
+}
+
+template <int FW>
+__global__ void __launch_bounds__(64 + 32 * FW, 1)
     k_corr_fold(const __grid_constant__ CUtensorMap tmap, const CorrParams p) {
+  constexpr int kFoldWarps = FW;
+  constexpr int kThreads = 64 + 32 * FW;
+  constexpr int G = FW / 4;   // K groups per tensor-memory lane quarter
+  constexpr int E = 32 / G;   // stage K elements folded per thread and item
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 128-byte-swizzled TMA destinations need 1024-byte alignment
   uint8_t *smem = smem_raw + ((1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
@@ -346,10 +398,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ fold warps, then epilogue
     const int fw = warp - 2;        // 0 .. kFoldWarps-1
     const int quarter = warp & 3;   // tensor-memory lanes 32*quarter .. +31
-    const int kq = fw >> 2;         // 8-deep quarter of the 32-deep stage this warp folds
+    const int kq = fw >> 2;         // K group of the stage this warp folds (E elements)
     const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
     const int nb = (p.acc_cols + 31) / 32;  // 32-column blocks of the accumulator
-    const int blk_begin = kq * nb / 4, blk_end = (kq + 1) * nb / 4;
+    const int blk_begin = kq * nb / G, blk_end = (kq + 1) * nb / G;
     for (int j = blk_begin; j < blk_end; ++j) ptx::tmem_st32_zero(tmem + lane_base + (uint32_t)(32 * j));
     ptx::tmem_wait_st();
     ptx::tc_fence_before();
@@ -359,8 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     if (!skip) {
       const int m = 32 * quarter + lane;  // row (tensor-memory lane) this thread folds
-      // elements 8 kq .. 8 kq + 7 of the stage: MMA chunk kq / 2, half kq % 2 of its 16 K
-      const uint32_t fold_off = (uint32_t)(16 * (kq >> 1) + 4 * (kq & 1));
+      const int q0 = kq * (E / 8);        // first 8-element quarter of the stage
       int it_strip = 0, k = 0;
       uint32_t lap = 0;
       for (int st = 0; st < p.stages && ok; ++st) {
@@ -401,26 +452,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) fail(64);
             break;
           }
-          uint32_t hv0[4], lv0[4], hv1[4], lv1[4];
-          {
-            uint64_t f0[4], f1[4];
-            load_row(X1, m + R + a, kq, f0);
-            if (a > 0) add_row(X1, m + R - a, kq, f0);
-            if (two) {
-              load_row(X1, m + R + a + 1, kq, f1);
-              add_row(X1, m + R - a - 1, kq, f1);
-            }
-            split_bf16(f0, hv0, lv0);
-            if (two) split_bf16(f1, hv1, lv1);
-          }
-          const uint32_t fa0 = tmem + lane_base + (uint32_t)(p.fold_col0 + 32 * k) + fold_off;
-          ptx::tmem_st4(fa0, hv0);
-          ptx::tmem_st4(fa0 + 8u, lv0);
-          if (two) {
-            const uint32_t fa1 = tmem + lane_base + (uint32_t)(p.fold_col0 + 32 * k1) + fold_off;
-            ptx::tmem_st4(fa1, hv1);
-            ptx::tmem_st4(fa1 + 8u, lv1);
-          }
+          uint32_t w0[E], w1[E];
+          fold_item<E>(X1, m, R, a, q0, w0);
+          if (two) fold_item<E>(X1, m, R, a + 1, q0, w1);
+          store_item<E>(tmem + lane_base + (uint32_t)(p.fold_col0 + 32 * k), q0, w0);
+          if (two) store_item<E>(tmem + lane_base + (uint32_t)(p.fold_col0 + 32 * k1), q0, w1);
           ptx::tmem_wait_st();
           ptx::tc_fence_before();
           __syncwarp();
@@ -737,6 +773,14 @@ oam_status plan_launch(const oam_model *m, const TcLayout *L, Launch *out) {
   return OAM_OK;
 }
 
+template <int FW>
+oam_status launch_fold(const Launch &lp, const TcLayout *L, dim3 grid, cudaStream_t st) {
+  OAM_CUDA_TRY(cudaFuncSetAttribute(k_corr_fold<FW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lp.smem));
+  k_corr_fold<FW><<<grid, 64 + 32 * FW, lp.smem, st>>>(L->tmap, lp.p);
+  OAM_LAUNCHED();
+  return OAM_OK;
+}
+
 oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int in_len, float *out, int out_len,
                     cudaStream_t st) {
   if (!m->d_tc_part || !m->d_tc_pack) return OAM_ERR_UNSUPPORTED;
@@ -751,12 +795,14 @@ oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int 
                                          m->grid.py, reinterpret_cast<float4 *>(m->d_tc_pack));
     OAM_LAUNCHED();
   }
-  OAM_CUDA_TRY(cudaFuncSetAttribute(k_corr_fold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lp.smem));
   const int n_tiles = (int)(((long long)m->grid.py * (m->grid.px + R) + kTileM - 1) / kTileM);
   {
     ProfScope prof(m, st, L->dir == 0);
-    k_corr_fold<<<dim3(n_tiles, R + 1), kThreads, lp.smem, st>>>(L->tmap, lp.p);
-    OAM_LAUNCHED();
+    const dim3 grid(n_tiles, R + 1);
+    if (L->fold_warps == 4) rc = launch_fold<4>(lp, L, grid, st);
+    else if (L->fold_warps == 16) rc = launch_fold<16>(lp, L, grid, st);
+    else rc = launch_fold<8>(lp, L, grid, st);
+    if (rc) return rc;
   }
   const size_t npos = (size_t)m->grid.py * m->grid.px;
   const int blocks = (int)std::min<size_t>((npos * out_len + 255) / 256, 16ull * m->sm_count);
@@ -829,9 +875,10 @@ oam_status oam::adjoint_tc(const oam_model *m, const float *s, float *H, cudaStr
 }
 
 // ---------------------------------------------------------------- autotuner
-// Ring depth per direction: time each candidate depth on the model's own
-// shapes (CUDA events on `st`) and keep the fastest.
-oam_status oam::tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_fwd, int *best_adj) {
+// Per direction, time every (fold-warp count, ring depth) pair on the model's
+// own shapes (CUDA events on `st`) and keep the fastest.
+oam_status oam::tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_fwd, int *best_adj, int *warps_fwd,
+                            int *warps_adj) {
   if (!m->tc_fwd) return OAM_ERR_UNSUPPORTED;
   const size_t nv = vol_elems(m), ns = sig_elems(m);
   float *buf = nullptr;
@@ -851,29 +898,66 @@ oam_status oam::tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_f
     if ((rc = plan_launch(m, L, &lp))) break;
     const int deepest = lp.p.n_items;
     float best_ms = 1e30f;
-    int best = deepest;
-    for (int depth = 2; depth <= deepest; depth += (depth < 4 ? 1 : 2)) {
-      L->ring_pref = depth;
-      for (int r = 0; r <= reps && !rc; ++r) {  // first run warms up
-        if (r == 1) cudaEventRecord(e0, st);
-        rc = dir == 0 ? run_corr(m, L, buf, m->grid.nz, buf + nv, m->grid.nt, st)
-                      : run_corr(m, L, buf + nv, m->grid.nt, buf, m->grid.nz, st);
+    int best = deepest, best_w = kDefaultFoldWarps;
+    for (int fw : kFoldWarpChoices) {
+      L->fold_warps = fw;
+      for (int depth = 2; depth <= deepest; depth += (depth < 4 ? 1 : 2)) {
+        L->ring_pref = depth;
+        for (int r = 0; r <= reps && !rc; ++r) {  // first run warms up
+          if (r == 1) cudaEventRecord(e0, st);
+          rc = dir == 0 ? run_corr(m, L, buf, m->grid.nz, buf + nv, m->grid.nt, st)
+                        : run_corr(m, L, buf + nv, m->grid.nt, buf, m->grid.nz, st);
+        }
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = OAM_ERR_CUDA;
+        if (rc) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = depth;
+          best_w = fw;
+        }
       }
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) rc = OAM_ERR_CUDA;
       if (rc) break;
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = depth;
-      }
     }
     L->ring_pref = best;
+    L->fold_warps = best_w;
     (dir == 0 ? *best_fwd : *best_adj) = best;
+    (dir == 0 ? *warps_fwd : *warps_adj) = best_w;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(buf);
   return rc;
+}
+
+oam_status oam::tc_set_tiles(oam_model *m, int dir, int fold_warps, int ring) {
+  TcLayout *L = dir == 0 ? m->tc_fwd : m->tc_adj;
+  if (!L) return OAM_ERR_UNSUPPORTED;
+  bool okw = false;
+  for (int fw : kFoldWarpChoices) okw = okw || fw == fold_warps;
+  if (!okw || ring < 0) return OAM_ERR_INVALID_ARG;
+  const int keep_ring = L->ring_pref, keep_w = L->fold_warps;
+  L->ring_pref = ring;
+  L->fold_warps = fold_warps;
+  Launch lp;
+  oam_status rc = plan_launch(m, L, &lp);
+  if (rc || (ring >= 2 && lp.p.n_items != ring)) {
+    L->ring_pref = keep_ring;
+    L->fold_warps = keep_w;
+    return rc ? rc : OAM_ERR_INVALID_ARG;
+  }
+  return OAM_OK;
+}
+
+void oam::tc_get_tiles(const oam_model *m, int dir, int *fold_warps, int *ring) {
+  const TcLayout *L = dir == 0 ? m->tc_fwd : m->tc_adj;
+  if (!L) {
+    *fold_warps = *ring = 0;
+    return;
+  }
+  Launch lp;
+  *fold_warps = L->fold_warps;
+  *ring = plan_launch(m, L, &lp) == OAM_OK ? lp.p.n_items : 0;
 }

@@ -30,6 +30,8 @@ def main():
     p.add_argument("--workload", default="volume_200x200x300", choices=sorted(configs.WORKLOADS))
     for k in ("px", "py", "nz", "nt", "win", "iters"):
         p.add_argument(f"--{k}", type=int, default=None)
+    p.add_argument("--fold-warps", type=int, default=None, help="split-BF16 kernels: fold warps (4, 8, 16)")
+    p.add_argument("--ring", type=int, default=0, help="split-BF16 kernels: item-ring depth (0 = deepest)")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=1)
     a = p.parse_args()
@@ -37,6 +39,9 @@ def main():
     cfg = configs.scaled(configs.WORKLOADS[a.workload], **over)
     prec = {"bf16x3": B.OAM_PREC_BF16X3, "fp32": B.OAM_PREC_FP32, "fft": B.OAM_PREC_FFT}[a.prec]
     m = Model(cfg, precision=prec)
+    if a.fold_warps is not None and prec == B.OAM_PREC_BF16X3:
+        for d in (0, 1):
+            B.oam_model_set_tiles(m.handle, d, a.fold_warps, a.ring)
     H = torch.from_numpy(inputs.phantom(cfg, 1, count=20)).float().cuda()
     s = m.forward(H)
     iters = a.iters or 5
@@ -64,7 +69,9 @@ def main():
     print(json.dumps({"op": a.op, "prec": a.prec, "grid": [cfg["py"], cfg["px"], cfg["nz"], cfg["nt"], cfg["win"]],
                       "ms_per_call": ms, "flops_per_op": m.info.flops_per_op,
                       "alg_tflops": m.info.flops_per_op / ms / 1e9 if a.op in ("forward", "adjoint") else None,
-                      "model_bytes": m.info.device_bytes, "op_bytes": m.info.op_bytes, **extra}))
+                      "model_bytes": m.info.device_bytes, "op_bytes": m.info.op_bytes,
+                      "tiles": [B.oam_model_get_tiles(m.handle, d) for d in (0, 1)]
+                      if prec == B.OAM_PREC_BF16X3 else None, **extra}))
     m.close()
 
 
