@@ -124,6 +124,21 @@ typedef struct {
 oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
                            oam_precision precision, void *stream, oam_model **out);
 
+/* Device bytes oam_build_model would allocate for these parameters (the
+ * model's device_bytes after the build; a band-pass filter set later adds
+ * its own), computed on the host before anything is allocated.  The paper's
+ * compressed model is a single scanning position's, so its size depends on
+ * the window, depths, samples and sensor, not on the number of scan
+ * positions (Results; Methods, Efficient reconstruction based on scanning
+ * symmetries) -- only the tensor-core staging buffers grow with the scan.
+ * The bands are planned from host-side distances with two samples of margin
+ * per band edge, so the result bounds the built model's device_bytes from
+ * above (by a few per cent).  Same argument errors as oam_build_model
+ * (OAM_ERR_WINDOW up to rounding at the window's exact edge;
+ * OAM_ERR_UNSUPPORTED for shapes a kernel does not take); no device call. */
+oam_status oam_model_bytes(const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
+                           oam_precision precision, size_t *bytes);
+
 /* Release a model (NULL is accepted).  Synchronises the device first. */
 oam_status oam_model_free(oam_model *model);
 
@@ -312,8 +327,9 @@ oam_status oam_batch_free(oam_batch *batch);
 /* A continuous-batching request server (no counterpart in the paper).  A host
  * thread admits queued requests first-in first-out while a slot (CUDA stream)
  * is free and the device-memory reservation stays within hbm_budget_bytes
- * (a conservative per-request estimate: model, signals, two images,
- * workspace); each admitted request builds its model, copies its host signals
+ * (oam_request_footprint: the model's planned bytes, signals, two images and
+ * the solver workspace; reconciled upward with the built model's bytes if
+ * they ever exceed it); each admitted request builds its model, copies its host signals
  * in, runs LSQR then FISTA, and copies both images out on its slot's stream,
  * so requests on different slots overlap on the GPU.  Finished requests
  * release their memory and slot to the next queued request.  Results do not
@@ -335,9 +351,13 @@ typedef struct {
   int32_t queued, running, peak_running;
   size_t reserved_bytes, peak_reserved_bytes;
 } oam_server_stats_t;
-/* Device bytes the server reserves for one request of this grid before
- * admitting it (an upper bound of what the request allocates). */
-oam_status oam_request_footprint(int32_t precision, const oam_grid *grid, size_t *bytes);
+/* Device bytes the server reserves for one request before admitting it:
+ * oam_model_bytes plus its signals, two images and solver workspace (an
+ * upper bound of what the request allocates).  Host only.  A request whose
+ * model cannot be built (oam_model_bytes fails) fails at admission with that
+ * status. */
+oam_status oam_request_footprint(int32_t precision, const oam_sensor *sensor, const oam_grid *grid,
+                                 const oam_eir *eir, size_t *bytes);
 oam_status oam_server_create(const oam_server_opts *opts, oam_server **out);
 /* h_s: host signals (py*px*nt floats), h_x_l2 / h_x_l1: host images
  * (py*px*nz floats, may be NULL); all must stay valid until the request ends. */

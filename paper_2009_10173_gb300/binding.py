@@ -23,7 +23,7 @@ EXPORTED = ("oam_build_model", "oam_model_free", "oam_model_get_info", "oam_mode
             "oam_server_create", "oam_server_submit", "oam_server_poll", "oam_server_wait", "oam_server_stats",
             "oam_server_stop", "oam_request_footprint", "oam_bandpass_taps", "oam_model_set_filter",
             "oam_filter_signals", "oam_lsqr_sweep", "oam_lsqr_sweep_work_bytes", "oam_model_get_tiles",
-            "oam_model_set_tiles")
+            "oam_model_set_tiles", "oam_model_bytes")
 
 OAM_MAX_FIR_HALF = 8191
 OAM_MAX_SWEEP = 32
@@ -129,6 +129,7 @@ def lib():
         L.oam_launch_count.restype = ctypes.c_int64
         L.oam_model_autotune.argtypes = [vp, i32, vp, P(i32), P(i32)]
         L.oam_model_get_tiles.argtypes = [vp, i32, P(i32), P(i32)]
+        L.oam_model_bytes.argtypes = [P(OamSensor), P(OamGrid), P(OamEir), i32, P(sz)]
         L.oam_model_set_tiles.argtypes = [vp, i32, i32, i32]
         L.oam_batch_create.argtypes = [i32, P(vp)]
         L.oam_batch_set_job.argtypes = [vp, i32, vp, vp, vp, vp, P(OamLsqrOpts), P(OamFistaOpts), vp, sz]
@@ -140,7 +141,7 @@ def lib():
         L.oam_server_wait.argtypes = [vp, ctypes.c_int64, ctypes.c_double]
         L.oam_server_stats.argtypes = [vp, P(OamServerStats)]
         L.oam_server_stop.argtypes = [vp]
-        L.oam_request_footprint.argtypes = [i32, P(OamGrid), P(sz)]
+        L.oam_request_footprint.argtypes = [i32, P(OamSensor), P(OamGrid), P(OamEir), P(sz)]
         f64 = ctypes.c_double
         L.oam_bandpass_taps.argtypes = [f64, f64, f64, i32, P(f64)]
         L.oam_model_set_filter.argtypes = [vp, P(f64), i32, vp]
@@ -313,6 +314,15 @@ def oam_model_autotune(model, reps=3, stream=None):
     return f.value, a.value
 
 
+def oam_model_bytes(cfg, precision):
+    """Device bytes oam_build_model would allocate for a configuration (host only)."""
+    sn, g, e = structs_from_config(cfg)
+    out = ctypes.c_size_t()
+    _check("oam_model_bytes", lib().oam_model_bytes(ctypes.byref(sn), ctypes.byref(g), ctypes.byref(e),
+                                                    int(precision), ctypes.byref(out)))
+    return out.value
+
+
 def oam_model_get_tiles(model, direction):
     """(fold warps, ring depth) of the split-BF16 kernel of one direction (0 forward, 1 adjoint)."""
     w, r = ctypes.c_int32(), ctypes.c_int32()
@@ -379,7 +389,10 @@ def oam_server_stop(server):
     _check("oam_server_stop", lib().oam_server_stop(server))
 
 
-def oam_request_footprint(precision, grid):
+def oam_request_footprint(precision, sensor, grid, eir):
+    """Device bytes the server reserves for a request (host only)."""
     n = ctypes.c_size_t()
-    _check("oam_request_footprint", lib().oam_request_footprint(int(precision), ctypes.byref(grid), ctypes.byref(n)))
+    _check("oam_request_footprint", lib().oam_request_footprint(int(precision), ctypes.byref(sensor),
+                                                                ctypes.byref(grid), ctypes.byref(eir),
+                                                                ctypes.byref(n)))
     return n.value

@@ -99,6 +99,51 @@ void plan_orbits(oam_model *m) {
     for (int a = -R; a <= R; ++a) m->h_tap_orbit[(b + R) * W + (a + R)] = id[std::abs(b) * (R + 1) + std::abs(a)];
 }
 
+// Range of d - F over the patch set for every (orbit, depth), on the host.
+// Within a ring (polar angle fixed) r.n = r_z cos(theta) + sin(theta) rho
+// cos(phi - psi), psi the voxel's azimuth, so the ring's largest and smallest
+// distances belong to the patches whose azimuths are nearest psi and psi + pi;
+// d - F = (2F r.n + |r|^2) / (d + F) grows with r.n.
+void host_ranges(const oam_model *m, const std::vector<Ring> &rings, std::vector<double2> *out) {
+  const double F = m->sensor.focal_m;
+  const int nz = m->grid.nz;
+  out->assign((size_t)m->n_orb * nz, make_double2(INFINITY, -INFINITY));
+  // patch normals as the device expands them: phi_m = (2m + 1) pi / count
+  std::vector<double> nx, ny, nzv;
+  for (const Ring &g : rings) {
+    const double sn = std::sqrt(1.0 - g.cos_mid * g.cos_mid);
+    for (int j = 0; j < g.count; ++j) {
+      const double phi = M_PI * (2.0 * j + 1.0) / g.count;
+      nx.push_back(sn * std::cos(phi));
+      ny.push_back(sn * std::sin(phi));
+      nzv.push_back(g.cos_mid);
+    }
+  }
+  std::vector<int> cand;
+  for (int o = 0; o < m->n_orb; ++o) {
+    const double rx = m->h_orb_a[o] * m->grid.dx_m, ry = m->h_orb_b[o] * m->grid.dy_m;
+    const double psi = std::atan2(ry, rx);
+    cand.clear();  // per ring: the patches nearest in azimuth to psi and to psi + pi
+    for (const Ring &g : rings)
+      for (int side = 0; side < 2; ++side) {
+        const long m0 = std::lround((psi + (side ? M_PI : 0.0)) * g.count / (2.0 * M_PI) - 0.5);
+        for (long dm = -1; dm <= 1; ++dm) cand.push_back(g.first + (int)(((m0 + dm) % g.count + g.count) % g.count));
+      }
+    for (int k = 0; k < nz; ++k) {
+      const double rz = m->grid.z0_rel_m + k * m->grid.dz_m;
+      const double r2 = rx * rx + ry * ry + rz * rz;
+      double2 &rg = (*out)[(size_t)o * nz + k];
+      for (int j : cand) {
+        const double rn = rx * nx[j] + ry * ny[j] + rz * nzv[j];
+        const double num = 2.0 * F * rn + r2;
+        const double dd = num / (std::sqrt(F * F + num) + F);
+        rg.x = std::min(rg.x, dd);
+        rg.y = std::max(rg.y, dd);
+      }
+    }
+  }
+}
+
 void free_model(oam_model *m, cudaStream_t st) {
   if (!m) return;
   tc_free(m, st);
@@ -264,6 +309,39 @@ oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const
     return rc;
   }
   *out = m;
+  return OAM_OK;
+}
+
+oam_status oam_model_bytes(const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
+                           oam_precision precision, size_t *bytes) {
+  if (!bytes) return OAM_ERR_INVALID_ARG;
+  oam_status rc = check_params(sensor, grid, eir);
+  if (rc) return rc;
+  if (precision != OAM_PREC_FP32 && precision != OAM_PREC_BF16X3 && precision != OAM_PREC_FFT)
+    return OAM_ERR_INVALID_ARG;
+  oam_model m;  // host-side plan only: no device memory, no device call
+  m.sensor = *sensor;
+  m.grid = *grid;
+  m.eir = *eir;
+  m.precision = precision;
+  m.W = grid->win;
+  m.R = (grid->win - 1) / 2;
+  const double sig_f = eir->fc_hz * eir->frac_bw / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+  m.sigma_s = grid->fs_hz / (2.0 * M_PI * sig_f);
+  m.omega = 2.0 * M_PI * eir->fc_hz / grid->fs_hz;
+  m.cut = eir->trunc_sigma * m.sigma_s;
+  m.M = sensor->n_patches;
+  plan_orbits(&m);
+  std::vector<double2> ranges;
+  host_ranges(&m, plan_rings(sensor), &ranges);
+  // two samples of margin per band edge: host and device distances may round
+  // a band edge, or the automatic time origin, one sample apart
+  if ((rc = plan_bands(&m, ranges, 2))) return rc;
+  size_t total = alloc_bytes<int>(1) + alloc_bytes<Patch>(m.M) + slab_plan_bytes(&m), extra = 0;
+  if (precision == OAM_PREC_BF16X3) rc = tc_plan_bytes(&m, &extra);
+  if (precision == OAM_PREC_FFT) rc = fft_plan_bytes(&m, &extra);
+  if (rc) return rc;
+  *bytes = total + extra;
   return OAM_OK;
 }
 

@@ -139,8 +139,18 @@ struct ProfScope {
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Bytes dev_alloc reserves for `count` elements of T (an empty array still takes one).
+template <typename T>
+inline size_t alloc_bytes(size_t count) {
+  return (count ? count : 1) * sizeof(T);
+}
+
 // slab.cu
 oam_status build_slab(oam_model *m, cudaStream_t st);
+oam_status plan_bands(oam_model *m, const std::vector<double2> &h_range, int widen);
+long long fwd_layout(const oam_model *m, std::vector<int> *kr, std::vector<long long> *off);
+long long adj_layout(const oam_model *m, std::vector<int> *nr, std::vector<long long> *off);
+size_t slab_plan_bytes(const oam_model *m);
 oam_status slab_column(const oam_model *m, int b, int a, int k, float *d_out, cudaStream_t st);
 
 // op_fp32.cu
@@ -153,6 +163,7 @@ void tc_free(oam_model *m, cudaStream_t st);
 oam_status forward_tc(const oam_model *m, const float *H, float *s, cudaStream_t st);
 oam_status adjoint_tc(const oam_model *m, const float *s, float *H, cudaStream_t st);
 double tc_exec_flops(const oam_model *m, int dir);
+oam_status tc_plan_bytes(const oam_model *m, size_t *bytes);
 oam_status tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_fwd, int *best_adj, int *warps_fwd,
                        int *warps_adj);
 oam_status tc_set_tiles(oam_model *m, int dir, int fold_warps, int ring);
@@ -165,6 +176,7 @@ oam_status forward_fft(const oam_model *m, const float *H, float *s, cudaStream_
 oam_status adjoint_fft(const oam_model *m, const float *s, float *H, cudaStream_t st);
 double fft_flops(const oam_model *m);
 double fft_bytes(const oam_model *m);
+oam_status fft_plan_bytes(const oam_model *m, size_t *bytes);
 
 // op_filter.cu: y = F x over the model's py*px A-lines (x and y may alias)
 oam_status fir_apply(const oam_model *m, const float *x, float *y, cudaStream_t st);

@@ -658,9 +658,17 @@ __global__ void __launch_bounds__(kBuildThreads) k_shat_pass2(const float *__res
 
 size_t fft_smem(int P, int KC) { return sizeof(float2) * ((size_t)(P >> 1) + (size_t)P * KC); }
 
-}  // namespace
+// Host tables of the lateral-FFT layout, planned from the model's bands.
+struct FftPlan {
+  std::vector<int> klo, klen;
+  std::vector<long long> koff, noff;
+  std::vector<int2> krange, entry_kn;
+  std::vector<int> rep_of;
+  std::vector<int4> members;
+};
 
-oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
+// Fill L's sizes and the host tables (no device call).
+oam_status fft_plan(const oam_model *m, FftLayout *L, FftPlan &pl) {
   const int R = m->R, W = m->W, nz = m->grid.nz;
   const int need = std::max(m->grid.py, m->grid.px) + R;
   int P = 2, lgP = 1;
@@ -669,9 +677,6 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
     ++lgP;
   }
   if (P > 2048) return OAM_ERR_UNSUPPORTED;
-  FftLayout *L = new (std::nothrow) FftLayout();
-  if (!L) return OAM_ERR_OOM;
-  m->fft = L;
   L->P = P;
   L->lgP = lgP;
   L->Q = P / 2 + 1;
@@ -686,8 +691,11 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
         break;
       }
   // union band per depth over all orbits
-  std::vector<int> klo(nz, 0), klen(nz, 0);
-  std::vector<long long> koff(nz, 0);
+  std::vector<int> &klo = pl.klo, &klen = pl.klen;
+  std::vector<long long> &koff = pl.koff;
+  klo.assign(nz, 0);
+  klen.assign(nz, 0);
+  koff.assign(nz, 0);
   long long row = 0;
   for (int k = 0; k < nz; ++k) {
     int lo = 1 << 30, hi = -1;
@@ -706,7 +714,8 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
   }
   L->row_len = std::max<long long>(row, 1);
   L->NS = std::max(1, m->n_hi - m->n_lo);
-  std::vector<int2> krange(L->NS, make_int2(0, 0));
+  std::vector<int2> &krange = pl.krange;
+  krange.assign(L->NS, make_int2(0, 0));
   for (int j = 0; j < L->NS; ++j) {
     const int n = m->n_lo + j;
     int kf = nz, kl = -1;
@@ -717,7 +726,8 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
       }
     krange[j] = kl >= kf ? make_int2(kf, kl + 1) : make_int2(0, 0);
   }
-  std::vector<long long> noff(L->NS, 0);
+  std::vector<long long> &noff = pl.noff;
+  noff.assign(L->NS, 0);
   long long rowt = 0;
   for (int j = 0; j < L->NS; ++j) {
     noff[j] = rowt;
@@ -725,12 +735,15 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
   }
   L->row_len_t = std::max<long long>(rowt, 1);
   L->C = std::max(nz, L->NS);
-  std::vector<int2> entry_kn((size_t)L->row_len, make_int2(0, 0));
+  std::vector<int2> &entry_kn = pl.entry_kn;
+  entry_kn.assign((size_t)L->row_len, make_int2(0, 0));
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < klen[k]; ++j) entry_kn[(size_t)koff[k] + j] = make_int2(k, klo[k] + j);
   // frequency orbits and their members in the half spectrum (index u*P + v)
-  std::vector<int> rep_of((size_t)Q * Q, -1);
-  std::vector<int4> members;
+  std::vector<int> &rep_of = pl.rep_of;
+  std::vector<int4> &members = pl.members;
+  rep_of.assign((size_t)Q * Q, -1);
+  members.clear();
   long long covered = 0;
   for (int u0 = 0; u0 < Q; ++u0)
     for (int v0 = 0; v0 < (L->d4 ? u0 + 1 : Q); ++v0) {
@@ -748,7 +761,43 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
     }
   if (covered != (long long)Q * P) return OAM_ERR_DEVICE;  // orbit plan must cover the half spectrum once
   L->n_rep = (int)members.size();
+  return OAM_OK;
+}
 
+// Device bytes fft_build allocates and keeps (host only).
+oam_status fft_layout_bytes(const FftLayout &L, const FftPlan &pl, int nz, size_t *bytes) {
+  *bytes = alloc_bytes<int>(nz) * 2 + alloc_bytes<long long>(nz) + alloc_bytes<int4>(pl.members.size()) +
+           alloc_bytes<int2>(L.NS) + alloc_bytes<long long>(L.NS) +
+           alloc_bytes<float>((size_t)L.n_rep * L.row_len_t) + alloc_bytes<float>((size_t)L.n_rep * L.row_len) +
+           2 * alloc_bytes<float2>((size_t)L.Q * L.P * L.C);
+  return OAM_OK;
+}
+
+}  // namespace
+
+oam_status oam::fft_plan_bytes(const oam_model *m, size_t *bytes) {
+  FftLayout L;
+  FftPlan pl;
+  oam_status rc = fft_plan(m, &L, pl);
+  if (rc) return rc;
+  return fft_layout_bytes(L, pl, m->grid.nz, bytes);
+}
+
+oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
+  const int R = m->R, W = m->W, nz = m->grid.nz;
+  FftLayout *L = new (std::nothrow) FftLayout();
+  if (!L) return OAM_ERR_OOM;
+  m->fft = L;
+  FftPlan pl;
+  {
+    oam_status rc0 = fft_plan(m, L, pl);
+    if (rc0) return rc0;
+  }
+  const int P = L->P, Q = L->Q, lgP = L->lgP;
+  std::vector<int> &klo = pl.klo, &klen = pl.klen, &rep_of = pl.rep_of;
+  std::vector<long long> &koff = pl.koff, &noff = pl.noff;
+  std::vector<int2> &krange = pl.krange, &entry_kn = pl.entry_kn;
+  std::vector<int4> &members = pl.members;
   oam_status rc;
   if ((rc = dev_alloc(m, &L->d_klo, nz)) || (rc = dev_alloc(m, &L->d_klen, nz)) ||
       (rc = dev_alloc(m, &L->d_koff, nz)) || (rc = dev_alloc(m, &L->d_members, members.size())) ||

@@ -624,8 +624,9 @@ oam_status encode_tmap(CUtensorMap *map, float *base, long long qtot, int elems,
   return OAM_OK;
 }
 
-// Build one direction's item and tile tables from the band form, then pack.
-oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d_band_hi) {
+// One direction's item and tile tables from the band form (host only).
+oam_status plan_dir(const oam_model *m, TcLayout *L, int dir, std::vector<TcItem> &items,
+                    std::vector<TcTile> &tiles) {
   const int nz = m->grid.nz, O = m->n_orb;
   const int t_lo = m->n_lo & ~15;
   L->dir = dir;
@@ -644,8 +645,8 @@ oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d
   L->tmem_cols = pow2_cols(L->acc_cols);
   if (L->tmem_cols > 512) return OAM_ERR_UNSUPPORTED;
 
-  std::vector<TcItem> items((size_t)O * L->stages);
-  std::vector<TcTile> tiles;
+  items.assign((size_t)O * L->stages, TcItem{});
+  tiles.clear();
   long long off = 0;
   int max_item = 16;
   for (int o = 0; o < O; ++o) {
@@ -715,7 +716,16 @@ oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d
     }
     L->exec_flops = 3.0 * 2.0 * kTileM * total;
   }
-  oam_status rc;
+  return OAM_OK;
+}
+
+// Build one direction's item and tile tables from the band form, then pack.
+oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d_band_hi) {
+  std::vector<TcItem> items;
+  std::vector<TcTile> tiles;
+  oam_status rc = plan_dir(m, L, dir, items, tiles);
+  if (rc) return rc;
+  const int nz = m->grid.nz, t_lo = m->n_lo & ~15;
   if ((rc = dev_alloc(m, &L->d_items, items.size()))) return rc;
   if ((rc = dev_alloc(m, &L->d_data, L->data_bytes))) return rc;
   OAM_CUDA_TRY(cudaMemcpyAsync(L->d_items, items.data(), sizeof(TcItem) * items.size(), cudaMemcpyHostToDevice, st));
@@ -812,6 +822,31 @@ oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int 
 }
 
 }  // namespace
+
+// Device bytes tc_build allocates, from the planned bands (host only; no
+// device call).  Fails like tc_build on shapes the kernels do not take.
+oam_status oam::tc_plan_bytes(const oam_model *m, size_t *bytes) {
+  if (kTileM + 2 * m->R > 256) return OAM_ERR_UNSUPPORTED;
+  TcLayout Lf, La;
+  std::vector<TcItem> items;
+  std::vector<TcTile> tiles;
+  size_t b = 0;
+  for (int dir = 0; dir < 2; ++dir) {
+    TcLayout *L = dir == 0 ? &Lf : &La;
+    oam_status rc = plan_dir(m, L, dir, items, tiles);
+    if (rc) return rc;
+    Launch lp;
+    if ((rc = plan_launch(m, L, &lp))) return rc;
+    b += alloc_bytes<TcItem>(items.size()) + alloc_bytes<uint8_t>(L->data_bytes);
+  }
+  const int wp = m->grid.px + m->R;
+  const long long qtot = (long long)(m->grid.py + 2 * m->R + 2) * wp + 256;
+  if (qtot > 0x7fffffffLL) return OAM_ERR_UNSUPPORTED;
+  b += alloc_bytes<uint8_t>((size_t)std::max(Lf.in_elems, La.in_elems) * qtot * sizeof(float));
+  b += alloc_bytes<float>((size_t)(m->R + 1) * m->grid.py * m->grid.px * std::max(Lf.acc_cols, La.acc_cols));
+  *bytes = b;
+  return OAM_OK;
+}
 
 oam_status oam::tc_build(oam_model *m, cudaStream_t st) {
   if (kTileM + 2 * m->R > 256) return OAM_ERR_UNSUPPORTED;  // strip rows per TMA box

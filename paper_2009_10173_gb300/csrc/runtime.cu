@@ -253,6 +253,8 @@ struct oam_server {
     float *h_x2 = nullptr, *h_x1 = nullptr;
     int32_t state = 0;  // 0 queued, 1 running, 2 done, 3 failed
     oam_status error = OAM_OK;
+    size_t need = 0;              // reservation planned at submit (model plan + buffers + workspace)
+    oam_status plan_rc = OAM_OK;  // the plan's status: a request that cannot be built fails at admission
     size_t reserved = 0;
     std::chrono::steady_clock::time_point t_submit, t_done;
     // device resources while running
@@ -282,28 +284,18 @@ namespace {
 size_t vol_bytes(const oam_grid &g) { return (size_t)g.px * g.py * g.nz * sizeof(float); }
 size_t sig_bytes(const oam_grid &g) { return (size_t)g.px * g.py * g.nt * sizeof(float); }
 
-// Device-memory reservation for a request before its model exists: signals,
-// two images, solver workspace, and an upper bound of the model (band form,
-// FP32 layouts, tensor-core tiles and per-|b| partial sums).
-size_t footprint_estimate(const oam_server_opts &o, const oam_grid &g) {
-  const size_t R = (g.win - 1) / 2;
-  const size_t orbits = (R + 1) * (R + 1);
-  const size_t band = 512;  // samples per (orbit, depth) upper bound
-  size_t model = orbits * g.nz * band * 4 * 3;  // band form + two FP32 layouts
-  if (o.precision == OAM_PREC_BF16X3) {
-    model += orbits * g.nz * band * 2 * 2 * 2;                      // BF16 hi/lo tiles, both directions
-    model += (R + 1) * (size_t)g.px * g.py * 512 * sizeof(float);   // per-|b| partial sums
-    model += (size_t)(g.py + 2 * R + 2) * (g.px + R) * 512 * sizeof(float);  // staged input
-  }
-  if (o.precision == OAM_PREC_FFT) {
-    size_t P = 2;
-    while (P < (size_t)std::max(g.py, g.px) + R) P <<= 1;
-    const size_t Q = P / 2 + 1, reps = Q * (Q + 1) / 2;
-    model += 2 * reps * g.nz * 256 * sizeof(float);                 // spectral slab, two orders (union bands <= 256)
-    model += 2 * Q * P * (size_t)std::max(g.nz, g.nt) * 8;          // complex work buffers
-  }
-  const size_t work = 256 * 1024 + 2 * sig_bytes(g) + 3 * vol_bytes(g);
-  return model + sig_bytes(g) + 2 * vol_bytes(g) + work;
+// Device-memory reservation for a request before its model exists: the
+// model's planned device bytes (oam_model_bytes, an upper bound of what the
+// build allocates), the signals, two images and the solver workspace (the
+// larger of LSQR's 2 signal + 3 volume vectors and FISTA's, plus scalars).
+oam_status request_footprint(int precision, const oam_sensor *sn, const oam_grid *g, const oam_eir *e,
+                             size_t *bytes) {
+  size_t model = 0;
+  oam_status rc = oam_model_bytes(sn, g, e, (oam_precision)precision, &model);
+  if (rc) return rc;
+  const size_t work = 256 * 1024 + 2 * sig_bytes(*g) + 3 * vol_bytes(*g);
+  *bytes = model + sig_bytes(*g) + 2 * vol_bytes(*g) + work;
+  return OAM_OK;
 }
 
 void release(oam_server *S, oam_server::Req &r) {
@@ -327,7 +319,7 @@ void release(oam_server *S, oam_server::Req &r) {
 }
 
 // Build and enqueue one admitted request (server thread, lock not held).
-oam_status launch(oam_server *S, oam_server::Req &r) {
+oam_status launch(oam_server *S, oam_server::Req &r, size_t *actual) {
   cudaStream_t st = S->streams[r.slot];
   oam_status rc = oam_build_model(&r.sensor, &r.grid, &r.eir, (oam_precision)S->opts.precision, st, &r.model);
   if (rc) return rc;
@@ -335,6 +327,7 @@ oam_status launch(oam_server *S, oam_server::Req &r) {
   oam_solver_work_bytes(r.model, 0, &w0);
   oam_solver_work_bytes(r.model, 1, &w1);
   const size_t wb = std::max(w0, w1);
+  *actual = r.model->bytes + sig_bytes(r.grid) + 2 * vol_bytes(r.grid) + wb;
   if (cudaMallocAsync((void **)&r.d_s, sig_bytes(r.grid), st) != cudaSuccess ||
       cudaMallocAsync((void **)&r.d_x2, vol_bytes(r.grid), st) != cudaSuccess ||
       cudaMallocAsync((void **)&r.d_x1, vol_bytes(r.grid), st) != cudaSuccess ||
@@ -384,7 +377,15 @@ void server_loop(oam_server *S) {
     // 2. admit queued requests (first in, first out) while a slot and memory are free
     while (!S->queue.empty()) {
       oam_server::Req &r = S->reqs[S->queue.front()];
-      const size_t need = footprint_estimate(S->opts, r.grid);
+      if (r.plan_rc) {  // the model cannot be built (invalid parameters, window, shape)
+        S->queue.pop_front();
+        r.state = 3;
+        r.error = r.plan_rc;
+        r.t_done = std::chrono::steady_clock::now();
+        S->cv.notify_all();
+        continue;
+      }
+      const size_t need = r.need;
       int slot = -1;
       for (int i = 0; i < (int)S->slot_busy.size(); ++i)
         if (!S->slot_busy[i]) {
@@ -411,8 +412,14 @@ void server_loop(oam_server *S) {
       S->peak_running = std::max(S->peak_running, S->running);
       r.state = 1;
       lk.unlock();
-      const oam_status rc = launch(S, r);
+      size_t actual = 0;
+      const oam_status rc = launch(S, r, &actual);
       lk.lock();
+      if (!rc && actual > r.reserved) {  // reconcile with what the request really holds
+        S->reserved += actual - r.reserved;
+        r.reserved = actual;
+        S->peak_reserved = std::max(S->peak_reserved, S->reserved);
+      }
       if (rc) {
         cudaStreamSynchronize(S->streams[slot]);
         cudaGetLastError();
@@ -430,15 +437,12 @@ void server_loop(oam_server *S) {
 
 }  // namespace
 
-extern "C" oam_status oam_request_footprint(int32_t precision, const oam_grid *grid, size_t *bytes) {
-  if (!grid || !bytes || grid->win < 1 || grid->px < 1 || grid->py < 1 || grid->nz < 1 || grid->nt < 1)
-    return OAM_ERR_INVALID_ARG;
+extern "C" oam_status oam_request_footprint(int32_t precision, const oam_sensor *sensor, const oam_grid *grid,
+                                            const oam_eir *eir, size_t *bytes) {
+  if (!sensor || !grid || !eir || !bytes) return OAM_ERR_INVALID_ARG;
   if (precision != OAM_PREC_FP32 && precision != OAM_PREC_BF16X3 && precision != OAM_PREC_FFT)
     return OAM_ERR_INVALID_ARG;
-  oam_server_opts o{};
-  o.precision = precision;
-  *bytes = footprint_estimate(o, *grid);
-  return OAM_OK;
+  return request_footprint(precision, sensor, grid, eir, bytes);
 }
 
 extern "C" oam_status oam_server_create(const oam_server_opts *opts, oam_server **out) {
@@ -473,9 +477,10 @@ extern "C" oam_status oam_server_submit(oam_server *S, const oam_sensor *sensor,
                                         const oam_eir *eir, const float *h_s, float *h_x_l2, float *h_x_l1,
                                         int64_t *request_id) {
   if (!S || !sensor || !grid || !eir || !h_s || !request_id) return OAM_ERR_INVALID_ARG;
+  oam_server::Req r;
+  r.plan_rc = request_footprint(S->opts.precision, sensor, grid, eir, &r.need);  // host only, outside the lock
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->stop) return OAM_ERR_BUSY;
-  oam_server::Req r;
   r.id = S->next_id++;
   r.sensor = *sensor;
   r.grid = *grid;

@@ -309,6 +309,138 @@ __global__ void k_slab_column(const float *band, const int *band_lo, int band_w,
 
 }  // namespace
 
+// Time origin, window check and bands [lo, hi) per (orbit, depth) from the
+// range of d - F over the patches; each band is widened by `widen` samples on
+// both sides (0 for a model build; the footprint planner widens to cover
+// rounding of its host-side distances).  Also the slab's nonzero count and
+// the operator's algorithmic flops.
+oam_status oam::plan_bands(oam_model *m, const std::vector<double2> &h_range, int widen) {
+  const oam_grid &gr = m->grid;
+  const int nz = gr.nz, nt = gr.nt, O = m->n_orb;
+  double dmin = INFINITY, dmax = -INFINITY;
+  for (const double2 &r : h_range) {
+    dmin = std::min(dmin, r.x);
+    dmax = std::max(dmax, r.y);
+  }
+  const double fs = gr.fs_hz, c = m->sensor.c_mps, F = m->sensor.focal_m, ks = fs / c;
+  const double t0 = std::isnan(gr.t0_s) ? (std::floor(fs * (F + dmin) / c - m->cut) - 2.0) / fs : gr.t0_s;
+  m->t0 = t0;
+  const double G = fs * (F / c - t0);
+  if (ks * dmin + G - m->cut < 0 || ks * dmax + G + m->cut >= nt) return OAM_ERR_WINDOW;
+  m->G = G;
+
+  // bands [lo, hi) per (orbit, depth)
+  m->h_band_lo.resize((size_t)O * nz);
+  m->h_band_hi.resize((size_t)O * nz);
+  int wmax = 1;
+  m->n_lo = nt;
+  m->n_hi = 0;
+  for (size_t i = 0; i < h_range.size(); ++i) {
+    int lo = (int)std::ceil(ks * h_range[i].x + G - m->cut) - widen;
+    int hi = (int)std::floor(ks * h_range[i].y + G + m->cut) + 1 + widen;
+    lo = std::max(lo, 0);
+    hi = std::min(hi, nt);
+    if (hi < lo) hi = lo;
+    m->h_band_lo[i] = lo;
+    m->h_band_hi[i] = hi;
+    wmax = std::max(wmax, hi - lo);
+    if (hi > lo) {
+      m->n_lo = std::min(m->n_lo, lo);
+      m->n_hi = std::max(m->n_hi, hi);
+    }
+  }
+  m->band_w = (wmax + 3) & ~3;
+  if (m->band_w > 512) return OAM_ERR_UNSUPPORTED;
+
+  // algorithmic work: entries in bands, and multiply-adds over in-grid voxel/position pairs
+  std::vector<long long> orb_sum(O, 0);
+  for (int o = 0; o < O; ++o)
+    for (int k = 0; k < nz; ++k) orb_sum[o] += m->h_band_hi[(size_t)o * nz + k] - m->h_band_lo[(size_t)o * nz + k];
+  long long nnz = 0;
+  double fl = 0;
+  for (int b = -m->R; b <= m->R; ++b)
+    for (int a = -m->R; a <= m->R; ++a) {
+      long long sum = orb_sum[m->h_tap_orbit[(b + m->R) * m->W + (a + m->R)]];
+      nnz += sum;
+      long long pairs = (long long)std::max(0, gr.py - std::abs(b)) * std::max(0, gr.px - std::abs(a));
+      fl += 2.0 * (double)pairs * (double)sum;
+    }
+  m->nnz = nnz;
+  m->flops = fl;
+  return OAM_OK;
+}
+
+// FP32 forward layout: per (orbit, 64-sample time tile) the depths [klo, khi)
+// whose band meets the tile, rows of kTimeTile samples.  Returns the floats.
+long long oam::fwd_layout(const oam_model *m, std::vector<int> *kr, std::vector<long long> *off) {
+  const int nz = m->grid.nz, O = m->n_orb, NT = (m->grid.nt + kTimeTile - 1) / kTimeTile;
+  kr->assign((size_t)O * NT * 2, 0);
+  off->assign((size_t)O * NT, 0);
+  long long total = 0;
+  for (int o = 0; o < O; ++o)
+    for (int T = 0; T < NT; ++T) {
+      int klo = nz, khi = 0;
+      for (int k = 0; k < nz; ++k) {
+        int lo = m->h_band_lo[(size_t)o * nz + k], hi = m->h_band_hi[(size_t)o * nz + k];
+        if (hi > lo && lo < (T + 1) * kTimeTile && hi > T * kTimeTile) {
+          klo = std::min(klo, k);
+          khi = std::max(khi, k + 1);
+        }
+      }
+      if (khi <= klo) klo = khi = 0;
+      size_t i = (size_t)o * NT + T;
+      (*kr)[2 * i] = klo;
+      (*kr)[2 * i + 1] = khi;
+      (*off)[i] = total;
+      total += (long long)(khi - klo) * kTimeTile;
+    }
+  return total;
+}
+
+// FP32 adjoint layout: per (orbit, 16-depth tile) the union sample range
+// [nlo, nlo + nlen), 4-aligned, rows of nlen samples.  Returns the floats.
+long long oam::adj_layout(const oam_model *m, std::vector<int> *nr, std::vector<long long> *off) {
+  const int nz = m->grid.nz, nt = m->grid.nt, O = m->n_orb, NK = (nz + kDepthTile - 1) / kDepthTile;
+  nr->assign((size_t)O * NK * 2, 0);
+  off->assign((size_t)O * NK, 0);
+  long long total = 0;
+  for (int o = 0; o < O; ++o)
+    for (int K = 0; K < NK; ++K) {
+      int nlo = nt, nhi = 0;
+      for (int k = K * kDepthTile; k < std::min(nz, (K + 1) * kDepthTile); ++k) {
+        int lo = m->h_band_lo[(size_t)o * nz + k], hi = m->h_band_hi[(size_t)o * nz + k];
+        if (hi > lo) {
+          nlo = std::min(nlo, lo);
+          nhi = std::max(nhi, hi);
+        }
+      }
+      if (nhi <= nlo) {
+        nlo = 0;
+        nhi = 0;
+      }
+      nlo &= ~3;
+      nhi = std::min((nhi + 3) & ~3, nt);
+      size_t i = (size_t)o * NK + K;
+      (*nr)[2 * i] = nlo;
+      (*nr)[2 * i + 1] = nhi - nlo;
+      (*off)[i] = total;
+      total += (long long)kDepthTile * (nhi - nlo);
+    }
+  return total;
+}
+
+// Device bytes build_slab allocates for a model whose bands are planned.
+size_t oam::slab_plan_bytes(const oam_model *m) {
+  const size_t O = m->n_orb, nz = m->grid.nz;
+  std::vector<int> iv;
+  std::vector<long long> lv;
+  const size_t NT = (m->grid.nt + kTimeTile - 1) / kTimeTile, NK = (nz + kDepthTile - 1) / kDepthTile;
+  size_t b = alloc_bytes<int>((size_t)m->W * m->W) + alloc_bytes<int>(O * nz) + alloc_bytes<float>(O * nz * m->band_w);
+  b += alloc_bytes<int>(O * NT * 2) + alloc_bytes<long long>(O * NT) + alloc_bytes<float>(fwd_layout(m, &iv, &lv));
+  b += alloc_bytes<int>(O * NK * 2) + alloc_bytes<long long>(O * NK) + alloc_bytes<float>(adj_layout(m, &iv, &lv));
+  return b;
+}
+
 oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
   const oam_grid &gr = m->grid;
   const int nz = gr.nz, nt = gr.nt, O = m->n_orb;
@@ -348,65 +480,15 @@ oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
   OAM_CUDA_TRY(cudaMemcpyAsync(h_range.data(), d_range, sizeof(double2) * O * nz, cudaMemcpyDeviceToHost, st));
   OAM_CUDA_TRY(cudaStreamSynchronize(st));
 
-  // time origin and window check
-  double dmin = INFINITY, dmax = -INFINITY;
-  for (const double2 &r : h_range) {
-    dmin = std::min(dmin, r.x);
-    dmax = std::max(dmax, r.y);
-  }
-  const double fs = gr.fs_hz, c = m->sensor.c_mps, F = m->sensor.focal_m;
-  const double t0 = std::isnan(gr.t0_s) ? (std::floor(fs * (F + dmin) / c - m->cut) - 2.0) / fs : gr.t0_s;
-  m->t0 = t0;
-  g.G = fs * (F / c - t0);
-  if (g.ks * dmin + g.G - m->cut < 0 || g.ks * dmax + g.G + m->cut >= nt) {
+  rc = plan_bands(m, h_range, 0);
+  if (rc) {
     cudaFreeAsync(d_orb_b, st);
     cudaFreeAsync(d_orb_a, st);
     cudaFreeAsync(d_range, st);
     cudaFreeAsync(d_pdw, st);
-    return OAM_ERR_WINDOW;
+    return rc;
   }
-  m->G = g.G;
-
-  // bands [lo, hi) per (orbit, depth)
-  m->h_band_lo.resize((size_t)O * nz);
-  m->h_band_hi.resize((size_t)O * nz);
-  int wmax = 1;
-  m->n_lo = nt;
-  m->n_hi = 0;
-  for (size_t i = 0; i < h_range.size(); ++i) {
-    int lo = (int)std::ceil(g.ks * h_range[i].x + g.G - m->cut);
-    int hi = (int)std::floor(g.ks * h_range[i].y + g.G + m->cut) + 1;
-    lo = std::max(lo, 0);
-    hi = std::min(hi, nt);
-    if (hi < lo) hi = lo;
-    m->h_band_lo[i] = lo;
-    m->h_band_hi[i] = hi;
-    wmax = std::max(wmax, hi - lo);
-    if (hi > lo) {
-      m->n_lo = std::min(m->n_lo, lo);
-      m->n_hi = std::max(m->n_hi, hi);
-    }
-  }
-  m->band_w = (wmax + 3) & ~3;
-  if (m->band_w > 512) return OAM_ERR_UNSUPPORTED;
-
-  // algorithmic work: entries in bands, and multiply-adds over in-grid voxel/position pairs
-  {
-    std::vector<long long> orb_sum(O, 0);
-    for (int o = 0; o < O; ++o)
-      for (int k = 0; k < nz; ++k) orb_sum[o] += m->h_band_hi[(size_t)o * nz + k] - m->h_band_lo[(size_t)o * nz + k];
-    long long nnz = 0;
-    double fl = 0;
-    for (int b = -m->R; b <= m->R; ++b)
-      for (int a = -m->R; a <= m->R; ++a) {
-        long long s = orb_sum[m->h_tap_orbit[(b + m->R) * m->W + (a + m->R)]];
-        nnz += s;
-        long long pairs = (long long)std::max(0, gr.py - std::abs(b)) * std::max(0, gr.px - std::abs(a));
-        fl += 2.0 * (double)pairs * (double)s;
-      }
-    m->nnz = nnz;
-    m->flops = fl;
-  }
+  g.G = m->G;
 
   int *d_band_hi = nullptr;
   if ((rc = dev_alloc(m, &m->d_band_lo, (size_t)O * nz))) return rc;
@@ -424,26 +506,9 @@ oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
   m->n_ttiles = (nt + kTimeTile - 1) / kTimeTile;
   {
     const int NT = m->n_ttiles;
-    std::vector<int> kr((size_t)O * NT * 2, 0);
-    std::vector<long long> off((size_t)O * NT, 0);
-    long long total = 0;
-    for (int o = 0; o < O; ++o)
-      for (int T = 0; T < NT; ++T) {
-        int klo = nz, khi = 0;
-        for (int k = 0; k < nz; ++k) {
-          int lo = m->h_band_lo[(size_t)o * nz + k], hi = m->h_band_hi[(size_t)o * nz + k];
-          if (hi > lo && lo < (T + 1) * kTimeTile && hi > T * kTimeTile) {
-            klo = std::min(klo, k);
-            khi = std::max(khi, k + 1);
-          }
-        }
-        if (khi <= klo) klo = khi = 0;
-        size_t i = (size_t)o * NT + T;
-        kr[2 * i] = klo;
-        kr[2 * i + 1] = khi;
-        off[i] = total;
-        total += (long long)(khi - klo) * kTimeTile;
-      }
+    std::vector<int> kr;
+    std::vector<long long> off;
+    const long long total = fwd_layout(m, &kr, &off);
     if ((rc = dev_alloc(m, &m->d_fwd_krange, kr.size()))) return rc;
     if ((rc = dev_alloc(m, &m->d_fwd_off, off.size()))) return rc;
     if ((rc = dev_alloc(m, &m->d_fwd, (size_t)total))) return rc;
@@ -458,31 +523,9 @@ oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
   m->n_ktiles = (nz + kDepthTile - 1) / kDepthTile;
   {
     const int NK = m->n_ktiles;
-    std::vector<int> nr((size_t)O * NK * 2, 0);
-    std::vector<long long> off((size_t)O * NK, 0);
-    long long total = 0;
-    for (int o = 0; o < O; ++o)
-      for (int K = 0; K < NK; ++K) {
-        int nlo = nt, nhi = 0;
-        for (int k = K * kDepthTile; k < std::min(nz, (K + 1) * kDepthTile); ++k) {
-          int lo = m->h_band_lo[(size_t)o * nz + k], hi = m->h_band_hi[(size_t)o * nz + k];
-          if (hi > lo) {
-            nlo = std::min(nlo, lo);
-            nhi = std::max(nhi, hi);
-          }
-        }
-        if (nhi <= nlo) {
-          nlo = 0;
-          nhi = 0;
-        }
-        nlo &= ~3;
-        nhi = std::min((nhi + 3) & ~3, nt);
-        size_t i = (size_t)o * NK + K;
-        nr[2 * i] = nlo;
-        nr[2 * i + 1] = nhi - nlo;
-        off[i] = total;
-        total += (long long)kDepthTile * (nhi - nlo);
-      }
+    std::vector<int> nr;
+    std::vector<long long> off;
+    const long long total = adj_layout(m, &nr, &off);
     if ((rc = dev_alloc(m, &m->d_adj_nrange, nr.size()))) return rc;
     if ((rc = dev_alloc(m, &m->d_adj_off, off.size()))) return rc;
     if ((rc = dev_alloc(m, &m->d_adj, (size_t)total))) return rc;

@@ -321,3 +321,22 @@ def test_fft_form_rejects_grids_beyond_its_transform_size():
     with pytest.raises(B.OamError) as e:
         Model(configs.scaled(C0, px=2100, py=2, nz=4, nt=128, win=3, n_patches=200), precision=B.OAM_PREC_FFT)
     assert e.value.code == B.OAM_ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------------ pre-build footprint
+@pytest.mark.parametrize("prec", PRECS)
+def test_model_bytes_bounds_the_built_model(prec):
+    """oam_model_bytes (host only, before any allocation) is an upper bound
+    of the built model's device memory, within a few per cent."""
+    cases = [C0, RAGGED, configs.batch_job(1000), configs.batch_job(1003), C1]
+    for cfg in cases:
+        try:
+            m = Model(cfg, precision=prec)
+        except B.OamError as e:
+            if e.code == B.OAM_ERR_WINDOW:  # such a job moves to the next sample count
+                continue
+            raise
+        planned = B.oam_model_bytes(cfg, prec)
+        built = m.info.device_bytes
+        m.close()
+        assert built <= planned <= 1.15 * built + (1 << 20), (cfg["py"], cfg["nz"], built, planned)

@@ -219,7 +219,7 @@ def test_server_budget_failure_and_timeout():
     assert B.oam_server_wait(srv, rid, 60.0) == B.OAM_ERR_OOM  # can never fit the budget
     B.oam_server_stop(srv)
 
-    need = max(B.oam_request_footprint(B.OAM_PREC_BF16X3, B.structs_from_config(c)[1]) for c, _ in reqs)
+    need = max(B.oam_request_footprint(B.OAM_PREC_BF16X3, *B.structs_from_config(c)) for c, _ in reqs)
     srv = _server(budget=int(need * 1.5), slots=2, iters=(40, 30, 10))
     outs, bufs = [], []  # host outputs must outlive their requests
     for cfg, s in reqs:
