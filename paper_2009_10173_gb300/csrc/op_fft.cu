@@ -42,14 +42,16 @@ struct FftLayout {
   int NS = 0;                 // support length n_hi - n_lo
   int C = 0;                  // max(nz, NS): channels of the work buffers
   long long row_len = 0;      // sum_k klen_k: entries of one orbit row of S^
+  long long row_stride = 0;   // row_len rounded up to 4 floats: each row starts on a 16-byte boundary
   int *d_klo = nullptr, *d_klen = nullptr;  // [nz] union band per depth (absolute samples)
   long long *d_koff = nullptr;              // [nz] offset of depth k in an orbit row
   int4 *d_members = nullptr;                // [n_rep] half-spectrum indices u*P + v (-1 unused)
   int2 *d_krange = nullptr;                 // [NS] depths [x, y) whose band can hold sample n_lo + j
   long long *d_noff = nullptr;              // [NS] offset of sample n_lo + j in a transposed orbit row
   long long row_len_t = 0;                  // sum_j (krange_j.y - krange_j.x)
-  float *d_shat_t = nullptr;                // [n_rep][row_len_t]: S^ by sample, depths krange_j (adjoint)
-  float *d_shat = nullptr;                  // [n_rep][row_len]
+  long long row_stride_t = 0;               // row_len_t rounded up to 4 floats
+  float *d_shat_t = nullptr;                // [n_rep][row_stride_t]: S^ by sample, depths krange_j (adjoint)
+  float *d_shat = nullptr;                  // [n_rep][row_stride]
   float2 *d_w1 = nullptr, *d_w2 = nullptr;  // [Q][P][C] work buffers
   double flops = 0;                         // flops of one application (matrix part + FFTs)
   double bytes = 0;                         // device bytes read + written per application
@@ -66,7 +68,7 @@ constexpr int kApplyMaxThreads = 1024;
 constexpr int kUnroll = 8;  // spectral products: independent row loads per lane in flight
 constexpr int kFwdPhases = 2;  // forward products: lane groups of a warp that walk interleaved depths
 constexpr int kFwdChunk = 256;  // forward products: samples per block (0: all samples of the orbit)
-constexpr int kAdjChunk = 128;  // adjoint products: depths per block (0: all depths of the orbit)
+constexpr int kAdjChunk = 160;  // adjoint products: depths per block (0: all depths of the orbit)
 constexpr int kBuildThreads = 128;
 
 
@@ -628,8 +630,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_shat_pass2(const float *__res
                                                               const int2 *__restrict__ entry_kn, int n_lo,
                                                               const int2 *__restrict__ krange,
                                                               const long long *__restrict__ noff,
-                                                              long long row_len_t, float *__restrict__ shat,
-                                                              float *__restrict__ shat_t) {
+                                                              long long stride, long long stride_t,
+                                                              float *__restrict__ shat, float *__restrict__ shat_t) {
   extern __shared__ float smb[];
   float *cosT = smb;    // [P]
   float *tv = smb + P;  // [R+1][blockDim]
@@ -651,8 +653,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_shat_pass2(const float *__res
     if (r < 0) continue;
     float acc = 0.0f;
     for (int bp = 0; bp <= R; ++bp) acc = fmaf(cosT[(v0 * bp) & (P - 1)], tv[bp * ts + tid], acc);
-    shat[(size_t)r * row_len + e] = acc;
-    shat_t[(size_t)r * row_len_t + et] = acc;
+    shat[(size_t)r * stride + e] = acc;
+    shat_t[(size_t)r * stride_t + et] = acc;
   }
 }
 
@@ -713,6 +715,7 @@ oam_status fft_plan(const oam_model *m, FftLayout *L, FftPlan &pl) {
     row += hi - lo;
   }
   L->row_len = std::max<long long>(row, 1);
+  L->row_stride = (L->row_len + 3) & ~3LL;
   L->NS = std::max(1, m->n_hi - m->n_lo);
   std::vector<int2> &krange = pl.krange;
   krange.assign(L->NS, make_int2(0, 0));
@@ -734,6 +737,7 @@ oam_status fft_plan(const oam_model *m, FftLayout *L, FftPlan &pl) {
     rowt += krange[j].y - krange[j].x;
   }
   L->row_len_t = std::max<long long>(rowt, 1);
+  L->row_stride_t = (L->row_len_t + 3) & ~3LL;
   L->C = std::max(nz, L->NS);
   std::vector<int2> &entry_kn = pl.entry_kn;
   entry_kn.assign((size_t)L->row_len, make_int2(0, 0));
@@ -768,7 +772,7 @@ oam_status fft_plan(const oam_model *m, FftLayout *L, FftPlan &pl) {
 oam_status fft_layout_bytes(const FftLayout &L, const FftPlan &pl, int nz, size_t *bytes) {
   *bytes = alloc_bytes<int>(nz) * 2 + alloc_bytes<long long>(nz) + alloc_bytes<int4>(pl.members.size()) +
            alloc_bytes<int2>(L.NS) + alloc_bytes<long long>(L.NS) +
-           alloc_bytes<float>((size_t)L.n_rep * L.row_len_t) + alloc_bytes<float>((size_t)L.n_rep * L.row_len) +
+           alloc_bytes<float>((size_t)L.n_rep * L.row_stride_t) + alloc_bytes<float>((size_t)L.n_rep * L.row_stride) +
            2 * alloc_bytes<float2>((size_t)L.Q * L.P * L.C);
   return OAM_OK;
 }
@@ -802,8 +806,8 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
   if ((rc = dev_alloc(m, &L->d_klo, nz)) || (rc = dev_alloc(m, &L->d_klen, nz)) ||
       (rc = dev_alloc(m, &L->d_koff, nz)) || (rc = dev_alloc(m, &L->d_members, members.size())) ||
       (rc = dev_alloc(m, &L->d_krange, (size_t)L->NS)) || (rc = dev_alloc(m, &L->d_noff, (size_t)L->NS)) ||
-      (rc = dev_alloc(m, &L->d_shat_t, (size_t)L->n_rep * L->row_len_t)) ||
-      (rc = dev_alloc(m, &L->d_shat, (size_t)L->n_rep * L->row_len)) ||
+      (rc = dev_alloc(m, &L->d_shat_t, (size_t)L->n_rep * L->row_stride_t)) ||
+      (rc = dev_alloc(m, &L->d_shat, (size_t)L->n_rep * L->row_stride)) ||
       (rc = dev_alloc(m, &L->d_w1, (size_t)Q * P * L->C)) || (rc = dev_alloc(m, &L->d_w2, (size_t)Q * P * L->C)))
     return rc;
   OAM_CUDA_TRY(cudaMemcpyAsync(L->d_klo, klo.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, st));
@@ -814,7 +818,7 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
   OAM_CUDA_TRY(cudaMemcpyAsync(L->d_krange, krange.data(), sizeof(int2) * krange.size(), cudaMemcpyHostToDevice, st));
   OAM_CUDA_TRY(cudaMemcpyAsync(L->d_noff, noff.data(), sizeof(long long) * noff.size(), cudaMemcpyHostToDevice, st));
   // entries of the row by sample whose depth band misses the sample stay zero
-  OAM_CUDA_TRY(cudaMemsetAsync(L->d_shat_t, 0, sizeof(float) * (size_t)L->n_rep * L->row_len_t, st));
+  OAM_CUDA_TRY(cudaMemsetAsync(L->d_shat_t, 0, sizeof(float) * (size_t)L->n_rep * L->row_stride_t, st));
   // build S^ (temporaries: entry table, band_hi, rep table, T)
   int2 *d_entry = nullptr;
   int *d_band_hi = nullptr, *d_rep_of = nullptr;
@@ -844,7 +848,7 @@ oam_status oam::fft_build(oam_model *m, cudaStream_t st) {
       m->d_band, m->d_band_lo, d_band_hi, m->band_w, m->d_tap_orbit, R, W, nz, d_entry, L->row_len, P, Q, d_T);
   OAM_LAUNCHED();
   k_shat_pass2<<<dim3(eblocks, Q), kBuildThreads, sb, st>>>(d_T, L->row_len, R, P, Q, d_rep_of, d_entry, m->n_lo,
-                                                            L->d_krange, L->d_noff, L->row_len_t, L->d_shat,
+                                                            L->d_krange, L->d_noff, L->row_stride, L->row_stride_t, L->d_shat,
                                                             L->d_shat_t);
   OAM_LAUNCHED();
   OAM_CUDA_TRY(cudaStreamSynchronize(st));  // host tables above go out of scope
@@ -969,7 +973,7 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     const int fchunk = kFwdChunk > 0 ? kFwdChunk : NS;
     const int fwd_threads = std::min(kApplyMaxThreads, 32 * ((fchunk + 32 / kFwdPhases - 1) / (32 / kFwdPhases)));
     const unsigned fblocks = (unsigned)(L->n_rep * ((NS + fchunk - 1) / fchunk));
-    k_fft_apply_fwd<<<fblocks, fwd_threads, sa, st>>>(L->d_shat, L->row_len, L->d_members, L->d_klo, L->d_klen,
+    k_fft_apply_fwd<<<fblocks, fwd_threads, sa, st>>>(L->d_shat, L->row_stride, L->d_members, L->d_klo, L->d_klen,
                                                       L->d_koff, L->d_krange, nz, m->n_lo, NS, L->d_w1, L->d_w2);
     OAM_LAUNCHED();
     K::cols(dim3(Q, cbs), st, L->d_w2, P, py, NS, P, lgP, 1, L->d_w1);
@@ -987,7 +991,7 @@ oam_status run_fft(const oam_model *m, const FftLayout *L, bool fwd, const float
     const int achunk = kAdjChunk > 0 ? kAdjChunk : nz;
     const int adj_threads = std::min(kApplyMaxThreads, 32 * ((achunk + 15) / 16));
     const unsigned ablocks = (unsigned)(L->n_rep * ((nz + achunk - 1) / achunk));
-    k_fft_apply_adj<<<ablocks, adj_threads, sa, st>>>(L->d_shat_t, L->row_len_t, L->d_members, L->d_klo, L->d_klen,
+    k_fft_apply_adj<<<ablocks, adj_threads, sa, st>>>(L->d_shat_t, L->row_stride_t, L->d_members, L->d_klo, L->d_klen,
                                                       L->d_krange, L->d_noff, nz, m->n_lo, NS, L->d_w1, L->d_w2);
     OAM_LAUNCHED();
     K::cols(dim3(Q, cbz), st, L->d_w2, P, py, nz, P, lgP, 1, L->d_w1);
