@@ -235,11 +235,13 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 128-byte-swizzled TMA destinations need 1024-byte alignment
   uint8_t *smem = smem_raw + ((1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
-  const int K = p.n_items;  // item ring: slab tile in shared memory + folded operand in tensor memory
+  // item ring: slab tile in shared memory + folded operand in tensor memory;
+  // items go in pairs (the two taps of one fold pass), one set of barriers per pair
+  const int K = p.n_items, KP = K / 2;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
   uint64_t *strip_full = bars, *strip_empty = bars + 2;
   uint64_t *acc_ready = bars + 4, *acc_full = bars + 5;
-  uint64_t *slab_full = bars + 6, *fold_full = bars + 6 + K, *item_empty = bars + 6 + 2 * K;
+  uint64_t *slab_full = bars + 6, *fold_full = bars + 6 + KP, *item_empty = bars + 6 + 2 * KP;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 512);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 516);
   volatile int *never = reinterpret_cast<volatile int *>(smem + 520);  // stays 0: waits that ignore abort
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
     }
     ptx::mbar_init(acc_ready, kFoldWarps);
     ptx::mbar_init(acc_full, 1);
-    for (int i = 0; i < K; ++i) {
+    for (int i = 0; i < KP; ++i) {
       ptx::mbar_init(&slab_full[i], 1);
       ptx::mbar_init(&fold_full[i], kFoldWarps);
       ptx::mbar_init(&item_empty[i], 1);
@@ -302,41 +304,57 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
       bool ok = true;
       const int q_p = (int)((long long)(R + 1) * p.wp + (long long)tile * kTileM + (long long)b * p.wp - R);
       const int q_m = (int)((long long)(R + 1) * p.wp + (long long)tile * kTileM - (long long)b * p.wp - R);
-      for (int st = 0; st < p.stages && ok; ++st) {
-        const int s = it_strip & 1;
-        if (!ptx::mbar_wait(&strip_empty[s], ((it_strip >> 1) & 1) ^ 1, abort_flag, p.budget)) {
-          fail(1);
-          ok = false;
-          break;
-        }
+      // Stage st's row pair goes into strip slot st & 1, whose previous stage
+      // (st - 2) the fold warps must have released.  The pair for stage st + 1
+      // is requested right after stage st's first slab tile, about a stage
+      // ahead of its use, instead of after stage st's last tile (which the
+      // item ring throttles to just before the fold warps need the rows).
+      auto load_strips = [&](int stage) {
+        const int s = stage & 1;
+        if (!ptx::mbar_wait(&strip_empty[s], ((stage >> 1) & 1) ^ 1, abort_flag, p.budget)) return false;
         ptx::mbar_arrive_expect_tx(&strip_full[s], (uint32_t)(n_rows * L * 128));
         uint8_t *dst = strips + (size_t)s * 2 * p.strip_bytes;
-        tma_load_2d(dst, &tmap, kStageK * st, q_p, &strip_full[s]);
-        if (n_rows == 2) tma_load_2d(dst + p.strip_bytes, &tmap, kStageK * st, q_m, &strip_full[s]);
+        tma_load_2d(dst, &tmap, kStageK * stage, q_p, &strip_full[s]);
+        if (n_rows == 2) tma_load_2d(dst + p.strip_bytes, &tmap, kStageK * stage, q_m, &strip_full[s]);
         ++it_strip;
+        return true;
+      };
+      if (!load_strips(0)) {
+        fail(1);
+        ok = false;
+      }
+      for (int st = 0; st < p.stages && ok; ++st) {
         const TcItem *row_items = sitems + st * NA;
-        for (int a = 0; a < NA; ++a) {
-          const TcItem item = row_items[a];
+        for (int a = 0; a < NA; a += 2) {  // pair slot k holds items a (slot 2k) and a + 1 (slot 2k + 1)
+          const TcItem ia = row_items[a], ib = a + 1 < NA ? row_items[a + 1] : TcItem{};
           if (!ptx::mbar_wait(&item_empty[k], lap ^ 1, abort_flag, p.budget)) {
             fail(2);
             ok = false;
             break;
           }
-          ptx::mbar_arrive_expect_tx(&slab_full[k], item.bytes);
-          if (item.bytes > 0)
-            ptx::bulk_g2s(slots + (size_t)k * p.slot_bytes, p.data + (size_t)item.off16 * 16, item.bytes,
+          ptx::mbar_arrive_expect_tx(&slab_full[k], ia.bytes + ib.bytes);
+          if (ia.bytes > 0)
+            ptx::bulk_g2s(slots + (size_t)(2 * k) * p.slot_bytes, p.data + (size_t)ia.off16 * 16, ia.bytes,
+                          &slab_full[k]);
+          if (ib.bytes > 0)
+            ptx::bulk_g2s(slots + (size_t)(2 * k + 1) * p.slot_bytes, p.data + (size_t)ib.off16 * 16, ib.bytes,
                           &slab_full[k]);
           ++it_slab;
-          if (++k == K) {
+          if (++k == KP) {
             k = 0;
             lap ^= 1;
+          }
+          if (a == 0 && st + 1 < p.stages && !load_strips(st + 1)) {
+            fail(1);
+            ok = false;
+            break;
           }
         }
       }
       if (!ok) {
         // let copies already issued land before the block exits
-        for (int i = std::max(0, it_slab - K); i < it_slab; ++i)
-          ptx::mbar_wait(&slab_full[i % K], (i / K) & 1, never, p.budget);
+        for (int i = std::max(0, it_slab - KP); i < it_slab; ++i)
+          ptx::mbar_wait(&slab_full[i % KP], (i / KP) & 1, never, p.budget);
         for (int i = std::max(0, it_strip - 2); i < it_strip; ++i)
           ptx::mbar_wait(&strip_full[i & 1], (i >> 1) & 1, never, p.budget);
       }
@@ -357,7 +375,7 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
     const uint32_t idesc_m128 = ptx::idesc_bf16_f32(kTileM, 0);
     for (int st = 0; st < p.stages && ok && !skip; ++st) {
       const TcItem *row_items = sitems + st * NA;
-      for (int a = 0; a < NA; ++a) {
+      for (int a = 0; a < NA; a += 2) {
         bool w = ptx::mbar_wait(&slab_full[k], lap, abort_flag, p.budget);
         if (w) w = ptx::mbar_wait(&fold_full[k], lap, abort_flag, p.budget);
         if (!__all_sync(0xffffffffu, w)) {
@@ -366,27 +384,30 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
           break;
         }
         ptx::tc_fence_after();
-        const TcItem item = row_items[a];
-        const uint32_t a_base = tmem + (uint32_t)(p.fold_col0 + 32 * k);
-        const uint64_t dB = slot_desc + (uint64_t)(((uint32_t)k * (uint32_t)p.slot_bytes) >> 4);
-        const uint32_t n0 = item.n[0], n1 = item.n[1];
-        const uint64_t b0h = dB + ((uint64_t)n0 << 16), b0l = b0h + 2u * n0;  // lbo = 16 n bytes; lo 32 n bytes on
-        const uint64_t dB1 = dB + 4u * n0;                                   // second tile 64 n0 bytes later
-        const uint64_t b1h = dB1 + ((uint64_t)n1 << 16), b1l = b1h + 2u * n1;
-        const uint32_t i0 = idesc_m128 | ((n0 >> 3) << 17), i1 = idesc_m128 | ((n1 >> 3) << 17);
-        const uint32_t d0 = tmem + item.col[0], d1 = tmem + item.col[1];
-        if (leader) {
-          // the two chunks accumulate into different columns: interleave them
-          if (n0) ptx::mma_bf16_ta(d0, a_base, b0h, i0, 1);
-          if (n1) ptx::mma_bf16_ta(d1, a_base + 16u, b1h, i1, 1);
-          if (n0) ptx::mma_bf16_ta(d0, a_base + 8u, b0h, i0, 1);
-          if (n1) ptx::mma_bf16_ta(d1, a_base + 24u, b1h, i1, 1);
-          if (n0) ptx::mma_bf16_ta(d0, a_base, b0l, i0, 1);
-          if (n1) ptx::mma_bf16_ta(d1, a_base + 16u, b1l, i1, 1);
-          ptx::mma_commit(&item_empty[k]);
+        for (int h = 0; h < 2 && a + h < NA; ++h) {
+          const TcItem item = row_items[a + h];
+          const uint32_t slot = (uint32_t)(2 * k + h);
+          const uint32_t a_base = tmem + (uint32_t)p.fold_col0 + 32u * slot;
+          const uint64_t dB = slot_desc + (uint64_t)((slot * (uint32_t)p.slot_bytes) >> 4);
+          const uint32_t n0 = item.n[0], n1 = item.n[1];
+          const uint64_t b0h = dB + ((uint64_t)n0 << 16), b0l = b0h + 2u * n0;  // lbo = 16 n bytes; lo 32 n bytes on
+          const uint64_t dB1 = dB + 4u * n0;                                   // second tile 64 n0 bytes later
+          const uint64_t b1h = dB1 + ((uint64_t)n1 << 16), b1l = b1h + 2u * n1;
+          const uint32_t i0 = idesc_m128 | ((n0 >> 3) << 17), i1 = idesc_m128 | ((n1 >> 3) << 17);
+          const uint32_t d0 = tmem + item.col[0], d1 = tmem + item.col[1];
+          if (leader) {
+            // the two chunks accumulate into different columns: interleave them
+            if (n0) ptx::mma_bf16_ta(d0, a_base, b0h, i0, 1);
+            if (n1) ptx::mma_bf16_ta(d1, a_base + 16u, b1h, i1, 1);
+            if (n0) ptx::mma_bf16_ta(d0, a_base + 8u, b0h, i0, 1);
+            if (n1) ptx::mma_bf16_ta(d1, a_base + 24u, b1h, i1, 1);
+            if (n0) ptx::mma_bf16_ta(d0, a_base, b0l, i0, 1);
+            if (n1) ptx::mma_bf16_ta(d1, a_base + 16u, b1l, i1, 1);
+          }
         }
+        if (leader) ptx::mma_commit(&item_empty[k]);  // the pair's slots are free once its MMAs complete
         __syncwarp();
-        if (++k == K) {
+        if (++k == KP) {
           k = 0;
           lap ^= 1;
         }
@@ -439,38 +460,28 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
           }
           asm volatile("bar.sync 1, %0;" ::"r"(32 * kFoldWarps) : "memory");  // fold warps only
         }
-        // two items (a, a + 1) per pass: one wait, fence and barrier step for both
+        // two items (a, a + 1) per pass, in pair slot k: one wait, fence and barrier step for both
         for (int a = 0; a < NA; a += 2) {
           const bool two = a + 1 < NA;
-          const bool wrap = k + 1 == p.n_items;
-          const int k1 = wrap ? 0 : k + 1;
-          const uint32_t lap1 = wrap ? lap ^ 1 : lap;
+          uint32_t w0[E], w1[E];  // folded in registers while the pair slot may still be in use
+          fold_item<E>(X1, m, R, a, q0, w0);
+          if (two) fold_item<E>(X1, m, R, a + 1, q0, w1);
           ok = ptx::mbar_wait(&item_empty[k], lap ^ 1, abort_flag, p.budget);
-          if (ok && two) ok = ptx::mbar_wait(&item_empty[k1], lap1 ^ 1, abort_flag, p.budget);
           ok = __all_sync(0xffffffffu, ok);
           if (!ok) {
             if (lane == 0) fail(64);
             break;
           }
-          uint32_t w0[E], w1[E];
-          fold_item<E>(X1, m, R, a, q0, w0);
-          if (two) fold_item<E>(X1, m, R, a + 1, q0, w1);
-          store_item<E>(tmem + lane_base + (uint32_t)(p.fold_col0 + 32 * k), q0, w0);
-          if (two) store_item<E>(tmem + lane_base + (uint32_t)(p.fold_col0 + 32 * k1), q0, w1);
+          const uint32_t fa = tmem + lane_base + (uint32_t)p.fold_col0 + 64u * (uint32_t)k;
+          store_item<E>(fa, q0, w0);
+          if (two) store_item<E>(fa + 32u, q0, w1);
           ptx::tmem_wait_st();
           ptx::tc_fence_before();
           __syncwarp();
-          if (lane == 0) {
-            ptx::mbar_arrive(&fold_full[k]);
-            if (two) ptx::mbar_arrive(&fold_full[k1]);
-          }
-          if (two) {
-            const bool wrap1 = k1 + 1 == p.n_items;
-            k = wrap1 ? 0 : k1 + 1;
-            lap = wrap1 ? lap1 ^ 1 : lap1;
-          } else {
-            k = k1;
-            lap = lap1;
+          if (lane == 0) ptx::mbar_arrive(&fold_full[k]);
+          if (++k == KP) {
+            k = 0;
+            lap ^= 1;
           }
         }
         __syncwarp();
@@ -769,6 +780,7 @@ oam_status plan_launch(const oam_model *m, const TcLayout *L, Launch *out) {
   const int tmem_items = (512 - p.fold_col0) / kFoldCols;
   p.n_items = std::min(kMaxItems, std::min(tmem_items, (kSmemLimit - fixed) / L->slot_bytes));
   if (L->ring_pref >= 2) p.n_items = std::min(p.n_items, L->ring_pref);
+  p.n_items &= ~1;  // items go in pairs (one fold pass each)
   if (p.n_items < 2) return OAM_ERR_UNSUPPORTED;
   p.acc_cols = L->acc_cols;
   p.tmem_cols = 32;
@@ -936,7 +948,7 @@ oam_status oam::tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_f
     int best = deepest, best_w = kDefaultFoldWarps;
     for (int fw : kFoldWarpChoices) {
       L->fold_warps = fw;
-      for (int depth = 2; depth <= deepest; depth += (depth < 4 ? 1 : 2)) {
+      for (int depth = 2; depth <= deepest; depth += 2) {
         L->ring_pref = depth;
         for (int r = 0; r <= reps && !rc; ++r) {  // first run warms up
           if (r == 1) cudaEventRecord(e0, st);
@@ -972,7 +984,7 @@ oam_status oam::tc_set_tiles(oam_model *m, int dir, int fold_warps, int ring) {
   if (!L) return OAM_ERR_UNSUPPORTED;
   bool okw = false;
   for (int fw : kFoldWarpChoices) okw = okw || fw == fold_warps;
-  if (!okw || ring < 0) return OAM_ERR_INVALID_ARG;
+  if (!okw || ring < 0 || (ring & 1)) return OAM_ERR_INVALID_ARG;
   const int keep_ring = L->ring_pref, keep_w = L->fold_warps;
   L->ring_pref = ring;
   L->fold_warps = fold_warps;
