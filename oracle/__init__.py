@@ -19,6 +19,10 @@ benchmark's CPU-baseline leg import this package; the product path
   the same two operators.
 * ``oracle.solvers``: LSQR for Eq. 5 with Eq. 6 (MB-L2) and FISTA for Eq. 5
   with Eq. 7 (MB-L1), written from the published algorithms the paper names.
+* ``tent_radon``, ``slab33_column``: the paper's own discretisation of Eq. 1
+  (trilinear interpolation of the voxel values for the surface integral, a
+  central finite difference for the time derivative), summed over the patches
+  of Eq. 3 and filtered by the sampled EIR.
 * ``oracle.bandpass``: the band-pass filtering of signals and model along
   time that precedes inversion in the Results (a windowed-sinc FIR, applied
   as a direct sum).
@@ -72,6 +76,9 @@ def lib():
         L.orc_adjoint_fft.argtypes = [dp, i32, i32, i32, i32, i32, i32, dp, dp]
         lp = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
         L.orc_depth_band.argtypes = [P, f64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.orc_tent_radon.argtypes = [f64] * 7
+        L.orc_tent_radon.restype = f64
+        L.orc_slab33_column.argtypes = [P, f64, i32, i32, i32, dp]
         L.orc_spectrum_depth.argtypes = [P, f64, i32, i32, i32, i32, i32, dp, dp]
         L.orc_forward_spec.argtypes = [dp, dp, ip, ip, lp, i32, i32, i32, i32, i32, i32, dp, dp]
         L.orc_adjoint_spec.argtypes = [dp, dp, ip, ip, lp, i32, i32, i32, i32, i32, i32, dp, dp]
@@ -79,7 +86,7 @@ def lib():
                   "orc_slab_column", "orc_slab", "orc_slab_time_slice", "orc_forward",
                   "orc_adjoint", "orc_forward_at", "orc_fft", "orc_slab_dft", "orc_forward_fft",
                   "orc_adjoint_fft", "orc_depth_band", "orc_spectrum_depth", "orc_forward_spec",
-                  "orc_adjoint_spec"):
+                  "orc_adjoint_spec", "orc_slab33_column"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -358,3 +365,20 @@ class Spectral:
         _check(lib().orc_adjoint_spec(self.re, self.im, self.klo, self.klen, self.koff, self.nz, self.nt,
                                       self.P, self.R, self.py, self.px, s, H))
         return H
+
+
+def tent_radon(d, e, s):
+    """Planar Radon transform of the trilinear tent with half-widths d = (dx,
+    dy, dz) along unit normal e at signed offsets s (any array)."""
+    L = lib()
+    return np.array([L.orc_tent_radon(d[0], d[1], d[2], e[0], e[1], e[2], float(x)) for x in np.ravel(s)])
+
+
+def slab33_column(cfg, b, a, k, t0_s=None):
+    """One column S33[b, a, k, :] of the discretised model (trilinear voxels,
+    finite-difference derivative, EIR at whole samples)."""
+    p = params(cfg)
+    t = t0(cfg) if t0_s is None else t0_s
+    out = np.zeros(p.nt)
+    _check(lib().orc_slab33_column(ctypes.byref(p), t, b, a, k, out))
+    return out

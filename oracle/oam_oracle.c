@@ -790,3 +790,113 @@ int orc_adjoint_spec(const double *re, const double *im, const int *klo, const i
   free(Sr); free(Si);
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The paper's own discretisation of Eq. 1 (Methods, Forward modeling, with  */
+/* its ref. [33]): the absorbed energy between voxel centres is the         */
+/* trilinear interpolation of the voxel values, i.e. each voxel carries the */
+/* tent phi(x) = L(x/dx) L(y/dy) L(z/dz), L(u) = max(0, 1 - |u|); the       */
+/* surface integral of Eq. 1 over the sphere |x - x'| = ct is taken of that */
+/* interpolant, and the time derivative by a central finite difference on   */
+/* the sample grid.                                                          */
+/*                                                                           */
+/* Over one tent's support (a few micrometres) the sphere of radius ct      */
+/* (millimetres) is a plane to within its sagitta (< 1e-3 voxel here), so    */
+/* the integral of the tent over the sphere is its planar Radon transform   */
+/*   R(s) = int phi(x) delta(e.x - s) dx                                     */
+/* along the unit normal e = (v - x)/|v - x| at s = ct - |v - x|.  Each     */
+/* factor L(x/dx) projects to a hat of half-width a = |e_x| dx and area dx, */
+/* a hat is (1/a) times the convolution of two boxes of width a, and the    */
+/* convolution of n boxes of widths c_i is                                   */
+/*   sum over sigma in {+-1}^n of prod(sigma) (s + sum sigma_i c_i / 2)_+^(n-1) / (n-1)! */
+/* (truncated powers).  An axis with a < 1e-3 max(a) (e nearly orthogonal to */
+/* it) projects to a spike of mass d, so its two boxes are dropped and its  */
+/* mass multiplies the rest (error ~ (a / max a)^2 < 1e-6).                  */
+/* ------------------------------------------------------------------------ */
+double orc_tent_radon(double dx, double dy, double dz, double ex, double ey, double ez, double s) {
+  const double d[3] = {dx, dy, dz}, e[3] = {fabs(ex), fabs(ey), fabs(ez)};
+  double a[3], amax = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    a[i] = e[i] * d[i];
+    if (a[i] > amax) amax = a[i];
+  }
+  double c[6], scale = 1.0;
+  int n = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (a[i] < 1e-3 * amax) {
+      scale *= d[i];  /* spike of mass d */
+    } else {
+      c[n++] = a[i];
+      c[n++] = a[i];
+      scale *= d[i] / (a[i] * a[i]);
+    }
+  }
+  double fact = 1.0; /* (n-1)! */
+  for (int i = 2; i < n; ++i) fact *= i;
+  double sum = 0.0;
+  for (int mask = 0; mask < (1 << n); ++mask) {
+    double x = s, sign = 1.0;
+    for (int i = 0; i < n; ++i) {
+      if (mask & (1 << i)) { x -= 0.5 * c[i]; sign = -sign; }
+      else x += 0.5 * c[i];
+    }
+    if (x > 0.0) sum += sign * pow(x, n - 1);
+  }
+  return scale * sum / fact;
+}
+
+/* One slab column of the discretised model, S33[b, a, k, 0..nt):            */
+/*   I_j(m)  = R_j(c t_m - r_j) / (c t_m),  t_m = t0 + m / fs  (r_j = |v - q_j|, */
+/*             lengths in mm; e_j the unit vector from patch j to the voxel) */
+/*   D_j(m)  = (I_j(m + 1) - I_j(m - 1)) / 2           (central difference)  */
+/*   S33(n)  = sum_j w_j sum_m e(n - m) D_j(m)          (EIR sampled at whole */
+/*             samples, e(tau) of the point model, zero beyond trunc_sigma)  */
+/* Arbitrary units as Eq. 2; for a tent much smaller than a wavelength and   */
+/* samples much finer than the tent it tends to (V fs / c) times the point-  */
+/* voxel column, V = dx dy dz the tent's volume.                             */
+int orc_slab33_column(const orc_params *p, double t0, int b, int a, int k, double *out) {
+  patchset ps;
+  int rc = load_patches(p, &ps);
+  if (rc) return rc;
+  double sg, om, cut;
+  eir_consts(p, &sg, &om, &cut);
+  const int T = (int)floor(cut);
+  const int nt = p->nt;
+  double *D = calloc((size_t)nt + 2, sizeof(double)); /* D[m + 1], m in [-1, nt] */
+  double *e = malloc(sizeof(double) * (2 * (size_t)T + 1));
+  if (!D || !e) { free(D); free(e); free(ps.nx); return ORC_ENOMEM; }
+  for (int m = -T; m <= T; ++m) e[m + T] = orc_eir(p, (double)m);
+  memset(out, 0, sizeof(double) * nt);
+  const double F = p->focal_m * 1e3, ddx = p->dx_m * 1e3, ddy = p->dy_m * 1e3, ddz = p->dz_m * 1e3;
+  const double vx = a * ddx, vy = b * ddy, vz = (p->z0_rel_m + k * p->dz_m) * 1e3;
+  const double c_mm = p->c_mps * 1e3, h = ddx + ddy + ddz; /* support half-width bound along any e */
+  for (int j = 0; j < ps.M; ++j) {
+    const double qx = -F * ps.nx[j], qy = -F * ps.ny[j], qz = -F * ps.nz[j];
+    const double ux = vx - qx, uy = vy - qy, uz = vz - qz;
+    const double r = sqrt(ux * ux + uy * uy + uz * uz);
+    const double ex = ux / r, ey = uy / r, ez = uz / r;
+    /* samples m with |c t_m - r| < h carry the tent */
+    const int m0 = (int)floor(p->fs_hz * ((r - h) / c_mm - t0)) - 1;
+    const int m1 = (int)ceil(p->fs_hz * ((r + h) / c_mm - t0)) + 1;
+    memset(D, 0, sizeof(double) * ((size_t)nt + 2));
+    for (int m = (m0 < -1 ? -1 : m0); m <= (m1 > nt ? nt : m1); ++m) {
+      /* D(m) = (I(m+1) - I(m-1)) / 2 */
+      const double rho1 = c_mm * (t0 + (m + 1) / p->fs_hz), rho0 = c_mm * (t0 + (m - 1) / p->fs_hz);
+      const double i1 = orc_tent_radon(ddx, ddy, ddz, ex, ey, ez, rho1 - r) / rho1;
+      const double i0 = orc_tent_radon(ddx, ddy, ddz, ex, ey, ez, rho0 - r) / rho0;
+      D[m + 1] = 0.5 * (i1 - i0);
+    }
+    const double wj = ps.w[j] * 1e6; /* mm^2 */
+    const int n0 = (m0 - T < 0 ? 0 : m0 - T), n1 = (m1 + T > nt - 1 ? nt - 1 : m1 + T);
+    for (int n = n0; n <= n1; ++n) { /* D is zero outside [m0, m1] */
+      double acc = 0.0;
+      for (int m = n - T; m <= n + T; ++m) {
+        if (m < -1 || m > nt) continue;
+        acc += e[n - m + T] * D[m + 1];
+      }
+      out[n] += wj * acc;
+    }
+  }
+  free(D); free(e); free(ps.nx);
+  return ORC_OK;
+}
