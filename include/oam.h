@@ -71,6 +71,28 @@ typedef enum {
                           per frequency orbit */
 } oam_precision;
 
+/* How Eq. 1 is discretised into the model slab.
+ * OAM_DISC_POINT (default): point voxels and the analytic time derivative of
+ *   the EIR: S = sum_j (w_j / d_j) e'(n - fs (d_j / c - t0)).
+ * OAM_DISC_TRILINEAR: the paper's two-step discretisation (Methods, Forward
+ *   modeling): the surface integral of Eq. 1 over the sphere |x - x'| = ct is
+ *   taken of the trilinear interpolation of the voxel values -- each voxel is
+ *   the tent L(x/dx) L(y/dy) L(z/dz), L(u) = max(0, 1 - |u|), and across a
+ *   tent's support the sphere is a plane, so the integral is the tent's
+ *   planar Radon transform R_j (in closed form) -- and the time derivative is
+ *   a central finite difference on the sample grid; the patch sum of Eq. 3
+ *   and the EIR sampled at whole samples follow:
+ *     I_j(m) = R_j(c t_m - r_j) / (c t_m),  t_m = t0 + m / fs,
+ *     S(n)   = sum_j w_j sum_m e(n - m) (I_j(m + 1) - I_j(m - 1)) / 2,
+ *   lengths in mm (arbitrary units, Eq. 2; for tents much smaller than a
+ *   wavelength it tends to (dx dy dz fs / c) times the point model).  Its
+ *   arrivals reach ceil(fs (dx + dy + dz) / c) + 2 samples beyond the point
+ *   model's, which the automatic time origin and the window check include. */
+typedef enum {
+  OAM_DISC_POINT = 0,
+  OAM_DISC_TRILINEAR = 1
+} oam_discretisation;
+
 /* Spherically focused sensor (AR-OAM set-up): focal length F, aperture
  * diameter D < 2F, optional central hole h < D, speed of sound c, and the
  * number M of surface patches (Eq. 3), a positive multiple of 8. */
@@ -138,6 +160,18 @@ oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const
  * OAM_ERR_UNSUPPORTED for shapes a kernel does not take); no device call. */
 oam_status oam_model_bytes(const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
                            oam_precision precision, size_t *bytes);
+
+/* Options of oam_build_model_ex / oam_model_bytes_ex (NULL = defaults). */
+typedef struct {
+  int32_t discretisation; /* oam_discretisation */
+} oam_model_opts;
+
+/* oam_build_model with options (the slab's discretisation of Eq. 1). */
+oam_status oam_build_model_ex(const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
+                              oam_precision precision, const oam_model_opts *opts, void *stream, oam_model **out);
+/* oam_model_bytes with options. */
+oam_status oam_model_bytes_ex(const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
+                              oam_precision precision, const oam_model_opts *opts, size_t *bytes);
 
 /* Release a model (NULL is accepted).  Synchronises the device first. */
 oam_status oam_model_free(oam_model *model);

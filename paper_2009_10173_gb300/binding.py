@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "liboam.so")
 OAM_OK, OAM_ERR_INVALID_ARG, OAM_ERR_WINDOW, OAM_ERR_OOM, OAM_ERR_CUDA = 0, 1, 2, 3, 4
 OAM_ERR_DEVICE, OAM_ERR_TIMEOUT, OAM_ERR_BUSY, OAM_ERR_UNSUPPORTED = 5, 6, 7, 8
 OAM_PREC_FP32, OAM_PREC_BF16X3, OAM_PREC_FFT = 0, 1, 2
+OAM_DISC_POINT, OAM_DISC_TRILINEAR = 0, 1
 
 EXPORTED = ("oam_build_model", "oam_model_free", "oam_model_get_info", "oam_model_slab_column", "oam_forward",
             "oam_adjoint", "oam_lsqr", "oam_l1_fista", "oam_solver_work_bytes", "oam_status_string",
@@ -23,10 +24,14 @@ EXPORTED = ("oam_build_model", "oam_model_free", "oam_model_get_info", "oam_mode
             "oam_server_create", "oam_server_submit", "oam_server_poll", "oam_server_wait", "oam_server_stats",
             "oam_server_stop", "oam_request_footprint", "oam_bandpass_taps", "oam_model_set_filter",
             "oam_filter_signals", "oam_lsqr_sweep", "oam_lsqr_sweep_work_bytes", "oam_model_get_tiles",
-            "oam_model_set_tiles", "oam_model_bytes")
+            "oam_model_set_tiles", "oam_model_bytes", "oam_build_model_ex", "oam_model_bytes_ex")
 
 OAM_MAX_FIR_HALF = 8191
 OAM_MAX_SWEEP = 32
+
+
+class OamModelOpts(ctypes.Structure):
+    _fields_ = [("discretisation", ctypes.c_int32)]
 
 
 class OamSensor(ctypes.Structure):
@@ -112,6 +117,9 @@ def lib():
         vp, i32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
         P = ctypes.POINTER
         L.oam_build_model.argtypes = [P(OamSensor), P(OamGrid), P(OamEir), ctypes.c_int, vp, P(vp)]
+        L.oam_build_model_ex.argtypes = [P(OamSensor), P(OamGrid), P(OamEir), ctypes.c_int, P(OamModelOpts), vp,
+                                         P(vp)]
+        L.oam_model_bytes_ex.argtypes = [P(OamSensor), P(OamGrid), P(OamEir), i32, P(OamModelOpts), P(sz)]
         L.oam_model_free.argtypes = [vp]
         L.oam_model_get_info.argtypes = [vp, P(OamModelInfo)]
         L.oam_model_slab_column.argtypes = [vp, i32, i32, i32, vp, vp]
@@ -189,10 +197,16 @@ def structs_from_config(cfg):
     return s, g, e
 
 
-def oam_build_model(sensor, grid, eir, precision=OAM_PREC_FP32, stream=None):
+def oam_build_model(sensor, grid, eir, precision=OAM_PREC_FP32, stream=None, discretisation=None):
     h = ctypes.c_void_p()
-    _check("oam_build_model", lib().oam_build_model(ctypes.byref(sensor), ctypes.byref(grid), ctypes.byref(eir),
-                                                     int(precision), _stream(stream), ctypes.byref(h)))
+    if discretisation is None:
+        _check("oam_build_model", lib().oam_build_model(ctypes.byref(sensor), ctypes.byref(grid), ctypes.byref(eir),
+                                                         int(precision), _stream(stream), ctypes.byref(h)))
+    else:
+        opts = OamModelOpts(int(discretisation))
+        _check("oam_build_model_ex", lib().oam_build_model_ex(ctypes.byref(sensor), ctypes.byref(grid),
+                                                               ctypes.byref(eir), int(precision), ctypes.byref(opts),
+                                                               _stream(stream), ctypes.byref(h)))
     return h
 
 
@@ -314,12 +328,17 @@ def oam_model_autotune(model, reps=3, stream=None):
     return f.value, a.value
 
 
-def oam_model_bytes(cfg, precision):
+def oam_model_bytes(cfg, precision, discretisation=None):
     """Device bytes oam_build_model would allocate for a configuration (host only)."""
     sn, g, e = structs_from_config(cfg)
     out = ctypes.c_size_t()
-    _check("oam_model_bytes", lib().oam_model_bytes(ctypes.byref(sn), ctypes.byref(g), ctypes.byref(e),
-                                                    int(precision), ctypes.byref(out)))
+    if discretisation is None:
+        _check("oam_model_bytes", lib().oam_model_bytes(ctypes.byref(sn), ctypes.byref(g), ctypes.byref(e),
+                                                        int(precision), ctypes.byref(out)))
+    else:
+        opts = OamModelOpts(int(discretisation))
+        _check("oam_model_bytes_ex", lib().oam_model_bytes_ex(ctypes.byref(sn), ctypes.byref(g), ctypes.byref(e),
+                                                              int(precision), ctypes.byref(opts), ctypes.byref(out)))
     return out.value
 
 

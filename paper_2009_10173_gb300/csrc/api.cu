@@ -265,10 +265,17 @@ const char *oam_status_string(oam_status s) {
 
 oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
                            oam_precision precision, void *stream, oam_model **out) {
+  return oam_build_model_ex(sensor, grid, eir, precision, nullptr, stream, out);
+}
+
+oam_status oam_build_model_ex(const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
+                              oam_precision precision, const oam_model_opts *opts, void *stream, oam_model **out) {
   if (!out) return OAM_ERR_INVALID_ARG;
   *out = nullptr;
   oam_status rc = check_params(sensor, grid, eir);
   if (rc) return rc;
+  const int disc = opts ? opts->discretisation : OAM_DISC_POINT;
+  if (disc != OAM_DISC_POINT && disc != OAM_DISC_TRILINEAR) return OAM_ERR_INVALID_ARG;
   if (precision != OAM_PREC_FP32 && precision != OAM_PREC_BF16X3 && precision != OAM_PREC_FFT)
     return OAM_ERR_INVALID_ARG;
   int dev = 0, major = 0, minor = 0, sms = 0;
@@ -284,6 +291,7 @@ oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const
   m->grid = *grid;
   m->eir = *eir;
   m->precision = precision;
+  m->disc = disc;
   m->sm_count = sms;
   m->W = grid->win;
   m->R = (grid->win - 1) / 2;
@@ -314,12 +322,20 @@ oam_status oam_build_model(const oam_sensor *sensor, const oam_grid *grid, const
 
 oam_status oam_model_bytes(const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
                            oam_precision precision, size_t *bytes) {
+  return oam_model_bytes_ex(sensor, grid, eir, precision, nullptr, bytes);
+}
+
+oam_status oam_model_bytes_ex(const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
+                              oam_precision precision, const oam_model_opts *opts, size_t *bytes) {
   if (!bytes) return OAM_ERR_INVALID_ARG;
   oam_status rc = check_params(sensor, grid, eir);
   if (rc) return rc;
   if (precision != OAM_PREC_FP32 && precision != OAM_PREC_BF16X3 && precision != OAM_PREC_FFT)
     return OAM_ERR_INVALID_ARG;
+  const int disc = opts ? opts->discretisation : OAM_DISC_POINT;
+  if (disc != OAM_DISC_POINT && disc != OAM_DISC_TRILINEAR) return OAM_ERR_INVALID_ARG;
   oam_model m;  // host-side plan only: no device memory, no device call
+  m.disc = disc;
   m.sensor = *sensor;
   m.grid = *grid;
   m.eir = *eir;

@@ -46,6 +46,7 @@ struct oam_model {
   oam_grid grid;
   oam_eir eir;
   int precision;
+  int disc = OAM_DISC_POINT;  // oam_discretisation of Eq. 1
   int R, W;                 // half window, window (taps per lateral axis)
   double t0;                // time of sample 0 (s)
   double sigma_s, omega, cut; // EIR in sample units: std dev, angular freq, truncation
@@ -184,6 +185,10 @@ float *fir_stage(const oam_model *m);
 int fir_half_len(const oam_model *m);
 int fir_size(const oam_model *m);
 void fir_free(oam_model *m, cudaStream_t st);
+
+// samples by which a trilinear voxel's arrivals (and the finite difference)
+// extend the point voxel's: ceil(fs (dx + dy + dz) / c) + 2; 0 for point voxels
+int disc_margin(const oam_model *m);
 
 // free every device buffer of a model with cudaFreeAsync on `st`, then the model
 void model_release(oam_model *m, cudaStream_t st);

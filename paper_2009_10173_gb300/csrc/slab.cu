@@ -7,6 +7,7 @@
 // tau = n - D_j (|tau| <= trunc_sigma * sigma_s), tau being the FP32 rounding
 // of the exact offset, and summed over patches with a compensated FP32 sum.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "internal.cuh"
@@ -178,6 +179,144 @@ __global__ void k_delta_range(Geo g, const Patch *__restrict__ patch, const Patc
   }
 }
 
+// ---------------------------------------------------------------- trilinear voxels
+// The paper's discretisation of Eq. 1 (Methods, Forward modeling): the
+// surface integral of the trilinear interpolation of the voxel values, and a
+// central finite difference in time.  A voxel is the tent
+// L(x/dx) L(y/dy) L(z/dz), L(u) = max(0, 1 - |u|); across its support the
+// sphere |x - x'| = ct is a plane, so the integral is the tent's planar
+// Radon transform along e = (v - q)/|v - q|: the hats of half-width
+// a = |e_i| d_i (area d_i) convolve, i.e. a six-box spline
+//   sum over sign vectors s of prod(s) (u + sum s_i c_i/2)_+^5 / 5!,
+// with an axis whose a < 1e-3 max(a) taken as a spike of mass d_i.  FP64:
+// the signed sum cancels heavily.
+__device__ double tent_radon(double dx, double dy, double dz, double ex, double ey, double ez, double u) {
+  const double d[3] = {dx, dy, dz}, e[3] = {fabs(ex), fabs(ey), fabs(ez)};
+  double a[3], amax = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    a[i] = e[i] * d[i];
+    amax = fmax(amax, a[i]);
+  }
+  double c[6], scale = 1.0;
+  int n = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (a[i] < 1e-3 * amax) {
+      scale *= d[i];
+    } else {
+      c[n++] = a[i];
+      c[n++] = a[i];
+      scale *= d[i] / (a[i] * a[i]);
+    }
+  }
+  double fact = 1.0;
+  for (int i = 2; i < n; ++i) fact *= i;
+  double sum = 0.0;
+  for (int mask = 0; mask < (1 << n); ++mask) {
+    double x = u, sign = 1.0;
+    for (int i = 0; i < n; ++i) {
+      if (mask & (1 << i)) {
+        x -= 0.5 * c[i];
+        sign = -sign;
+      } else {
+        x += 0.5 * c[i];
+      }
+    }
+    if (x > 0.0) {
+      double pw = 1.0;
+      for (int q = 1; q < n; ++q) pw *= x;
+      sum += sign * pw;
+    }
+  }
+  return scale * sum / fact;
+}
+
+struct Geo33 {
+  double F, dx, dy, dz, z0;  // mm
+  double c;                  // mm / s
+  double fs, t0;             // Hz, s
+  double sigma, omega;       // EIR in samples: std dev, rad per sample
+  int T;                     // EIR taps each side (whole samples within the cut)
+  int len;                   // samples of a patch's finite-difference support held per patch
+};
+
+constexpr int k33Chunk = 128;  // patches per shared-memory chunk
+
+// Block (orbit o, depth k): band values S[o][k][lo .. hi) =
+//   sum_j w_j sum_m e(n - m) D_j(m),  D_j(m) = (I_j(m+1) - I_j(m-1)) / 2,
+//   I_j(m) = R_j(c t_m - r_j) / (c t_m),  t_m = t0 + m / fs,
+// patches in index order, each patch's sum over m first (FP64 throughout).
+__global__ void k_slab33_values(Geo33 g, const Patch *__restrict__ patch, int M, const int *orb_b, const int *orb_a,
+                                int nz, int nt, const int *band_lo, const int *band_hi, int band_w,
+                                float *__restrict__ band) {
+  extern __shared__ double sm33[];
+  double *e = sm33;                           // [2T + 1]
+  double *D = e + 2 * g.T + 1;                // [k33Chunk][len]
+  int *m0s = reinterpret_cast<int *>(D + (size_t)k33Chunk * g.len);  // [k33Chunk]
+  double *ws = reinterpret_cast<double *>(m0s + k33Chunk + (k33Chunk & 1));  // [k33Chunk] (8-byte aligned)
+  const int o = blockIdx.x, k = blockIdx.y;
+  const double vx = orb_a[o] * g.dx, vy = orb_b[o] * g.dy, vz = g.z0 + k * g.dz;
+  const int lo = band_lo[(size_t)o * nz + k], hi = band_hi[(size_t)o * nz + k];
+  for (int i = threadIdx.x; i <= 2 * g.T; i += blockDim.x) {
+    const double tau = i - g.T;
+    e[i] = exp(-tau * tau / (2.0 * g.sigma * g.sigma)) * cos(g.omega * tau);
+  }
+  constexpr int kPer = 4;  // band samples per thread (band_w <= 4 * blockDim)
+  double acc[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) acc[q] = 0.0;
+  const double h = g.dx + g.dy + g.dz;
+  for (int j0 = 0; j0 < M; j0 += k33Chunk) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < k33Chunk; i += blockDim.x) {
+      const int j = j0 + i;
+      if (j >= M) {
+        m0s[i] = INT_MIN / 2;
+        continue;
+      }
+      const Patch pj = patch[j];
+      const double ux = vx + g.F * pj.x, uy = vy + g.F * pj.y, uz = vz + g.F * pj.z;  // v - q, q = -F n
+      const double r = sqrt(ux * ux + uy * uy + uz * uz);
+      const double ex = ux / r, ey = uy / r, ez = uz / r;
+      const int m0 = (int)floor(g.fs * ((r - h) / g.c - g.t0)) - 1;
+      m0s[i] = m0;
+      ws[i] = pj.w;
+      for (int q = 0; q < g.len; ++q) {
+        const int m = m0 + q;
+        double dv = 0.0;
+        if (m >= -1 && m <= nt) {
+          const double rho1 = g.c * (g.t0 + (m + 1) / g.fs), rho0 = g.c * (g.t0 + (m - 1) / g.fs);
+          const double i1 = tent_radon(g.dx, g.dy, g.dz, ex, ey, ez, rho1 - r) / rho1;
+          const double i0 = tent_radon(g.dx, g.dy, g.dz, ex, ey, ez, rho0 - r) / rho0;
+          dv = 0.5 * (i1 - i0);
+        }
+        D[(size_t)i * g.len + q] = dv;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int n = lo + threadIdx.x + q * blockDim.x;
+      if (n >= hi) continue;
+      for (int i = 0; i < k33Chunk; ++i) {
+        const int m0 = m0s[i];
+        if (n < m0 - g.T || n > m0 + g.len - 1 + g.T) continue;
+        double sj = 0.0;
+        for (int qq = 0; qq < g.len; ++qq) {
+          const int dm = n - (m0 + qq);
+          if (dm >= -g.T && dm <= g.T) sj += e[dm + g.T] * D[(size_t)i * g.len + qq];
+        }
+        acc[q] += ws[i] * sj;
+      }
+    }
+  }
+  float *row = band + ((size_t)o * nz + k) * band_w;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int i = threadIdx.x + q * blockDim.x;
+    if (i < band_w) row[i] = lo + i < hi ? (float)acc[q] : 0.0f;
+  }
+}
+
 constexpr int kPatchChunk = 512;
 
 // Band values: thread i of block (o, k) owns sample lo + i (+ blockDim.x ...).
@@ -309,6 +448,12 @@ __global__ void k_slab_column(const float *band, const int *band_lo, int band_w,
 
 }  // namespace
 
+int oam::disc_margin(const oam_model *m) {
+  if (m->disc != OAM_DISC_TRILINEAR) return 0;
+  const oam_grid &g = m->grid;
+  return (int)std::ceil(g.fs_hz * (g.dx_m + g.dy_m + g.dz_m) / m->sensor.c_mps) + 2;
+}
+
 // Time origin, window check and bands [lo, hi) per (orbit, depth) from the
 // range of d - F over the patches; each band is widened by `widen` samples on
 // both sides (0 for a model build; the footprint planner widens to cover
@@ -323,11 +468,13 @@ oam_status oam::plan_bands(oam_model *m, const std::vector<double2> &h_range, in
     dmax = std::max(dmax, r.y);
   }
   const double fs = gr.fs_hz, c = m->sensor.c_mps, F = m->sensor.focal_m, ks = fs / c;
-  const double t0 = std::isnan(gr.t0_s) ? (std::floor(fs * (F + dmin) / c - m->cut) - 2.0) / fs : gr.t0_s;
+  const double reach = m->cut + disc_margin(m);  // samples an arrival reaches on either side
+  const double t0 = std::isnan(gr.t0_s) ? (std::floor(fs * (F + dmin) / c - reach) - 2.0) / fs : gr.t0_s;
   m->t0 = t0;
   const double G = fs * (F / c - t0);
-  if (ks * dmin + G - m->cut < 0 || ks * dmax + G + m->cut >= nt) return OAM_ERR_WINDOW;
+  if (ks * dmin + G - reach < 0 || ks * dmax + G + reach >= nt) return OAM_ERR_WINDOW;
   m->G = G;
+  widen += disc_margin(m);
 
   // bands [lo, hi) per (orbit, depth)
   m->h_band_lo.resize((size_t)O * nz);
@@ -496,10 +643,33 @@ oam_status oam::build_slab(oam_model *m, cudaStream_t st) {
   OAM_CUDA_TRY(cudaMemcpyAsync(m->d_band_lo, m->h_band_lo.data(), sizeof(int) * O * nz, cudaMemcpyHostToDevice, st));
   OAM_CUDA_TRY(cudaMemcpyAsync(d_band_hi, m->h_band_hi.data(), sizeof(int) * O * nz, cudaMemcpyHostToDevice, st));
   if ((rc = dev_alloc(m, &m->d_band, (size_t)O * nz * m->band_w))) return rc;
-  const int threads = m->band_w <= 128 ? 128 : 256;
-  const int T0 = (int)std::floor(m->cut + 0.5) + 1;  // rotation table half-length
-  k_slab_values<<<dim3(O, nz), threads, sizeof(float2) * (2 * T0 + 1), st>>>(
-      g, d_pdw, m->M, d_orb_b, d_orb_a, nz, m->d_band_lo, d_band_hi, m->band_w, T0, m->d_band);
+  if (m->disc == OAM_DISC_TRILINEAR) {
+    Geo33 g3{};
+    g3.F = m->sensor.focal_m * 1e3;
+    g3.dx = gr.dx_m * 1e3;
+    g3.dy = gr.dy_m * 1e3;
+    g3.dz = gr.dz_m * 1e3;
+    g3.z0 = gr.z0_rel_m * 1e3;
+    g3.c = m->sensor.c_mps * 1e3;
+    g3.fs = gr.fs_hz;
+    g3.t0 = m->t0;
+    g3.sigma = m->sigma_s;
+    g3.omega = m->omega;
+    g3.T = (int)std::floor(m->cut);
+    g3.len = (int)std::ceil(2.0 * gr.fs_hz * (gr.dx_m + gr.dy_m + gr.dz_m) / m->sensor.c_mps) + 4;
+    const int threads = std::max(128, ((m->band_w + 3) / 4 + 31) & ~31);
+    const size_t sm = sizeof(double) * (2 * g3.T + 1 + (size_t)k33Chunk * g3.len) + sizeof(int) * (k33Chunk + 2) +
+                      sizeof(double) * k33Chunk;
+    if (threads > 1024 || sm > 200 * 1024) return OAM_ERR_UNSUPPORTED;
+    if (sm > 48 * 1024) OAM_CUDA_TRY(cudaFuncSetAttribute(k_slab33_values, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_slab33_values<<<dim3(O, nz), threads, sm, st>>>(g3, m->d_patch, m->M, d_orb_b, d_orb_a, nz, nt, m->d_band_lo,
+                                                      d_band_hi, m->band_w, m->d_band);
+  } else {
+    const int threads = m->band_w <= 128 ? 128 : 256;
+    const int T0 = (int)std::floor(m->cut + 0.5) + 1;  // rotation table half-length
+    k_slab_values<<<dim3(O, nz), threads, sizeof(float2) * (2 * T0 + 1), st>>>(
+        g, d_pdw, m->M, d_orb_b, d_orb_a, nz, m->d_band_lo, d_band_hi, m->band_w, T0, m->d_band);
+  }
   OAM_LAUNCHED();
 
   // FP32 forward layout

@@ -7,7 +7,8 @@ start vectors.  Every draw uses numpy's PCG64 with an explicit seed in FP64.
 The paper's datasets (microsphere and carbon-fibre phantoms, mouse skin) are
 measured data; these generators stand in for them with the same kind of
 structure: Gaussian microspheres of 20-50 um diameter and a branching tree of
-tubes of 5-30 um radius.
+tubes of 5-30 um radius.  ``paraboloids`` draws the truncated paraboloids of
+the paper's simulations (no randomness).
 """
 import math
 
@@ -109,6 +110,19 @@ def vessel_tree(cfg, seed, root_radius=30e-6, min_radius=5e-6, out=None):
             nd = np.array([c * dvec[0] - s * dvec[1], s * dvec[0] + c * dvec[1],
                            dvec[2] + rng.uniform(-0.15, 0.15)])
             stack.append((p1, nd / np.linalg.norm(nd), rc, depth + 1))
+    return H
+
+
+def paraboloids(cfg, centres, diameter):
+    """Truncated paraboloids max(0, 1 - |x - c|^2 / (D/2)^2) of diameter D at the
+    given centres (metres, in the frame of ``_grid``: x = i dx, y = j dy,
+    z = z0_rel + k dz), merged by max.  Layout H[py][px][nz], FP64."""
+    x, y, z = _grid(cfg)
+    gy, gx, gz = np.meshgrid(y, x, z, indexing="ij")
+    H = np.zeros((cfg["py"], cfg["px"], cfg["nz"]))
+    r2 = (0.5 * diameter) ** 2
+    for cx, cy, cz in centres:
+        H = np.maximum(H, np.maximum(0.0, 1.0 - ((gx - cx) ** 2 + (gy - cy) ** 2 + (gz - cz) ** 2) / r2))
     return H
 
 

@@ -11,12 +11,12 @@ from . import binding as B
 class Model:
     """A device-resident model slab plus the operators and solvers that use it."""
 
-    def __init__(self, cfg, precision=B.OAM_PREC_FP32, stream=None, device=None):
+    def __init__(self, cfg, precision=B.OAM_PREC_FP32, stream=None, device=None, discretisation=None):
         self.cfg = dict(cfg)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         with torch.cuda.device(self.device):
             s, g, e = B.structs_from_config(cfg)
-            self.handle = B.oam_build_model(s, g, e, precision, stream)
+            self.handle = B.oam_build_model(s, g, e, precision, stream, discretisation)
         self.info = B.oam_model_get_info(self.handle)
         self.precision = precision
         self.vol_shape = (cfg["py"], cfg["px"], cfg["nz"])
