@@ -428,7 +428,7 @@ def run_serve(args):
     for k, rate in enumerate(args.rates):
         server = serve.make_server(150e9, args.slots, precision=prec, lsqr_iters=SERVE_ITERS[0],
                                    fista_iters=SERVE_ITERS[1], power_iters=SERVE_ITERS[2], lambda_rel=LAMBDA_REL)
-        res, _ = serve.run_rate(server, pool, rate, args.requests, seed=3000 + k, check=check)
+        res = serve.run_rate(server, pool, rate, args.requests, seed=3000 + k, check=check, check_picks=checked_pool)
         B.oam_server_stop(server)
         results.append(res)
     err = None

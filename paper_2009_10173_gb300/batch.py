@@ -3,7 +3,8 @@
     python -m paper_2009_10173_gb300.batch --jobs 16 --reps 3
 
 builds the batched workload (seeded sensors, sizes and vessel phantoms),
-autotunes each model's tensor-core ring depth, records one graph with every
+autotunes each model's tensor-core tile shape (fold warps and item-ring depth
+per direction), records one graph with every
 job's LSQR and FISTA on its own branch, and times graph launches.  Marshalling
 only: all arithmetic runs in liboam.so.
 """
@@ -105,7 +106,9 @@ def main():
                       "ms_per_batch": ms, "volumes_per_s": a.jobs / (ms / 1e3),
                       "op_tflops_algorithmic": flops / (ms * 1e-3) / 1e12,
                       "jobs": [[c["py"], c["px"], c["nz"], c["nt"], round(c["focal_m"] * 1e3, 2),
-                                round(c["aperture_m"] * 1e3, 2)] for c in cfgs]}))
+                                round(c["aperture_m"] * 1e3, 2)] for c in cfgs],
+                      "tiles": [[B.oam_model_get_tiles(c["_model"].handle, d) for d in (0, 1)] for c in cfgs]
+                      if prec == B.OAM_PREC_BF16X3 else None}))
     batch.close()
 
 

@@ -26,6 +26,7 @@ Marshalling only: all arithmetic runs in liboam.so.
 """
 import argparse
 import json
+import time
 
 import numpy as np
 import torch
@@ -76,30 +77,41 @@ def fwhm_um(x):
 
 
 def reconstruct(m, s, lsqr_iters, fista_iters, lambda_rel):
+    """MB-L2 and MB-L1 images of the filtered signals, with each solve's device time (ms)."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     s_f = m.filter_signals(s)
+    ev[0].record()
     x2, _ = m.lsqr(s_f, lsqr_iters)
+    ev[1].record()
     x1, _ = m.fista(s_f, fista_iters, power_iters=30, lambda_rel=lambda_rel, nonneg=True)
-    return x2.cpu().numpy(), x1.cpu().numpy()
+    ev[2].record()
+    torch.cuda.synchronize()
+    return x2.cpu().numpy(), x1.cpu().numpy(), (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]))
 
 
 def run(separations_um=(60, 40), precision=B.OAM_PREC_FFT, lsqr_iters=50, fista_iters=400, lambda_rel=1e-3):
     cfg = config()
+    torch.cuda.synchronize()
+    t_build = time.perf_counter()
     m = Model(cfg, precision=precision, discretisation=B.OAM_DISC_TRILINEAR)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t_build
     m.set_filter(B.oam_bandpass_taps(BAND[0], BAND[1], cfg["fs_hz"], FIR_HALF))
     cx, cy, cz = 20 * STEP, 20 * STEP, 0.0
     j, k = 20, 15  # profile row (y = cy) and focal depth (z = 0)
     out = {"workload": "two 20 um truncated paraboloids at the focus, 200x200x150 um^3 at 5 um, "
                        "F 7 mm / NA 0.43 sensor, 0.5-80 MHz band-pass, discretised model (trilinear voxels, "
                        "finite-difference derivative), noiseless normalised signals",
-           "lsqr_iters": lsqr_iters, "fista_iters": fista_iters, "lambda_rel": lambda_rel, "results": {}}
+           "lsqr_iters": lsqr_iters, "fista_iters": fista_iters, "lambda_rel": lambda_rel,
+           "model_build_s": t_build, "model_bytes": m.info.device_bytes, "results": {}}
     single = inputs.paraboloids(cfg, [(cx, cy, cz)], DIAMETER)
-    for name, H in [("single", single)] + [(f"{sep}um", inputs.paraboloids(
+    for name, H in [("single", single)] + [(f"{float(sep):.1f}um", inputs.paraboloids(
             cfg, [(cx - 0.5 * sep * 1e-6, cy, cz), (cx + 0.5 * sep * 1e-6, cy, cz)], DIAMETER))
             for sep in separations_um]:
         s = m.forward(torch.from_numpy(H.astype(np.float32)).cuda())  # F A H: the filtered model's signals
         s = s / s.abs().max()
-        x2, x1 = reconstruct(m, s, lsqr_iters, fista_iters, lambda_rel)
-        res = {}
+        x2, x1, ms = reconstruct(m, s, lsqr_iters, fista_iters, lambda_rel)
+        res = {"lsqr_ms": ms[0], "fista_ms": ms[1]}
         for method, x in (("MB-L2", x2), ("MB-L1", x1)):
             prof = x[j, :, k]
             if name == "single":

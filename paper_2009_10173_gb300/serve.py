@@ -70,16 +70,49 @@ def make_server(budget_bytes=150 * 10 ** 9, slots=8, precision=B.OAM_PREC_BF16X3
     return B.oam_server_create(opts)
 
 
-def run_rate(server, pool, rate, n_requests, seed, timeout_s=3600.0, check=None):
+def run_rate(server, pool, rate, n_requests, seed, timeout_s=3600.0, check=None, check_picks=None,
+             buffers_per_instance=2):
     """Submit n_requests at Poisson arrival times (rate per second), wait for all.
 
-    ``check(index_in_pool, x_l2, x_l1)``, if given, is called for every
-    completed request; it returns None (not checked) or a dict of errors,
-    which are summarised in the result."""
+    Output images go into pinned host buffers allocated before the clock
+    starts (``buffers_per_instance`` pairs per prepared instance); a pair is
+    reused once the request that held it has completed, and a new pair is
+    allocated only when every pair of that instance is still in flight
+    (counted in ``output_allocs``).  Latency is reported from submission (the
+    server's clock) and from the scheduled arrival time (adds any delay of the
+    submission itself).  ``check(index_in_pool, x_l2, x_l1)``, if given, is
+    called for every completed request; it
+    returns None (not checked) or a dict of errors, summarised in the result.
+    Checks run after the clock stops, on copies of the images of the instances
+    in ``check_picks`` (every instance if None)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     gaps = rng.exponential(1.0 / rate, n_requests)
     picks = rng.integers(0, len(pool), n_requests)
-    keep = []
+    free = {j: [inst.new_outputs() for _ in range(buffers_per_instance)] for j, inst in enumerate(pool)}
+    busy = {j: [] for j in range(len(pool))}  # (request id, submit lag, x2, x1), oldest first
+    lat, lat_arrival, to_check = [], [], []
+    state = {"failed": 0, "allocs": 0}
+
+    def finish(pick, rid, lag, x2, x1):
+        info = B.oam_server_poll(server, rid)
+        if info.state != 2:
+            state["failed"] += 1
+            return
+        lat.append(info.latency_s)
+        lat_arrival.append(lag + info.latency_s)
+        if check is not None and (check_picks is None or pick in check_picks):
+            to_check.append((pick, x2.clone(), x1.clone()))
+
+    def take(j):
+        if free[j]:
+            return free[j].pop()
+        if busy[j] and B.oam_server_poll(server, busy[j][0][0]).state >= 2:
+            rid, lag, x2, x1 = busy[j].pop(0)
+            finish(j, rid, lag, x2, x1)
+            return x2, x1
+        state["allocs"] += 1
+        return pool[j].new_outputs()
+
     t0 = time.perf_counter()
     t_next = t0
     for i in range(n_requests):
@@ -87,36 +120,36 @@ def run_rate(server, pool, rate, n_requests, seed, timeout_s=3600.0, check=None)
         delay = t_next - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        inst = pool[picks[i]]
-        x2, x1 = inst.new_outputs()
-        s, g, e = inst.structs
-        rid = B.oam_server_submit(server, s, g, e, inst.h_s, x2, x1)
-        keep.append((rid, int(picks[i]), x2, x1))
+        j = int(picks[i])
+        x2, x1 = take(j)
+        s, g, e = pool[j].structs
+        rid = B.oam_server_submit(server, s, g, e, pool[j].h_s, x2, x1)
+        busy[j].append((rid, max(0.0, time.perf_counter() - t_next), x2, x1))
     t_last_submit = time.perf_counter() - t0
-    lat, failed, done = [], 0, []
-    for rid, pick, x2, x1 in keep:
-        rc = B.oam_server_wait(server, rid, timeout_s)
-        info = B.oam_server_poll(server, rid)
-        if rc != B.OAM_OK or info.state != 2:
-            failed += 1
-        else:
-            lat.append(info.latency_s)
-            done.append((pick, x2, x1))
+    for j in busy:
+        for rid, lag, x2, x1 in busy[j]:
+            rc = B.oam_server_wait(server, rid, timeout_s)
+            if rc != B.OAM_OK:
+                state["failed"] += 1
+                continue
+            finish(j, rid, lag, x2, x1)
     makespan = time.perf_counter() - t0
     stats = B.oam_server_stats(server)
+    pct = (lambda v, q: float(np.percentile(v, q)) if v else None)
     out = {"rate_offered_per_s": rate, "rate_achieved_submit_per_s": n_requests / t_last_submit,
-           "requests": n_requests, "completed": len(lat), "failed": failed, "makespan_s": makespan,
+           "requests": n_requests, "completed": len(lat), "failed": state["failed"], "makespan_s": makespan,
            "volumes_per_s": len(lat) / makespan,
-           "p50_latency_s": float(np.percentile(lat, 50)) if lat else None,
-           "p99_latency_s": float(np.percentile(lat, 99)) if lat else None,
+           "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99),
+           "p50_latency_from_arrival_s": pct(lat_arrival, 50), "p99_latency_from_arrival_s": pct(lat_arrival, 99),
+           "output_allocs": state["allocs"],
            "peak_running": stats.peak_running, "peak_reserved_gb": stats.peak_reserved_bytes / 1e9}
     if check is not None:
-        errs = [e for e in (check(p, x2, x1) for p, x2, x1 in done) if e is not None]
+        errs = [e for e in (check(p, x2, x1) for p, x2, x1 in to_check) if e is not None]
         out["checked"] = len(errs)
         if errs:
             for key in errs[0]:
                 out[f"max_{key}"] = max(float(e[key]) for e in errs)
-    return out, keep
+    return out
 
 
 def main():
@@ -133,7 +166,7 @@ def main():
     pool = [Instance(configs.served_request(2000 + j), prec) for j in range(a.pool)]
     for k, rate in enumerate(a.rates):
         server = make_server(a.budget_gb * 1e9, a.slots, precision=prec)
-        res, _ = run_rate(server, pool, rate, a.requests, seed=3000 + k)
+        res = run_rate(server, pool, rate, a.requests, seed=3000 + k)
         B.oam_server_stop(server)
         res.update({"workload": "served: Poisson arrivals, sizes as the batched workload plus occasional "
                                 "200x200x300 volumes, 30 LSQR + 50 FISTA each",
