@@ -71,14 +71,16 @@ def make_server(budget_bytes=150 * 10 ** 9, slots=8, precision=B.OAM_PREC_BF16X3
 
 
 def run_rate(server, pool, rate, n_requests, seed, timeout_s=3600.0, check=None, check_picks=None,
-             buffers_per_instance=2):
+             buffers_per_instance=None):
     """Submit n_requests at Poisson arrival times (rate per second), wait for all.
 
     Output images go into pinned host buffers allocated before the clock
-    starts (``buffers_per_instance`` pairs per prepared instance); a pair is
-    reused once the request that held it has completed, and a new pair is
-    allocated only when every pair of that instance is still in flight
-    (counted in ``output_allocs``).  Latency is reported from submission (the
+    starts: ``buffers_per_instance`` pairs per prepared instance, or by default
+    one pair per request of the schedule (no allocation while the clock runs,
+    at the cost of host memory for every request's images).  A pair is reused
+    once the request that held it has completed, and a new pair is allocated
+    only when every pair of that instance is still in flight (counted in
+    ``output_allocs``).  Latency is reported from submission (the
     server's clock) and from the scheduled arrival time (adds any delay of the
     submission itself).  ``check(index_in_pool, x_l2, x_l1)``, if given, is
     called for every completed request; it
@@ -88,7 +90,10 @@ def run_rate(server, pool, rate, n_requests, seed, timeout_s=3600.0, check=None,
     rng = np.random.Generator(np.random.PCG64(seed))
     gaps = rng.exponential(1.0 / rate, n_requests)
     picks = rng.integers(0, len(pool), n_requests)
-    free = {j: [inst.new_outputs() for _ in range(buffers_per_instance)] for j, inst in enumerate(pool)}
+    counts = np.bincount(picks, minlength=len(pool))
+    free = {j: [inst.new_outputs() for _ in range(int(counts[j]) if buffers_per_instance is None
+                                                  else min(int(counts[j]), buffers_per_instance))]
+            for j, inst in enumerate(pool)}
     busy = {j: [] for j in range(len(pool))}  # (request id, submit lag, x2, x1), oldest first
     lat, lat_arrival, to_check = [], [], []
     state = {"failed": 0, "allocs": 0}
