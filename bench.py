@@ -32,10 +32,10 @@ OPS_PER_STEP = (1 + 2 * LSQR_ITERS) + (2 * POWER_ITERS + 1 + 2 * FISTA_ITERS)
 FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the tensor-core operator kernel (k_corr_fold) on this
 # workload: dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of the
-# same kernel on a 96x96-position case of this workload (121.6 MB + 319.5 MB for
-# 2945 blocks; profiles/k_corr_fold_fwd_96x96x300_win61.md), scaled by blocks
-# processed (11160 / 2945).  Set to None when the kernel changes.
-TC_TRAFFIC_BYTES = 441.09e6 * 11160 / 2945
+# same kernel on a 96x96-position case of this workload, scaled by blocks
+# processed (profiles/k_corr_fold_fwd_96x96x300_win61.md).  None until the
+# current kernel has been captured.
+TC_TRAFFIC_BYTES = None
 # DRAM bytes per application of the lateral-FFT form on this workload:
 # dram__bytes_read.sum + dram__bytes_write.sum over the five launches of one
 # forward, from an ncu capture of the full 200x200x300 workload (1.191 GB read,

@@ -322,7 +322,8 @@ oam_status oam_solver_work_bytes(const oam_model *model, int32_t solver, size_t 
  * build the folded split-BF16 operand, each folding 32, 16 or 8 of a stage's
  * 32 K elements per item) and the item-ring depth (slab tiles in shared
  * memory and folded operands in tensor memory, 2 up to the deepest that
- * fits).  The choice is kept in the model (read it with oam_model_get_tiles).
+ * fits), and the position tiling (oam_model_set_tiling).  The choice is kept
+ * in the model (read it with oam_model_get_tiles and oam_model_get_tiling).
  * Allocates and frees a scratch volume and signal buffer; synchronises
  * `stream`.  No-op for the other precisions.  The paper has no counterpart
  * (tuning of this implementation). */
@@ -336,6 +337,18 @@ oam_status oam_model_get_tiles(const oam_model *model, int32_t direction, int32_
  * 2 .. deepest); OAM_ERR_INVALID_ARG leaves the model unchanged.  Results do
  * not depend on the shape (fixed summation order per accumulator). */
 oam_status oam_model_set_tiles(oam_model *model, int32_t direction, int32_t fold_warps, int32_t ring);
+/* Position tiling of the split-BF16 kernels, direction 0 or 1: the grid whose
+ * 128 consecutive positions a block takes.  1 = the padded scan grid (rows of
+ * px + R positions, the R padding positions per row computed and dropped;
+ * strips of 128 + 2R staged rows), 2 = the scan grid itself (every position an
+ * output; a tile that wraps w scan rows stages 128 + (w + 2) R rows, so it
+ * needs w + 2 <= 128 / R and more shared memory), 0 = automatic (the scan grid
+ * unless it leaves a shallower item ring).  get returns the tiling in use (1
+ * or 2); set returns OAM_ERR_UNSUPPORTED and leaves the model unchanged when
+ * the tiling does not fit.  oam_model_autotune searches it too.  Results do not
+ * depend on it. */
+oam_status oam_model_get_tiling(const oam_model *model, int32_t direction, int32_t *tiling);
+oam_status oam_model_set_tiling(oam_model *model, int32_t direction, int32_t tiling);
 
 /* --------------------------------------------------------------- batching */
 /* Many uneven reconstructions in one CUDA-graph launch (the paper reconstructs

@@ -3,8 +3,8 @@
     python -m paper_2009_10173_gb300.batch --jobs 16 --reps 3
 
 builds the batched workload (seeded sensors, sizes and vessel phantoms),
-autotunes each model's tensor-core tile shape (fold warps and item-ring depth
-per direction), records one graph with every
+autotunes each model's tensor-core tile shape (position tiling, fold warps
+and item-ring depth per direction), records one graph with every
 job's LSQR and FISTA on its own branch, and times graph launches.  Marshalling
 only: all arithmetic runs in liboam.so.
 """
@@ -107,8 +107,11 @@ def main():
                       "op_tflops_algorithmic": flops / (ms * 1e-3) / 1e12,
                       "jobs": [[c["py"], c["px"], c["nz"], c["nt"], round(c["focal_m"] * 1e3, 2),
                                 round(c["aperture_m"] * 1e3, 2)] for c in cfgs],
-                      "tiles": [[B.oam_model_get_tiles(c["_model"].handle, d) for d in (0, 1)] for c in cfgs]
-                      if prec == B.OAM_PREC_BF16X3 else None}))
+                      "tiles": [[B.oam_model_get_tiles(c["_model"].handle, d) + (B.oam_model_get_tiling(c["_model"].handle, d),)
+                                 for d in (0, 1)] for c in cfgs]
+                      if prec == B.OAM_PREC_BF16X3 else None,
+                      "tiles_fields": "per job and direction (forward, adjoint): fold warps, item-ring depth, "
+                                      "position tiling (1 padded grid, 2 scan grid)"}))
     batch.close()
 
 

@@ -24,7 +24,8 @@ EXPORTED = ("oam_build_model", "oam_model_free", "oam_model_get_info", "oam_mode
             "oam_server_create", "oam_server_submit", "oam_server_poll", "oam_server_wait", "oam_server_stats",
             "oam_server_stop", "oam_request_footprint", "oam_bandpass_taps", "oam_model_set_filter",
             "oam_filter_signals", "oam_lsqr_sweep", "oam_lsqr_sweep_work_bytes", "oam_model_get_tiles",
-            "oam_model_set_tiles", "oam_model_bytes", "oam_build_model_ex", "oam_model_bytes_ex")
+            "oam_model_set_tiles", "oam_model_bytes", "oam_build_model_ex", "oam_model_bytes_ex",
+            "oam_model_get_tiling", "oam_model_set_tiling")
 
 OAM_MAX_FIR_HALF = 8191
 OAM_MAX_SWEEP = 32
@@ -139,6 +140,8 @@ def lib():
         L.oam_model_get_tiles.argtypes = [vp, i32, P(i32), P(i32)]
         L.oam_model_bytes.argtypes = [P(OamSensor), P(OamGrid), P(OamEir), i32, P(sz)]
         L.oam_model_set_tiles.argtypes = [vp, i32, i32, i32]
+        L.oam_model_get_tiling.argtypes = [vp, i32, P(i32)]
+        L.oam_model_set_tiling.argtypes = [vp, i32, i32]
         L.oam_batch_create.argtypes = [i32, P(vp)]
         L.oam_batch_set_job.argtypes = [vp, i32, vp, vp, vp, vp, P(OamLsqrOpts), P(OamFistaOpts), vp, sz]
         L.oam_batch_run.argtypes = [vp, vp]
@@ -351,6 +354,20 @@ def oam_model_get_tiles(model, direction):
 
 def oam_model_set_tiles(model, direction, fold_warps, ring=0):
     _check("oam_model_set_tiles", lib().oam_model_set_tiles(model, int(direction), int(fold_warps), int(ring)))
+
+
+TILING_AUTO, TILING_PADDED, TILING_SCAN = 0, 1, 2
+
+
+def oam_model_get_tiling(model, direction):
+    """Position tiling in use by the split-BF16 kernel of one direction: 1 padded grid, 2 scan grid."""
+    t = ctypes.c_int32()
+    _check("oam_model_get_tiling", lib().oam_model_get_tiling(model, int(direction), ctypes.byref(t)))
+    return t.value
+
+
+def oam_model_set_tiling(model, direction, tiling):
+    _check("oam_model_set_tiling", lib().oam_model_set_tiling(model, int(direction), int(tiling)))
 
 
 def oam_batch_create(n_jobs):

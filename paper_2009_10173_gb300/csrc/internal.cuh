@@ -169,6 +169,9 @@ oam_status tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_fwd, i
                        int *warps_adj);
 oam_status tc_set_tiles(oam_model *m, int dir, int fold_warps, int ring);
 void tc_get_tiles(const oam_model *m, int dir, int *fold_warps, int *ring);
+// Position tiling of the split-BF16 kernels (0 auto, 1 padded grid, 2 scan grid).
+oam_status tc_set_tiling(oam_model *m, int dir, int tiling);
+int tc_get_tiling(const oam_model *m, int dir);
 
 // op_fft.cu
 oam_status fft_build(oam_model *m, cudaStream_t st);

@@ -16,21 +16,27 @@
 // and their operand rows are summed before the product:
 //   F[pos][k] = X[pos + (b, a)] + X[pos + (b, -a)] + X[pos + (-b, a)] + X[pos + (-b, -a)]
 // (duplicates dropped when a or b is 0).  One block handles one 128-position
-// tile and one |b|; it stages the FP32 rows y+b and y-b (TMA, 128-byte
+// tile and a group of kBPerBlock consecutive |b|, one after the other into the
+// same accumulator; for each it stages the FP32 rows y+b and y-b (TMA, 128-byte
 // swizzle) and adds them once per stage, sixteen warps build F from two shifted
 // rows of that sum (8 of the stage's 32 K elements each), split it into BF16
 // hi/lo in tensor memory, and one warp walks the items while an elected lane
 // issues the MMAs with A read from tensor memory.  This cuts the MMA count by
 // ~4 for a 61x61 window.
 //
-// Positions use a padded flat index q = y*Wp + x with Wp = px + R, so a lateral
-// offset a is a shift by a rows of a staged strip of 128 + 2R rows.  Padding
-// columns and the R+1 padding rows above and below hold zeros.
+// The iterate is packed with a padded flat index q = y*Wp + x, Wp = px + R
+// (zero columns px .. Wp-1 and R+1 zero rows above and below), so a lateral
+// offset a is a shift by a rows of a staged strip.  A block's 128 positions
+// are consecutive in one of two grids (the position tiling, a tile parameter):
+// the padded grid (o = y*Wp + x; padding positions compute and are dropped;
+// strips of 128 + 2R rows) or the scan grid (o = y*px + x, every lane an
+// output; lane m reads strip row m + R*(rows wrapped before m) + R + a, and a
+// strip holds 128 + (w + 2) R rows for tiles that wrap w scan rows).
 //
 // Each product uses hi = bf16(v), lo = bf16(v - hi) splits of the slab and of
 // the folded iterate: D += F_hi S_hi + F_hi S_lo + F_lo S_hi, accumulated in
 // FP32 in tensor memory.  Each block's tensor-memory sums are written as one
-// partial per |b|; k_sum_parts adds them in index order (this bounds how many
+// partial per |b| group; k_sum_parts adds them in index order (this bounds how many
 // MMA results any one accumulator takes, which keeps the tensor cores' FP32
 // accumulation within 1e-4 of the FP64 oracle).
 #include <cuda.h>
@@ -51,14 +57,19 @@ constexpr int kTileM = 128;        // positions per block
 constexpr int kFoldWarpChoices[] = {4, 8, 16};  // warps that build the folded operand (then run the epilogue)
 constexpr int kDefaultFoldWarps = 8;
 constexpr int kMaxItems = 8;       // item ring depth (slab tile + folded operand)
+constexpr int kBPerBlock = 4;      // consecutive |b| per block (one partial sum per group)
 constexpr int kFoldCols = 32;      // tensor-memory columns per folded operand: 2 chunks x (hi, lo) x 8
 constexpr int kSmemLimit = 227 * 1024;
 
-struct __align__(16) TcItem {
-  uint32_t off16;    // byte offset of the item's tiles in data, in 16-byte units
-  uint32_t bytes;    // total bytes (hi + lo of both tiles)
-  uint16_t col[2];   // accumulator column of each tile
-  uint16_t n[2];     // MMA N of each tile (0 = no tile)
+// One ring item: the slab tiles of one (orbit, stage), hi then lo of each of
+// its two 16-deep chunks; 8 bytes, so a block's item tables stay small.
+struct __align__(8) TcItem {
+  uint32_t off16;  // byte offset of the item's tiles in data, in 16-byte units
+  uint8_t c16[2];  // accumulator column / 16 of each tile
+  uint8_t n16[2];  // MMA N / 16 of each tile (0 = no tile)
+  __host__ __device__ uint32_t col(int c) const { return 16u * c16[c]; }
+  __host__ __device__ uint32_t n(int c) const { return 16u * n16[c]; }
+  __host__ __device__ uint32_t bytes() const { return 64u * (n(0) + n(1)); }  // hi + lo of both tiles
 };
 
 struct TcTile {
@@ -76,12 +87,14 @@ struct TcLayout {
   int in_elems = 0;       // packed elements per position (32 * stages)
   int slot_bytes = 0;     // shared-memory slot per item
   int ring_pref = 0;      // item-ring depth chosen by oam_model_autotune (0 = deepest that fits)
+  int tiling = 0;         // position tiling: 0 auto, 1 padded grid, 2 scan grid
+  std::vector<double> row_cols;  // per |b|: MMA columns x 16 summed over a = 0 .. R and the stages
   int fold_warps = kDefaultFoldWarps;  // fold-warp count chosen by oam_model_autotune (4, 8 or 16)
   TcItem *d_items = nullptr;
   uint8_t *d_data = nullptr;
   size_t data_bytes = 0;
-  double exec_flops = 0;  // MMA flops of one application (3 products, band and tile padding)
-  CUtensorMap tmap;  // FP32 packed input [qtot][in_elems], box 32 x (128 + 2R), 128-byte swizzle
+  CUtensorMap tmap;       // FP32 packed input [qtot][in_elems], box 32 x (128 + 2R), 128-byte swizzle
+  CUtensorMap tmap_scan;  // the same with the scan-grid strip rows (when they fit one box)
 };
 
 }  // namespace oam
@@ -91,12 +104,13 @@ namespace {
 struct CorrParams {
   long long qtot;
   int wp, px, py, R, W, stages;
+  int sp;  // row stride of the grid the position tiles follow: Wp (padded) or px (scan)
   const int *tap_orbit;
   const TcItem *items;  // [n_orb][stages]
   const uint8_t *data;
   int slot_bytes, n_items, strip_rows, strip_bytes, items_bytes;
   int acc_cols, tmem_cols, fold_col0;
-  float *part;         // partial sums [R+1][py*px][acc_cols], one slice per |b|
+  float *part;         // partial sums [groups][py*px][acc_cols], one slice per group of kBPerBlock |b|
   size_t part_stride;  // py*px
   int *status;
   long long budget;
@@ -112,9 +126,25 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 
 // Does row offset `off` put any of the tile's rows inside the grid?
 __device__ __forceinline__ bool row_live(const CorrParams &p, int tile, int off) {
-  const int q0 = tile * kTileM;
-  const int y_first = q0 / p.wp, y_last = (q0 + kTileM - 1) / p.wp;
+  const int o0 = tile * kTileM, o1 = min(o0 + kTileM, p.py * p.sp) - 1;
+  const int y_first = o0 / p.sp, y_last = o1 / p.sp;
   return !(y_last + off < 0 || y_first + off >= p.py);
+}
+
+// Lateral offset |a| of the j-th item of a stage.  Items alternate between
+// the small and the large offsets (0, R, 1, R - 1, ...): the band, and with it
+// the MMA width N, grows with the offset, so each pair of items costs about
+// the same MMA time while its fold work is the same for every pair.
+__device__ __forceinline__ int a_of(int j, int R) { return (j & 1) ? R - (j >> 1) : (j >> 1); }
+
+// Index of the n-th set bit of mask (n counted from 0).
+__device__ __forceinline__ int nth_set(unsigned mask, int n) {
+  for (int i = 0; i < kBPerBlock; ++i)
+    if ((mask >> i) & 1u) {
+      if (n == 0) return i;
+      --n;
+    }
+  return 0;
 }
 
 // Packed FP32 pairs (two lanes of one 64-bit register) and their arithmetic.
@@ -245,17 +275,23 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 512);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 516);
   volatile int *never = reinterpret_cast<volatile int *>(smem + 520);  // stays 0: waits that ignore abort
-  TcItem *sitems = reinterpret_cast<TcItem *>(smem + 1024);           // [stages][R+1] for this |b|
+  TcItem *sitems = reinterpret_cast<TcItem *>(smem + 1024);           // [kBPerBlock][stages][R+1]: the group's items
   uint8_t *strips = smem + 1024 + p.items_bytes;                       // [2 slots][2 rows][strip_bytes]
   uint8_t *slots = strips + 4 * p.strip_bytes;                         // [K][slot_bytes]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x;
-  const int b = (int)blockIdx.y;  // |b|: rows y + b and y - b
-  const int R = p.R, NA = R + 1;  // a = 0 .. R
-  const bool live_p = row_live(p, tile, b), live_m = row_live(p, tile, -b);
-  const bool skip = !live_p && !live_m;
-  const int n_rows = b > 0 ? 2 : 1;
+  const int grp = (int)blockIdx.y;  // |b| = kBPerBlock * grp + i: rows y + b and y - b
+  const int R = p.R, NA = R + 1;    // a = 0 .. R
+  unsigned live = 0;                // group members i whose rows meet the grid
+  for (int i = 0; i < kBPerBlock; ++i) {
+    const int b = kBPerBlock * grp + i;
+    if (b <= R && (row_live(p, tile, b) || row_live(p, tile, -b))) live |= 1u << i;
+  }
+  const bool skip = live == 0;
+  const int y0 = tile * kTileM / p.sp, x0 = tile * kTileM % p.sp;  // the tile's first position
+  const long long qt = (long long)y0 * p.wp + x0;                  // its padded index
+  const int total = __popc(live) * p.stages;  // strip stages of the block: live members in order, stages within
   const int L = p.strip_rows;
 
   if (threadIdx.x == 0) {
@@ -274,11 +310,13 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
     *never = 0;
     ptx::mbar_fence_init();
   }
-  if (!skip) {  // this |b|'s item table, loaded by every thread in one pass
+  if (!skip) {  // the group's item tables [member][stage][item j], loaded by every thread in one pass
     const int n = p.stages * NA;
-    for (int i = threadIdx.x; i < n; i += kThreads) {
-      const int st = i / NA, a = i % NA;
-      sitems[i] = p.items[p.tap_orbit[(b + R) * p.W + (a + R)] * p.stages + st];
+    for (int j = threadIdx.x; j < kBPerBlock * n; j += kThreads) {
+      const int i = j / n, r = j % n, b = kBPerBlock * grp + i;
+      if (!((live >> i) & 1u)) continue;
+      const int st = r / NA, a = a_of(r % NA, R);
+      sitems[j] = p.items[p.tap_orbit[(b + R) * p.W + (a + R)] * p.stages + st];
     }
   }
   if (warp == 1) {
@@ -302,20 +340,23 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
       int k = 0;
       uint32_t lap = 0;  // parity of the item ring's current lap
       bool ok = true;
-      const int q_p = (int)((long long)(R + 1) * p.wp + (long long)tile * kTileM + (long long)b * p.wp - R);
-      const int q_m = (int)((long long)(R + 1) * p.wp + (long long)tile * kTileM - (long long)b * p.wp - R);
-      // Stage st's row pair goes into strip slot st & 1, whose previous stage
-      // (st - 2) the fold warps must have released.  The pair for stage st + 1
-      // is requested right after stage st's first slab tile, about a stage
-      // ahead of its use, instead of after stage st's last tile (which the
-      // item ring throttles to just before the fold warps need the rows).
-      auto load_strips = [&](int stage) {
-        const int s = stage & 1;
-        if (!ptx::mbar_wait(&strip_empty[s], ((stage >> 1) & 1) ^ 1, abort_flag, p.budget)) return false;
+      // Block stage gs (member gs / stages, K stage gs % stages) puts its row
+      // pair into strip slot gs & 1, whose previous stage (gs - 2) the fold
+      // warps must have released.  The pair for stage gs + 1 is requested right
+      // after stage gs's first slab tile, about a stage ahead of its use,
+      // instead of after stage gs's last tile (which the item ring throttles
+      // to just before the fold warps need the rows).
+      auto load_strips = [&](int gs) {
+        const int s = gs & 1, st = gs % p.stages;
+        const int b = kBPerBlock * grp + nth_set(live, gs / p.stages);
+        const int n_rows = b > 0 ? 2 : 1;
+        const int q_p = (int)((long long)(R + 1) * p.wp + qt + (long long)b * p.wp - R);
+        const int q_m = (int)((long long)(R + 1) * p.wp + qt - (long long)b * p.wp - R);
+        if (!ptx::mbar_wait(&strip_empty[s], ((gs >> 1) & 1) ^ 1, abort_flag, p.budget)) return false;
         ptx::mbar_arrive_expect_tx(&strip_full[s], (uint32_t)(n_rows * L * 128));
         uint8_t *dst = strips + (size_t)s * 2 * p.strip_bytes;
-        tma_load_2d(dst, &tmap, kStageK * stage, q_p, &strip_full[s]);
-        if (n_rows == 2) tma_load_2d(dst + p.strip_bytes, &tmap, kStageK * stage, q_m, &strip_full[s]);
+        tma_load_2d(dst, &tmap, kStageK * st, q_p, &strip_full[s]);
+        if (n_rows == 2) tma_load_2d(dst + p.strip_bytes, &tmap, kStageK * st, q_m, &strip_full[s]);
         ++it_strip;
         return true;
       };
@@ -323,28 +364,28 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
         fail(1);
         ok = false;
       }
-      for (int st = 0; st < p.stages && ok; ++st) {
-        const TcItem *row_items = sitems + st * NA;
-        for (int a = 0; a < NA; a += 2) {  // pair slot k holds items a (slot 2k) and a + 1 (slot 2k + 1)
+      for (int gs = 0; gs < total && ok; ++gs) {
+        const TcItem *row_items = sitems + (nth_set(live, gs / p.stages) * p.stages + gs % p.stages) * NA;
+        for (int a = 0; a < NA; a += 2) {  // pair slot k holds items a (slot 2k) and a + 1 (slot 2k + 1) of the stage
           const TcItem ia = row_items[a], ib = a + 1 < NA ? row_items[a + 1] : TcItem{};
           if (!ptx::mbar_wait(&item_empty[k], lap ^ 1, abort_flag, p.budget)) {
             fail(2);
             ok = false;
             break;
           }
-          ptx::mbar_arrive_expect_tx(&slab_full[k], ia.bytes + ib.bytes);
-          if (ia.bytes > 0)
-            ptx::bulk_g2s(slots + (size_t)(2 * k) * p.slot_bytes, p.data + (size_t)ia.off16 * 16, ia.bytes,
+          ptx::mbar_arrive_expect_tx(&slab_full[k], ia.bytes() + ib.bytes());
+          if (ia.bytes() > 0)
+            ptx::bulk_g2s(slots + (size_t)(2 * k) * p.slot_bytes, p.data + (size_t)ia.off16 * 16, ia.bytes(),
                           &slab_full[k]);
-          if (ib.bytes > 0)
-            ptx::bulk_g2s(slots + (size_t)(2 * k + 1) * p.slot_bytes, p.data + (size_t)ib.off16 * 16, ib.bytes,
+          if (ib.bytes() > 0)
+            ptx::bulk_g2s(slots + (size_t)(2 * k + 1) * p.slot_bytes, p.data + (size_t)ib.off16 * 16, ib.bytes(),
                           &slab_full[k]);
           ++it_slab;
           if (++k == KP) {
             k = 0;
             lap ^= 1;
           }
-          if (a == 0 && st + 1 < p.stages && !load_strips(st + 1)) {
+          if (a == 0 && gs + 1 < total && !load_strips(gs + 1)) {
             fail(1);
             ok = false;
             break;
@@ -373,8 +414,8 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
     // B descriptor template (start-address field in 16-byte units; fields never carry)
     const uint64_t slot_desc = ptx::smem_desc(ptx::smem_addr(slots), 0, 128);
     const uint32_t idesc_m128 = ptx::idesc_bf16_f32(kTileM, 0);
-    for (int st = 0; st < p.stages && ok && !skip; ++st) {
-      const TcItem *row_items = sitems + st * NA;
+    for (int gs = 0; gs < total && ok && !skip; ++gs) {
+      const TcItem *row_items = sitems + (nth_set(live, gs / p.stages) * p.stages + gs % p.stages) * NA;
       for (int a = 0; a < NA; a += 2) {
         bool w = ptx::mbar_wait(&slab_full[k], lap, abort_flag, p.budget);
         if (w) w = ptx::mbar_wait(&fold_full[k], lap, abort_flag, p.budget);
@@ -389,12 +430,12 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
           const uint32_t slot = (uint32_t)(2 * k + h);
           const uint32_t a_base = tmem + (uint32_t)p.fold_col0 + 32u * slot;
           const uint64_t dB = slot_desc + (uint64_t)((slot * (uint32_t)p.slot_bytes) >> 4);
-          const uint32_t n0 = item.n[0], n1 = item.n[1];
+          const uint32_t n0 = item.n(0), n1 = item.n(1);
           const uint64_t b0h = dB + ((uint64_t)n0 << 16), b0l = b0h + 2u * n0;  // lbo = 16 n bytes; lo 32 n bytes on
           const uint64_t dB1 = dB + 4u * n0;                                   // second tile 64 n0 bytes later
           const uint64_t b1h = dB1 + ((uint64_t)n1 << 16), b1l = b1h + 2u * n1;
           const uint32_t i0 = idesc_m128 | ((n0 >> 3) << 17), i1 = idesc_m128 | ((n1 >> 3) << 17);
-          const uint32_t d0 = tmem + item.col[0], d1 = tmem + item.col[1];
+          const uint32_t d0 = tmem + item.col(0), d1 = tmem + item.col(1);
           if (leader) {
             // the two chunks accumulate into different columns: interleave them
             if (n0) ptx::mma_bf16_ta(d0, a_base, b0h, i0, 1);
@@ -432,10 +473,13 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
     bool ok = true;
     if (!skip) {
       const int m = 32 * quarter + lane;  // row (tensor-memory lane) this thread folds
+      const int om = tile * kTileM + m;
+      const int pm = (om / p.sp - y0) * p.wp + (om % p.sp - x0);  // its padded offset from the tile's first
       const int q0 = kq * (E / 8);        // first 8-element quarter of the stage
       int it_strip = 0, k = 0;
       uint32_t lap = 0;
-      for (int st = 0; st < p.stages && ok; ++st) {
+      for (int gs = 0; gs < total && ok; ++gs) {
+        const int b = kBPerBlock * grp + nth_set(live, gs / p.stages);
         const int s = it_strip & 1;
         ok = ptx::mbar_wait(&strip_full[s], (it_strip >> 1) & 1, abort_flag, p.budget);
         ok = __all_sync(0xffffffffu, ok);
@@ -464,8 +508,8 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
         for (int a = 0; a < NA; a += 2) {
           const bool two = a + 1 < NA;
           uint32_t w0[E], w1[E];  // folded in registers while the pair slot may still be in use
-          fold_item<E>(X1, m, R, a, q0, w0);
-          if (two) fold_item<E>(X1, m, R, a + 1, q0, w1);
+          fold_item<E>(X1, pm, R, a_of(a, R), q0, w0);
+          if (two) fold_item<E>(X1, pm, R, a_of(a + 1, R), q0, w1);
           ok = ptx::mbar_wait(&item_empty[k], lap ^ 1, abort_flag, p.budget);
           ok = __all_sync(0xffffffffu, ok);
           if (!ok) {
@@ -495,10 +539,10 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
     done = __all_sync(0xffffffffu, done && ok);
     ptx::tc_fence_after();
     const int mrow = 32 * quarter + lane;
-    const long long qf = (long long)tile * kTileM + mrow;
-    const int y = (int)(qf / p.wp), x = (int)(qf % p.wp);
+    const int o = tile * kTileM + mrow;  // this lane's position in the tile grid
+    const int y = o / p.sp, x = o % p.sp;
     const bool valid = done && y < p.py && x < p.px;
-    float *row = p.part + ((size_t)b * p.part_stride + (size_t)y * p.px + x) * p.acc_cols;
+    float *row = p.part + ((size_t)grp * p.part_stride + (size_t)y * p.px + x) * p.acc_cols;
     if (done) {
       for (int j = blk_begin; j < blk_end; ++j) {
         const int col = 32 * j;
@@ -602,6 +646,31 @@ __global__ void k_sum_parts(const float *__restrict__ part, int parts, size_t np
   }
 }
 
+// Strip rows a block stages per row offset: 128 positions wrap at most
+// (px + 126) / px scan rows, each adding R rows of padding to the span, plus
+// R rows of halo on either side.
+int strip_rows_for(int px, int R) { return kTileM + ((px + kTileM - 2) / px + 2) * R; }
+
+// Executed MMA flops of one application: 3 products x 2 x M x (16 x N) over
+// the (position tile, |b|, a >= 0) work items whose rows meet the grid, for
+// position tiles along rows of stride sp.
+double exec_flops_for(const oam_model *m, const TcLayout *L, int sp) {
+  const int R = m->R, py = m->grid.py;
+  const long long n_tiles = ((long long)py * sp + kTileM - 1) / kTileM;
+  double total = 0;
+  for (long long t = 0; t < n_tiles; ++t) {
+    const long long yf = t * kTileM / sp, yl = (std::min(t * kTileM + kTileM, (long long)py * sp) - 1) / sp;
+    for (int b = 0; b <= R; ++b) {
+      const bool lp = !(yl + b < 0 || yf + b >= py), lm = !(yl - b < 0 || yf - b >= py);
+      if (lp || lm) total += L->row_cols[b];
+    }
+  }
+  return 3.0 * 2.0 * kTileM * total;
+}
+
+// Groups of kBPerBlock consecutive |b| = 0 .. R (the kernel's grid y, the partial sums).
+int b_groups(int R) { return (R + 1 + kBPerBlock - 1) / kBPerBlock; }
+
 int pow2_cols(int n) {
   int c = 32;
   while (c < n) c <<= 1;
@@ -688,44 +757,34 @@ oam_status plan_dir(const oam_model *m, TcLayout *L, int dir, std::vector<TcItem
           }
         }
         if (hi <= lo) {
-          it.col[c] = 0;
-          it.n[c] = 0;
+          it.c16[c] = 0;
+          it.n16[c] = 0;
           continue;
         }
         const int col = lo & ~15;
         const int n = ((hi - col) + 15) & ~15;
         if (n > 256 || col + n > L->acc_cols) return OAM_ERR_UNSUPPORTED;
-        it.col[c] = (uint16_t)col;
-        it.n[c] = (uint16_t)n;
+        it.c16[c] = (uint8_t)(col / 16);
+        it.n16[c] = (uint8_t)(n / 16);
         tiles.push_back(TcTile{o, chunk, col, n, off});
         off += 64LL * n;  // hi + lo: 2 x (n rows x 16 elements x 2 bytes)
       }
-      it.bytes = (uint32_t)(off - item_off);
-      max_item = std::max(max_item, (int)it.bytes);
+      if (it.bytes() != (uint32_t)(off - item_off)) return OAM_ERR_DEVICE;  // the tiles are packed back to back
+      max_item = std::max(max_item, (int)it.bytes());
       items[(size_t)o * L->stages + s] = it;
     }
   }
   L->slot_bytes = (max_item + 127) & ~127;
   L->data_bytes = (size_t)std::max<long long>(off, 16);
-  // executed MMA flops of one application: 3 products x 2 x M x (16 x N) over the
-  // (position tile, |b|, a >= 0) work items whose rows meet the grid
+  // MMA columns per |b| (summed over a = 0 .. R); executed flops follow from
+  // the tiles whose rows meet the grid (exec_flops_for)
   {
     std::vector<double> orb_cols(O, 0.0);
     for (const TcTile &t : tiles) orb_cols[t.orbit] += 16.0 * t.n;
-    const int wp = m->grid.px + m->R, W = m->W, R = m->R;
-    const long long n_tiles = ((long long)m->grid.py * wp + kTileM - 1) / kTileM;
-    std::vector<double> row_cols(R + 1, 0.0);
+    const int W = m->W, R = m->R;
+    L->row_cols.assign(R + 1, 0.0);
     for (int b = 0; b <= R; ++b)
-      for (int a = 0; a <= R; ++a) row_cols[b] += orb_cols[m->h_tap_orbit[(b + R) * W + (a + R)]];
-    double total = 0;
-    for (long long t = 0; t < n_tiles; ++t) {
-      const long long yf = t * kTileM / wp, yl = (t * kTileM + kTileM - 1) / wp;
-      for (int b = 0; b <= R; ++b) {
-        const bool lp = !(yl + b < 0 || yf + b >= m->grid.py), lm = !(yl - b < 0 || yf - b >= m->grid.py);
-        if (lp || lm) total += row_cols[b];
-      }
-    }
-    L->exec_flops = 3.0 * 2.0 * kTileM * total;
+      for (int a = 0; a <= R; ++a) L->row_cols[b] += orb_cols[m->h_tap_orbit[(b + R) * W + (a + R)]];
   }
   return OAM_OK;
 }
@@ -756,15 +815,17 @@ oam_status build_dir(oam_model *m, TcLayout *L, int dir, cudaStream_t st, int *d
 struct Launch {
   CorrParams p;
   size_t smem;
+  int tiling;   // 1 padded grid, 2 scan grid
+  int n_tiles;  // position tiles (the grid's x)
 };
 
 oam_status plan_launch(const oam_model *m, const TcLayout *L, Launch *out) {
-  const int R = m->R;
+  const int R = m->R, px = m->grid.px, py = m->grid.py;
   CorrParams p{};
   p.qtot = m->tc_qtot;
-  p.wp = m->grid.px + R;
-  p.px = m->grid.px;
-  p.py = m->grid.py;
+  p.wp = px + R;
+  p.px = px;
+  p.py = py;
   p.R = R;
   p.W = m->W;
   p.stages = L->stages;
@@ -772,13 +833,25 @@ oam_status plan_launch(const oam_model *m, const TcLayout *L, Launch *out) {
   p.items = L->d_items;
   p.data = L->d_data;
   p.slot_bytes = L->slot_bytes;
-  p.strip_rows = kTileM + 2 * R;
-  p.strip_bytes = (p.strip_rows * 128 + 1023) & ~1023;  // 128-byte rows, 1024-byte aligned
-  p.items_bytes = (int)((sizeof(TcItem) * L->stages * (R + 1) + 1023) & ~size_t(1023));
-  const int fixed = 1024 /* alignment slack */ + 1024 + p.items_bytes + 4 * p.strip_bytes;
+  p.items_bytes = (int)((sizeof(TcItem) * kBPerBlock * L->stages * (R + 1) + 1023) & ~size_t(1023));
   p.fold_col0 = (L->acc_cols + 31) & ~31;
   const int tmem_items = (512 - p.fold_col0) / kFoldCols;
-  p.n_items = std::min(kMaxItems, std::min(tmem_items, (kSmemLimit - fixed) / L->slot_bytes));
+  auto strip_bytes = [](int rows) { return (rows * 128 + 1023) & ~1023; };  // 128-byte rows, 1024-byte aligned
+  auto fixed_for = [&](int rows) { return 1024 /* alignment slack */ + 1024 + p.items_bytes + 4 * strip_bytes(rows); };
+  auto ring_for = [&](int rows) {  // deepest ring (whole pairs) that shared and tensor memory hold
+    const int n = std::min(kMaxItems, std::min(tmem_items, (kSmemLimit - fixed_for(rows)) / L->slot_bytes));
+    return n < 0 ? 0 : n & ~1;
+  };
+  const int rows_pad = kTileM + 2 * R, rows_scan = strip_rows_for(px, R);
+  int tiling = L->tiling;
+  if (tiling == 0)  // the scan grid unless its longer strips cost ring depth
+    tiling = rows_scan <= 256 && ring_for(rows_scan) >= ring_for(rows_pad) ? 2 : 1;
+  if (tiling == 2 && rows_scan > 256) return OAM_ERR_UNSUPPORTED;
+  p.sp = tiling == 2 ? px : p.wp;
+  p.strip_rows = tiling == 2 ? rows_scan : rows_pad;
+  p.strip_bytes = strip_bytes(p.strip_rows);
+  const int fixed = fixed_for(p.strip_rows);
+  p.n_items = ring_for(p.strip_rows);
   if (L->ring_pref >= 2) p.n_items = std::min(p.n_items, L->ring_pref);
   p.n_items &= ~1;  // items go in pairs (one fold pass each)
   if (p.n_items < 2) return OAM_ERR_UNSUPPORTED;
@@ -786,11 +859,13 @@ oam_status plan_launch(const oam_model *m, const TcLayout *L, Launch *out) {
   p.tmem_cols = 32;
   while (p.tmem_cols < p.fold_col0 + kFoldCols * p.n_items) p.tmem_cols <<= 1;
   p.part = m->d_tc_part;
-  p.part_stride = (size_t)m->grid.py * m->grid.px;
+  p.part_stride = (size_t)py * px;
   p.status = m->d_status;
   p.budget = 4000000000LL;  // ~2 s at 2 GHz
   out->p = p;
   out->smem = (size_t)fixed + (size_t)p.n_items * p.slot_bytes;
+  out->tiling = tiling;
+  out->n_tiles = (int)(((long long)py * p.sp + kTileM - 1) / kTileM);
   if (out->smem > (size_t)kSmemLimit) return OAM_ERR_UNSUPPORTED;
   return OAM_OK;
 }
@@ -798,7 +873,7 @@ oam_status plan_launch(const oam_model *m, const TcLayout *L, Launch *out) {
 template <int FW>
 oam_status launch_fold(const Launch &lp, const TcLayout *L, dim3 grid, cudaStream_t st) {
   OAM_CUDA_TRY(cudaFuncSetAttribute(k_corr_fold<FW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lp.smem));
-  k_corr_fold<FW><<<grid, 64 + 32 * FW, lp.smem, st>>>(L->tmap, lp.p);
+  k_corr_fold<FW><<<grid, 64 + 32 * FW, lp.smem, st>>>(lp.tiling == 2 ? L->tmap_scan : L->tmap, lp.p);
   OAM_LAUNCHED();
   return OAM_OK;
 }
@@ -817,10 +892,9 @@ oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int 
                                          m->grid.py, reinterpret_cast<float4 *>(m->d_tc_pack));
     OAM_LAUNCHED();
   }
-  const int n_tiles = (int)(((long long)m->grid.py * (m->grid.px + R) + kTileM - 1) / kTileM);
   {
     ProfScope prof(m, st, L->dir == 0);
-    const dim3 grid(n_tiles, R + 1);
+    const dim3 grid(lp.n_tiles, b_groups(R));
     if (L->fold_warps == 4) rc = launch_fold<4>(lp, L, grid, st);
     else if (L->fold_warps == 16) rc = launch_fold<16>(lp, L, grid, st);
     else rc = launch_fold<8>(lp, L, grid, st);
@@ -828,7 +902,7 @@ oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int 
   }
   const size_t npos = (size_t)m->grid.py * m->grid.px;
   const int blocks = (int)std::min<size_t>((npos * out_len + 255) / 256, 16ull * m->sm_count);
-  k_sum_parts<<<blocks, 256, 0, st>>>(m->d_tc_part, R + 1, npos, L->acc_cols, L->out_lo, out_len, out);
+  k_sum_parts<<<blocks, 256, 0, st>>>(m->d_tc_part, b_groups(R), npos, L->acc_cols, L->out_lo, out_len, out);
   OAM_LAUNCHED();
   return OAM_OK;
 }
@@ -838,7 +912,7 @@ oam_status run_corr(const oam_model *m, const TcLayout *L, const float *in, int 
 // Device bytes tc_build allocates, from the planned bands (host only; no
 // device call).  Fails like tc_build on shapes the kernels do not take.
 oam_status oam::tc_plan_bytes(const oam_model *m, size_t *bytes) {
-  if (kTileM + 2 * m->R > 256) return OAM_ERR_UNSUPPORTED;
+  if (kTileM + 2 * m->R > 256) return OAM_ERR_UNSUPPORTED;  // padded-grid strip rows per TMA box
   TcLayout Lf, La;
   std::vector<TcItem> items;
   std::vector<TcTile> tiles;
@@ -855,13 +929,13 @@ oam_status oam::tc_plan_bytes(const oam_model *m, size_t *bytes) {
   const long long qtot = (long long)(m->grid.py + 2 * m->R + 2) * wp + 256;
   if (qtot > 0x7fffffffLL) return OAM_ERR_UNSUPPORTED;
   b += alloc_bytes<uint8_t>((size_t)std::max(Lf.in_elems, La.in_elems) * qtot * sizeof(float));
-  b += alloc_bytes<float>((size_t)(m->R + 1) * m->grid.py * m->grid.px * std::max(Lf.acc_cols, La.acc_cols));
+  b += alloc_bytes<float>((size_t)b_groups(m->R) * m->grid.py * m->grid.px * std::max(Lf.acc_cols, La.acc_cols));
   *bytes = b;
   return OAM_OK;
 }
 
 oam_status oam::tc_build(oam_model *m, cudaStream_t st) {
-  if (kTileM + 2 * m->R > 256) return OAM_ERR_UNSUPPORTED;  // strip rows per TMA box
+  if (kTileM + 2 * m->R > 256) return OAM_ERR_UNSUPPORTED;  // padded-grid strip rows per TMA box
   int *d_band_hi = nullptr;
   const size_t nb = (size_t)m->n_orb * m->grid.nz;
   OAM_CUDA_TRY(cudaMallocAsync((void **)&d_band_hi, sizeof(int) * nb, st));
@@ -882,14 +956,19 @@ oam_status oam::tc_build(oam_model *m, cudaStream_t st) {
   for (TcLayout *L : {m->tc_fwd, m->tc_adj}) {
     rc = encode_tmap(&L->tmap, reinterpret_cast<float *>(m->d_tc_pack), m->tc_qtot, L->in_elems, kTileM + 2 * m->R);
     if (rc) return rc;
+    if (strip_rows_for(m->grid.px, m->R) <= 256) {
+      rc = encode_tmap(&L->tmap_scan, reinterpret_cast<float *>(m->d_tc_pack), m->tc_qtot, L->in_elems,
+                       strip_rows_for(m->grid.px, m->R));
+      if (rc) return rc;
+    }
     Launch lp;
     rc = plan_launch(m, L, &lp);
     if (rc) return rc;
   }
-  // One partial per (position, |b|): bounds the MMA results summed into one
-  // tensor-memory accumulator; the parts are added in FP32 in a fixed order.
+  // One partial per (position, |b| group): bounds the MMA results summed into
+  // one tensor-memory accumulator; the parts are added in FP32 in a fixed order.
   const int acc = std::max(m->tc_fwd->acc_cols, m->tc_adj->acc_cols);
-  rc = dev_alloc(m, &m->d_tc_part, (size_t)(m->R + 1) * m->grid.py * m->grid.px * acc);
+  rc = dev_alloc(m, &m->d_tc_part, (size_t)b_groups(m->R) * m->grid.py * m->grid.px * acc);
   if (rc) return rc;
   return OAM_OK;
 }
@@ -910,7 +989,9 @@ void oam::tc_free(oam_model *m, cudaStream_t st) {
 
 double oam::tc_exec_flops(const oam_model *m, int dir) {
   const TcLayout *L = dir == 0 ? m->tc_fwd : m->tc_adj;
-  return L ? L->exec_flops : 0.0;
+  Launch lp;
+  if (!L || plan_launch(m, L, &lp)) return 0.0;
+  return exec_flops_for(m, L, lp.p.sp);
 }
 
 oam_status oam::forward_tc(const oam_model *m, const float *H, float *s, cudaStream_t st) {
@@ -922,8 +1003,8 @@ oam_status oam::adjoint_tc(const oam_model *m, const float *s, float *H, cudaStr
 }
 
 // ---------------------------------------------------------------- autotuner
-// Per direction, time every (fold-warp count, ring depth) pair on the model's
-// own shapes (CUDA events on `st`) and keep the fastest.
+// Per direction, time every (position tiling, fold-warp count, ring depth) on
+// the model's own shapes (CUDA events on `st`) and keep the fastest.
 oam_status oam::tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_fwd, int *best_adj, int *warps_fwd,
                             int *warps_adj) {
   if (!m->tc_fwd) return OAM_ERR_UNSUPPORTED;
@@ -940,34 +1021,39 @@ oam_status oam::tc_autotune(oam_model *m, int reps, cudaStream_t st, int *best_f
   cudaMemsetAsync(buf, 0, (nv + ns) * sizeof(float), st);
   for (int dir = 0; dir < 2 && !rc; ++dir) {
     TcLayout *L = dir == 0 ? m->tc_fwd : m->tc_adj;
-    L->ring_pref = 0;
-    Launch lp;
-    if ((rc = plan_launch(m, L, &lp))) break;
-    const int deepest = lp.p.n_items;
     float best_ms = 1e30f;
-    int best = deepest, best_w = kDefaultFoldWarps;
-    for (int fw : kFoldWarpChoices) {
-      L->fold_warps = fw;
-      for (int depth = 2; depth <= deepest; depth += 2) {
-        L->ring_pref = depth;
-        for (int r = 0; r <= reps && !rc; ++r) {  // first run warms up
-          if (r == 1) cudaEventRecord(e0, st);
-          rc = dir == 0 ? run_corr(m, L, buf, m->grid.nz, buf + nv, m->grid.nt, st)
-                        : run_corr(m, L, buf + nv, m->grid.nt, buf, m->grid.nz, st);
+    int best = 0, best_w = kDefaultFoldWarps, best_t = 0;
+    for (int tiling = 1; tiling <= 2 && !rc; ++tiling) {
+      L->tiling = tiling;
+      L->ring_pref = 0;
+      Launch lp;
+      if (plan_launch(m, L, &lp)) continue;  // this tiling does not fit the model
+      const int deepest = lp.p.n_items;
+      for (int fw : kFoldWarpChoices) {
+        L->fold_warps = fw;
+        for (int depth = 2; depth <= deepest; depth += 2) {
+          L->ring_pref = depth;
+          for (int r = 0; r <= reps && !rc; ++r) {  // first run warms up
+            if (r == 1) cudaEventRecord(e0, st);
+            rc = dir == 0 ? run_corr(m, L, buf, m->grid.nz, buf + nv, m->grid.nt, st)
+                          : run_corr(m, L, buf + nv, m->grid.nt, buf, m->grid.nz, st);
+          }
+          cudaEventRecord(e1, st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) rc = OAM_ERR_CUDA;
+          if (rc) break;
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = depth;
+            best_w = fw;
+            best_t = tiling;
+          }
         }
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) rc = OAM_ERR_CUDA;
         if (rc) break;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = depth;
-          best_w = fw;
-        }
       }
-      if (rc) break;
     }
+    L->tiling = best_t;
     L->ring_pref = best;
     L->fold_warps = best_w;
     (dir == 0 ? *best_fwd : *best_adj) = best;
@@ -996,6 +1082,24 @@ oam_status oam::tc_set_tiles(oam_model *m, int dir, int fold_warps, int ring) {
     return rc ? rc : OAM_ERR_INVALID_ARG;
   }
   return OAM_OK;
+}
+
+oam_status oam::tc_set_tiling(oam_model *m, int dir, int tiling) {
+  TcLayout *L = dir == 0 ? m->tc_fwd : m->tc_adj;
+  if (!L) return OAM_ERR_UNSUPPORTED;
+  if (tiling < 0 || tiling > 2) return OAM_ERR_INVALID_ARG;
+  const int keep = L->tiling;
+  L->tiling = tiling;
+  Launch lp;
+  const oam_status rc = plan_launch(m, L, &lp);
+  if (rc) L->tiling = keep;
+  return rc;
+}
+
+int oam::tc_get_tiling(const oam_model *m, int dir) {
+  const TcLayout *L = dir == 0 ? m->tc_fwd : m->tc_adj;
+  Launch lp;
+  return L && plan_launch(m, L, &lp) == OAM_OK ? lp.tiling : 0;
 }
 
 void oam::tc_get_tiles(const oam_model *m, int dir, int *fold_warps, int *ring) {

@@ -48,6 +48,19 @@ extern "C" oam_status oam_model_set_tiles(oam_model *m, int32_t direction, int32
   return tc_set_tiles(m, direction, fold_warps, ring);
 }
 
+extern "C" oam_status oam_model_get_tiling(const oam_model *m, int32_t direction, int32_t *tiling) {
+  if (!m || (direction != 0 && direction != 1) || !tiling) return OAM_ERR_INVALID_ARG;
+  if (m->precision != OAM_PREC_BF16X3) return OAM_ERR_UNSUPPORTED;
+  *tiling = tc_get_tiling(m, direction);
+  return OAM_OK;
+}
+
+extern "C" oam_status oam_model_set_tiling(oam_model *m, int32_t direction, int32_t tiling) {
+  if (!m || (direction != 0 && direction != 1)) return OAM_ERR_INVALID_ARG;
+  if (m->precision != OAM_PREC_BF16X3) return OAM_ERR_UNSUPPORTED;
+  return tc_set_tiling(m, direction, tiling);
+}
+
 // ---------------------------------------------------------------- batch
 struct oam_batch {
   struct Job {

@@ -32,6 +32,7 @@ def main():
         p.add_argument(f"--{k}", type=int, default=None)
     p.add_argument("--fold-warps", type=int, default=None, help="split-BF16 kernels: fold warps (4, 8, 16)")
     p.add_argument("--ring", type=int, default=0, help="split-BF16 kernels: item-ring depth (0 = deepest)")
+    p.add_argument("--tiling", type=int, default=None, help="split-BF16 kernels: 0 auto, 1 padded grid, 2 scan grid")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=1)
     a = p.parse_args()
@@ -42,6 +43,9 @@ def main():
     if a.fold_warps is not None and prec == B.OAM_PREC_BF16X3:
         for d in (0, 1):
             B.oam_model_set_tiles(m.handle, d, a.fold_warps, a.ring)
+    if a.tiling is not None and prec == B.OAM_PREC_BF16X3:
+        for d in (0, 1):
+            B.oam_model_set_tiling(m.handle, d, a.tiling)
     H = torch.from_numpy(inputs.phantom(cfg, 1, count=20)).float().cuda()
     s = m.forward(H)
     iters = a.iters or 5
@@ -70,7 +74,7 @@ def main():
                       "ms_per_call": ms, "flops_per_op": m.info.flops_per_op,
                       "alg_tflops": m.info.flops_per_op / ms / 1e9 if a.op in ("forward", "adjoint") else None,
                       "model_bytes": m.info.device_bytes, "op_bytes": m.info.op_bytes,
-                      "tiles": [B.oam_model_get_tiles(m.handle, d) for d in (0, 1)]
+                      "tiles": [B.oam_model_get_tiles(m.handle, d) + (B.oam_model_get_tiling(m.handle, d),) for d in (0, 1)]
                       if prec == B.OAM_PREC_BF16X3 else None, **extra}))
     m.close()
 

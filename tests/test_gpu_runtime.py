@@ -143,23 +143,30 @@ def test_autotune_keeps_results():
 
 @pytest.mark.parametrize("name", ["job", "ragged"])
 def test_every_tile_shape_gives_the_same_bits(name):
-    """Fold-warp count and ring depth change how the work is spread over the
-    block, not the order of any sum: results are bit-identical."""
+    """Position tiling, fold-warp count and ring depth change how the work is
+    spread over blocks and warps, not the order of any sum: results are
+    bit-identical."""
     cfg = JOBS[2] if name == "job" else configs.scaled(configs.TINY_32, px=70, py=37, nz=52, nt=200, win=15,
                                                         n_patches=800, dz_m=8e-6, z0_rel_m=-200e-6)
     m = Model(cfg, precision=B.OAM_PREC_BF16X3)
     H = torch.from_numpy(inputs.gaussian(m.vol_shape, 15).astype(np.float32)).cuda()
     s = torch.from_numpy(inputs.gaussian(m.sig_shape, 16).astype(np.float32)).cuda()
     ref_f, ref_a = None, None
-    for w in (4, 8, 16):
-        for ring in (0, 2, 4):
-            for d in (0, 1):
-                B.oam_model_set_tiles(m.handle, d, w, ring)
-                assert B.oam_model_get_tiles(m.handle, d)[0] == w
-            f, a = m.forward(H).cpu().numpy(), m.adjoint(s).cpu().numpy()
-            if ref_f is None:
-                ref_f, ref_a = f, a
-            assert np.array_equal(f, ref_f) and np.array_equal(a, ref_a), (w, ring)
+    for tiling in (B.TILING_PADDED, B.TILING_SCAN):
+        for d in (0, 1):
+            B.oam_model_set_tiling(m.handle, d, tiling)
+            assert B.oam_model_get_tiling(m.handle, d) == tiling
+        for w in (4, 8, 16):
+            for ring in (0, 2, 4):
+                for d in (0, 1):
+                    B.oam_model_set_tiles(m.handle, d, w, ring)
+                    assert B.oam_model_get_tiles(m.handle, d)[0] == w
+                f, a = m.forward(H).cpu().numpy(), m.adjoint(s).cpu().numpy()
+                if ref_f is None:
+                    ref_f, ref_a = f, a
+                assert np.array_equal(f, ref_f) and np.array_equal(a, ref_a), (tiling, w, ring)
+    with pytest.raises(B.OamError):
+        B.oam_model_set_tiling(m.handle, 0, 3)  # not a tiling
     with pytest.raises(B.OamError):
         B.oam_model_set_tiles(m.handle, 0, 6, 0)  # 6 fold warps: not a kernel shape
     with pytest.raises(B.OamError):

@@ -272,3 +272,46 @@ def test_fir_schedule_computes_the_convolution(lgNF, L):
     full = np.concatenate([h[:0:-1], h])
     want = np.convolve(x, full)[L:L + nt]
     assert np.allclose(a[:nt], want, atol=1e-10 * np.abs(want).max())
+
+
+# ------------------------------------------------------------------ k_corr_fold
+def strip_rows_for(px, R):
+    return 128 + ((px + 126) // px + 2) * R
+
+
+@pytest.mark.parametrize("tiling", ["padded", "scan"])
+@pytest.mark.parametrize("px,py,R", [(32, 32, 5), (24, 20, 3), (64, 64, 30), (96, 96, 30), (128, 128, 30),
+                                     (160, 160, 30), (200, 200, 30), (256, 256, 30), (33, 7, 4), (1, 9, 5)])
+def test_corr_fold_strip_rows_hold_every_tap_of_every_lane(px, py, R, tiling):
+    """Tiles of 128 consecutive positions of the padded grid (stride Wp = px + R)
+    or the scan grid (stride px): lane m of tile t reads strip row pm + R + a,
+    pm its padded offset from the tile's first position, of the strip that
+    starts at padded index (R+1)*Wp + q_t + b*Wp - R.  That row must lie in the
+    staged strip and be the padded index of (y + b, x + a), which is a zero
+    padding column when x + a falls outside the row."""
+    wp = px + R
+    sp = px if tiling == "scan" else wp
+    rows = strip_rows_for(px, R) if tiling == "scan" else 128 + 2 * R
+    for t in range((py * sp + 127) // 128):
+        y0, x0 = t * 128 // sp, t * 128 % sp
+        qt = y0 * wp + x0
+        m = np.arange(128)
+        o = t * 128 + m
+        y, x = o // sp, o % sp
+        pm = (y - y0) * wp + (x - x0)
+        if tiling == "padded":
+            assert np.array_equal(pm, m)
+        for a in (-R, -1, 0, 1, R):
+            r = pm + R + a
+            assert r.min() >= 0 and r.max() < rows
+            for b in (-R, 0, R):
+                start = (R + 1) * wp + qt + b * wp - R
+                q = start + r
+                assert np.array_equal(q, (y + b + R + 1) * wp + x + a)
+                col = q % wp
+                out = x < px  # lanes whose results are kept (padding positions of the padded grid are dropped)
+                inside = (x + a >= 0) & (x + a < px)
+                assert np.array_equal(col[inside & out], (x + a)[inside & out])
+                assert (col[~inside & out] >= px).all()
+    if R <= 30 and px >= 64 or tiling == "padded":
+        assert rows <= 256  # one TMA box
