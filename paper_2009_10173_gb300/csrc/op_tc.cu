@@ -269,15 +269,19 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
   // items go in pairs (the two taps of one fold pass), one set of barriers per pair
   const int K = p.n_items, KP = K / 2;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-  uint64_t *strip_full = bars, *strip_empty = bars + 2;
-  uint64_t *acc_ready = bars + 4, *acc_full = bars + 5;
-  uint64_t *slab_full = bars + 6, *fold_full = bars + 6 + KP, *item_empty = bars + 6 + 2 * KP;
+  uint64_t *strip_full = bars, *strip_empty = bars + 3;  // one pair per strip buffer
+  uint64_t *acc_ready = bars + 6, *acc_full = bars + 7;
+  uint64_t *slab_full = bars + 8, *fold_full = bars + 8 + KP, *item_empty = bars + 8 + 2 * KP;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 512);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 516);
   volatile int *never = reinterpret_cast<volatile int *>(smem + 520);  // stays 0: waits that ignore abort
   TcItem *sitems = reinterpret_cast<TcItem *>(smem + 1024);           // [kBPerBlock][stages][R+1]: the group's items
-  uint8_t *strips = smem + 1024 + p.items_bytes;                       // [2 slots][2 rows][strip_bytes]
-  uint8_t *slots = strips + 4 * p.strip_bytes;                         // [K][slot_bytes]
+  // Three strip buffers in rotation: stage gs stages its row y+b in buffer
+  // gs % 3 (which then holds P = X(y+b) + X(y-b)) and its row y-b in buffer
+  // (gs + 1) % 3, free again once P is formed, so stage gs + 1 reuses it and
+  // the buffer stage gs - 1 held P.
+  uint8_t *strips = smem + 1024 + p.items_bytes;                       // [3][strip_bytes]
+  uint8_t *slots = strips + 3 * p.strip_bytes;                         // [K][slot_bytes]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x;
@@ -295,7 +299,7 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
   const int L = p.strip_rows;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
       ptx::mbar_init(&strip_full[i], 1);
       ptx::mbar_init(&strip_empty[i], kFoldWarps);
     }
@@ -336,28 +340,31 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0 && !skip) {
-      int it_strip = 0, it_slab = 0;
+      int it_slab = 0;
+      int uses[3] = {0, 0, 0};  // loads issued per strip buffer (one full / empty phase each)
       int k = 0;
       uint32_t lap = 0;  // parity of the item ring's current lap
       bool ok = true;
-      // Block stage gs (member gs / stages, K stage gs % stages) puts its row
-      // pair into strip slot gs & 1, whose previous stage (gs - 2) the fold
-      // warps must have released.  The pair for stage gs + 1 is requested right
-      // after stage gs's first slab tile, about a stage ahead of its use,
-      // instead of after stage gs's last tile (which the item ring throttles
-      // to just before the fold warps need the rows).
+      // Block stage gs (member gs / stages, K stage gs % stages) loads row y+b
+      // into buffer gs % 3 and row y-b into buffer (gs + 1) % 3 (a load of no
+      // bytes for b = 0), each once the fold warps have released the buffer's
+      // previous use.  The rows for stage gs + 1 are requested right after
+      // stage gs's first slab tile, about a stage ahead of their use, instead
+      // of after stage gs's last tile (which the item ring throttles to just
+      // before the fold warps need the rows).
       auto load_strips = [&](int gs) {
-        const int s = gs & 1, st = gs % p.stages;
+        const int st = gs % p.stages;
         const int b = kBPerBlock * grp + nth_set(live, gs / p.stages);
-        const int n_rows = b > 0 ? 2 : 1;
         const int q_p = (int)((long long)(R + 1) * p.wp + qt + (long long)b * p.wp - R);
         const int q_m = (int)((long long)(R + 1) * p.wp + qt - (long long)b * p.wp - R);
-        if (!ptx::mbar_wait(&strip_empty[s], ((gs >> 1) & 1) ^ 1, abort_flag, p.budget)) return false;
-        ptx::mbar_arrive_expect_tx(&strip_full[s], (uint32_t)(n_rows * L * 128));
-        uint8_t *dst = strips + (size_t)s * 2 * p.strip_bytes;
-        tma_load_2d(dst, &tmap, kStageK * st, q_p, &strip_full[s]);
-        if (n_rows == 2) tma_load_2d(dst + p.strip_bytes, &tmap, kStageK * st, q_m, &strip_full[s]);
-        ++it_strip;
+        for (int r = 0; r < 2; ++r) {
+          const int s = (gs + r) % 3;
+          if (!ptx::mbar_wait(&strip_empty[s], (uses[s] & 1) ^ 1, abort_flag, p.budget)) return false;
+          const bool load = r == 0 || b > 0;
+          ptx::mbar_arrive_expect_tx(&strip_full[s], load ? (uint32_t)(L * 128) : 0u);
+          if (load) tma_load_2d(strips + (size_t)s * p.strip_bytes, &tmap, kStageK * st, r == 0 ? q_p : q_m, &strip_full[s]);
+          ++uses[s];
+        }
         return true;
       };
       if (!load_strips(0)) {
@@ -396,8 +403,8 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
         // let copies already issued land before the block exits
         for (int i = std::max(0, it_slab - KP); i < it_slab; ++i)
           ptx::mbar_wait(&slab_full[i % KP], (i / KP) & 1, never, p.budget);
-        for (int i = std::max(0, it_strip - 2); i < it_strip; ++i)
-          ptx::mbar_wait(&strip_full[i & 1], (i >> 1) & 1, never, p.budget);
+        for (int s = 0; s < 3; ++s)  // each buffer's last load (earlier ones were consumed before it was issued)
+          if (uses[s] > 0) ptx::mbar_wait(&strip_full[s], (uses[s] - 1) & 1, never, p.budget);
       }
     }
   } else if (warp == 1) {
@@ -476,22 +483,23 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
       const int om = tile * kTileM + m;
       const int pm = (om / p.sp - y0) * p.wp + (om % p.sp - x0);  // its padded offset from the tile's first
       const int q0 = kq * (E / 8);        // first 8-element quarter of the stage
-      int it_strip = 0, k = 0;
+      int uses[3] = {0, 0, 0}, k = 0;  // strip buffer uses consumed, as the producer counts them
       uint32_t lap = 0;
       for (int gs = 0; gs < total && ok; ++gs) {
         const int b = kBPerBlock * grp + nth_set(live, gs / p.stages);
-        const int s = it_strip & 1;
-        ok = ptx::mbar_wait(&strip_full[s], (it_strip >> 1) & 1, abort_flag, p.budget);
+        const int s = gs % 3, s2 = (gs + 1) % 3;
+        ok = ptx::mbar_wait(&strip_full[s], uses[s] & 1, abort_flag, p.budget);
+        if (ok) ok = ptx::mbar_wait(&strip_full[s2], uses[s2] & 1, abort_flag, p.budget);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) {
           if (lane == 0) fail(32);
           break;
         }
-        float *X1 = reinterpret_cast<float *>(strips + (size_t)s * 2 * p.strip_bytes);
+        float *X1 = reinterpret_cast<float *>(strips + (size_t)s * p.strip_bytes);
         if (b > 0) {
           // P = X(y+b) + X(y-b) in place: both strips share the swizzle, so the
           // sum runs over physical float4s.
-          const float4 *X2 = reinterpret_cast<const float4 *>(strips + (size_t)s * 2 * p.strip_bytes + p.strip_bytes);
+          const float4 *X2 = reinterpret_cast<const float4 *>(strips + (size_t)s2 * p.strip_bytes);
           float4 *P4 = reinterpret_cast<float4 *>(X1);
           for (int i = threadIdx.x - 64; i < L * 8; i += 32 * kFoldWarps) {
             float4 u = P4[i];
@@ -504,6 +512,9 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
           }
           asm volatile("bar.sync 1, %0;" ::"r"(32 * kFoldWarps) : "memory");  // fold warps only
         }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&strip_empty[s2]);  // row y-b is folded into P (or was not loaded)
+        ++uses[s2];
         // two items (a, a + 1) per pass, in pair slot k: one wait, fence and barrier step for both
         for (int a = 0; a < NA; a += 2) {
           const bool two = a + 1 < NA;
@@ -530,7 +541,7 @@ __global__ void __launch_bounds__(64 + 32 * FW, 1)
         }
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&strip_empty[s]);
-        ++it_strip;
+        ++uses[s];
       }
     }
 
@@ -837,7 +848,7 @@ oam_status plan_launch(const oam_model *m, const TcLayout *L, Launch *out) {
   p.fold_col0 = (L->acc_cols + 31) & ~31;
   const int tmem_items = (512 - p.fold_col0) / kFoldCols;
   auto strip_bytes = [](int rows) { return (rows * 128 + 1023) & ~1023; };  // 128-byte rows, 1024-byte aligned
-  auto fixed_for = [&](int rows) { return 1024 /* alignment slack */ + 1024 + p.items_bytes + 4 * strip_bytes(rows); };
+  auto fixed_for = [&](int rows) { return 1024 /* alignment slack */ + 1024 + p.items_bytes + 3 * strip_bytes(rows); };
   auto ring_for = [&](int rows) {  // deepest ring (whole pairs) that shared and tensor memory hold
     const int n = std::min(kMaxItems, std::min(tmem_items, (kSmemLimit - fixed_for(rows)) / L->slot_bytes));
     return n < 0 ? 0 : n & ~1;
