@@ -30,12 +30,12 @@ LSQR_ITERS, FISTA_ITERS, POWER_ITERS, LAMBDA_REL = 50, 100, 20, 1e-3
 # operator applications per step: LSQR 1 + 2*50; FISTA 2*20 power + 1 lambda + 2*100
 OPS_PER_STEP = (1 + 2 * LSQR_ITERS) + (2 * POWER_ITERS + 1 + 2 * FISTA_ITERS)
 FP32_LANES_PER_SM = 128
-# DRAM bytes per launch of the tensor-core operator kernel (k_corr_fold) on this
-# workload: dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of the
-# same kernel on a 96x96-position case of this workload, scaled by blocks
-# processed (profiles/k_corr_fold_fwd_96x96x300_win61.md).  None until the
-# current kernel has been captured.
-TC_TRAFFIC_BYTES = None
+# DRAM bytes per launch of the tensor-core operator kernel (k_corr_fold) per
+# direction on this workload: dram__bytes_read.sum + dram__bytes_write.sum of an
+# ncu capture of the same kernel on a 96x96-position case of this workload (576
+# blocks), scaled by blocks processed (2504 / 576; profiles/k_corr_fold_fwd_ and
+# k_corr_fold_adj_96x96x300_win61.md).  Set to None when the kernel changes.
+TC_TRAFFIC_BYTES = {"forward": (106.70e6 + 61.04e6) * 2504 / 576, "adjoint": (100.98e6 + 56.94e6) * 2504 / 576}
 # DRAM bytes per application of the lateral-FFT form on this workload:
 # dram__bytes_read.sum + dram__bytes_write.sum over the five launches of one
 # forward, from an ncu capture of the full 200x200x300 workload (1.191 GB read,
@@ -735,7 +735,8 @@ def run_ours(args, rank, world, acc=None):
     else:
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         roof = {"bound": "tensor", "kernel": f"{dom} (tcgen05 split-BF16, mirror-folded)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": TC_TRAFFIC_BYTES,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": TC_TRAFFIC_BYTES[dom] if TC_TRAFFIC_BYTES else None,
                 "executed_tflops": (info.exec_flops_adjoint if dom == "adjoint" else info.exec_flops_forward) /
                                    (dom_ms * 1e-3) / 1e12,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
