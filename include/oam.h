@@ -407,7 +407,10 @@ oam_status oam_request_footprint(int32_t precision, const oam_sensor *sensor, co
                                  const oam_eir *eir, size_t *bytes);
 oam_status oam_server_create(const oam_server_opts *opts, oam_server **out);
 /* h_s: host signals (py*px*nt floats), h_x_l2 / h_x_l1: host images
- * (py*px*nz floats, may be NULL); all must stay valid until the request ends. */
+ * (py*px*nz floats, may be NULL); all must stay valid until the request ends.
+ * Submit plans the request's device footprint on the host (oam_model_bytes
+ * plus buffers and workspace) and keeps the plan by geometry (the bytes of
+ * sensor, grid and eir), so requests that repeat a geometry skip the planning. */
 oam_status oam_server_submit(oam_server *server, const oam_sensor *sensor, const oam_grid *grid, const oam_eir *eir,
                              const float *h_s, float *h_x_l2, float *h_x_l1, int64_t *request_id);
 oam_status oam_server_poll(oam_server *server, int64_t request_id, oam_request_info *info);

@@ -8,8 +8,9 @@
 // forward: block = (row y, 64 positions, 64-sample time tile); it walks every
 //   tap (b, a) and the depths whose band meets the time tile, staging 16 depths
 //   of the shifted volume row and the packed slab rows in shared memory.
-// adjoint: block = (row y, 64 positions, 16-depth tile); it walks every tap and
-//   the samples of the tile's band union, 64 samples at a time.
+// adjoint: block = (row y, 64 positions, 16-depth tile), 64 threads of 4
+//   positions x 4 depths; it walks every tap and the samples of the tile's band
+//   union, 64 samples at a time.
 //
 // Each output sums up to win^2 x band products (about 3e5 at 61 x 61 taps).
 // One FP32 accumulator for all of them loses about sqrt(n) units in the last
@@ -30,7 +31,7 @@ __global__ void __launch_bounds__(256) k_fwd_fp32(const float *__restrict__ H, f
   const int x0 = blockIdx.x * kPos, y = blockIdx.y, T = blockIdx.z;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int W = 2 * R + 1;
-  __shared__ float Hs[kPos][kDepthTile + 1];
+  __shared__ __align__(16) float Hs[kPos][kDepthTile + 4];  // rows of 16 depths, 16-byte aligned
   __shared__ float4 Ps[kDepthTile][kTimeTile / 4];
   float acc[4][4] = {}, row_acc[4][4], tap_acc[4][4];
   for (int b = -R; b <= R; ++b) {
@@ -64,17 +65,25 @@ __global__ void __launch_bounds__(256) k_fwd_fp32(const float *__restrict__ H, f
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();
+        // four depths per step: 4 + 4 16-byte reads for 64 FMAs, each
+        // accumulator still taking its depths in increasing order
 #pragma unroll
-        for (int kk = 0; kk < kDepthTile; ++kk) {
-          const float4 p = Ps[kk][tx];
+        for (int k4 = 0; k4 < kDepthTile; k4 += 4) {
+          float4 p[4], h[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float h = Hs[4 * ty + i][kk];
-            tap_acc[i][0] = fmaf(h, p.x, tap_acc[i][0]);
-            tap_acc[i][1] = fmaf(h, p.y, tap_acc[i][1]);
-            tap_acc[i][2] = fmaf(h, p.z, tap_acc[i][2]);
-            tap_acc[i][3] = fmaf(h, p.w, tap_acc[i][3]);
-          }
+          for (int u = 0; u < 4; ++u) p[u] = Ps[k4 + u][tx];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) h[i] = *reinterpret_cast<const float4 *>(&Hs[4 * ty + i][k4]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const float hv = u == 0 ? h[i].x : u == 1 ? h[i].y : u == 2 ? h[i].z : h[i].w;
+              tap_acc[i][0] = fmaf(hv, p[u].x, tap_acc[i][0]);
+              tap_acc[i][1] = fmaf(hv, p[u].y, tap_acc[i][1]);
+              tap_acc[i][2] = fmaf(hv, p[u].z, tap_acc[i][2]);
+              tap_acc[i][3] = fmaf(hv, p[u].w, tap_acc[i][3]);
+            }
         }
         __syncthreads();
       }
@@ -99,21 +108,28 @@ __global__ void __launch_bounds__(256) k_fwd_fp32(const float *__restrict__ H, f
   }
 }
 
-__global__ void __launch_bounds__(256) k_adj_fp32(const float *__restrict__ s, float *__restrict__ H, int px, int py,
-                                                  int nz, int nt, int R, const int *__restrict__ tap_orbit, int n_kt,
-                                                  const int *__restrict__ nrange, const long long *__restrict__ off,
-                                                  const float *__restrict__ Q) {
+constexpr int kAdjThreads = 64;
+
+__global__ void __launch_bounds__(kAdjThreads) k_adj_fp32(const float *__restrict__ s, float *__restrict__ H, int px,
+                                                          int py, int nz, int nt, int R,
+                                                          const int *__restrict__ tap_orbit, int n_kt,
+                                                          const int *__restrict__ nrange,
+                                                          const long long *__restrict__ off,
+                                                          const float *__restrict__ Q) {
   const int x0 = blockIdx.x * kPos, y = blockIdx.y, K = blockIdx.z;
-  const int tid = threadIdx.x, p = tid & 63, kq = tid >> 6;
+  // thread: positions pg + 16 i (i < 4) and depths 4 dg + d (d < 4) of the tile
+  const int tid = threadIdx.x, pg = tid & 15, dg = tid >> 4;
   const int W = 2 * R + 1;
   __shared__ float4 Ss[kPos][kTimeTile / 4 + 1];
   __shared__ float4 Qs[kDepthTile][kTimeTile / 4];
-  float acc[4] = {0.f, 0.f, 0.f, 0.f}, row_acc[4], tap_acc[4];
+  float acc[4][4] = {}, row_acc[4][4], tap_acc[4][4];
   for (int b = -R; b <= R; ++b) {
     const int yy = y - b;
     if (yy < 0 || yy >= py) continue;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) row_acc[i] = 0.0f;
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int d = 0; d < 4; ++d) row_acc[i][d] = 0.0f;
     for (int a = -R; a <= R; ++a) {
       const int xs = x0 - a;
       if (xs + kPos <= 0 || xs >= px) continue;
@@ -121,48 +137,65 @@ __global__ void __launch_bounds__(256) k_adj_fp32(const float *__restrict__ s, f
       const int nlo = nrange[2 * oi], nlen = nrange[2 * oi + 1];
       if (nlen <= 0) continue;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) tap_acc[i] = 0.0f;
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) tap_acc[i][d] = 0.0f;
       const float4 *Q4 = reinterpret_cast<const float4 *>(Q + off[oi]);
       for (int nc = 0; nc < nlen; nc += kTimeTile) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int e = tid + 256 * r, pp = e >> 4, j4 = e & 15;
+#pragma unroll 4
+        for (int r = 0; r < kPos * (kTimeTile / 4) / kAdjThreads; ++r) {
+          const int e = tid + kAdjThreads * r, pp = e >> 4, j4 = e & 15;
           const int x = xs + pp, j = nc + 4 * j4;
           Ss[pp][j4] = (x >= 0 && x < px && j < nlen)
                            ? *reinterpret_cast<const float4 *>(s + ((size_t)yy * px + x) * nt + nlo + j)
                            : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        {
-          const int row = tid >> 4, j4 = tid & 15, j = nc + 4 * j4;
+#pragma unroll
+        for (int r = 0; r < kDepthTile * (kTimeTile / 4) / kAdjThreads; ++r) {
+          const int e = tid + kAdjThreads * r, row = e >> 4, j4 = e & 15, j = nc + 4 * j4;
           Qs[row][j4] = (j < nlen) ? Q4[((size_t)row * nlen + j) >> 2] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();
-#pragma unroll
+        // 4 + 4 16-byte reads for 64 FMAs; each accumulator takes its samples
+        // in increasing order
+#pragma unroll 2
         for (int j4 = 0; j4 < kTimeTile / 4; ++j4) {
-          const float4 v = Ss[p][j4];
+          float4 v[4], q[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float4 q = Qs[4 * kq + i][j4];
-            tap_acc[i] = fmaf(v.x, q.x, tap_acc[i]);
-            tap_acc[i] = fmaf(v.y, q.y, tap_acc[i]);
-            tap_acc[i] = fmaf(v.z, q.z, tap_acc[i]);
-            tap_acc[i] = fmaf(v.w, q.w, tap_acc[i]);
-          }
+          for (int i = 0; i < 4; ++i) v[i] = Ss[pg + 16 * i][j4];
+#pragma unroll
+          for (int d = 0; d < 4; ++d) q[d] = Qs[4 * dg + d][j4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+              tap_acc[i][d] = fmaf(v[i].x, q[d].x, tap_acc[i][d]);
+              tap_acc[i][d] = fmaf(v[i].y, q[d].y, tap_acc[i][d]);
+              tap_acc[i][d] = fmaf(v[i].z, q[d].z, tap_acc[i][d]);
+              tap_acc[i][d] = fmaf(v[i].w, q[d].w, tap_acc[i][d]);
+            }
         }
         __syncthreads();
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) row_acc[i] += tap_acc[i];
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) row_acc[i][d] += tap_acc[i][d];
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i] += row_acc[i];
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int d = 0; d < 4; ++d) acc[i][d] += row_acc[i][d];
   }
-  const int x = x0 + p;
-  if (x >= px) return;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int k = K * kDepthTile + 4 * kq + i;
-    if (k < nz) H[((size_t)y * px + x) * nz + k] = acc[i];
+    const int x = x0 + pg + 16 * i;
+    if (x >= px) continue;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int k = K * kDepthTile + 4 * dg + d;
+      if (k < nz) H[((size_t)y * px + x) * nz + k] = acc[i][d];
+    }
   }
 }
 
@@ -182,8 +215,8 @@ oam_status oam::adjoint_fp32(const oam_model *m, const float *s, float *H, cudaS
   const oam_grid &g = m->grid;
   dim3 grid((g.px + kPos - 1) / kPos, g.py, m->n_ktiles);
   ProfScope prof(m, st, false);
-  k_adj_fp32<<<grid, 256, 0, st>>>(s, H, g.px, g.py, g.nz, g.nt, m->R, m->d_tap_orbit, m->n_ktiles, m->d_adj_nrange,
-                                   m->d_adj_off, m->d_adj);
+  k_adj_fp32<<<grid, kAdjThreads, 0, st>>>(s, H, g.px, g.py, g.nz, g.nt, m->R, m->d_tap_orbit, m->n_ktiles,
+                                           m->d_adj_nrange, m->d_adj_off, m->d_adj);
   OAM_LAUNCHED();
   return OAM_OK;
 }

@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -286,6 +287,10 @@ struct oam_server {
   std::deque<int64_t> queue;
   std::map<int64_t, Req> reqs;
   int64_t next_id = 1;
+  // Footprint plans by request geometry (the raw bytes of sensor, grid and
+  // EIR): repeated geometries skip the host planning at submit.
+  std::mutex plan_mu;
+  std::map<std::string, std::pair<oam_status, size_t>> plans;
   size_t reserved = 0, peak_reserved = 0;
   int running = 0, peak_running = 0;
   bool stop = false;
@@ -491,7 +496,25 @@ extern "C" oam_status oam_server_submit(oam_server *S, const oam_sensor *sensor,
                                         int64_t *request_id) {
   if (!S || !sensor || !grid || !eir || !h_s || !request_id) return OAM_ERR_INVALID_ARG;
   oam_server::Req r;
-  r.plan_rc = request_footprint(S->opts.precision, sensor, grid, eir, &r.need);  // host only, outside the lock
+  std::string key(reinterpret_cast<const char *>(sensor), sizeof(oam_sensor));
+  key.append(reinterpret_cast<const char *>(grid), sizeof(oam_grid));
+  key.append(reinterpret_cast<const char *>(eir), sizeof(oam_eir));
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> pl(S->plan_mu);
+    auto it = S->plans.find(key);
+    if (it != S->plans.end()) {
+      r.plan_rc = it->second.first;
+      r.need = it->second.second;
+      cached = true;
+    }
+  }
+  if (!cached) {
+    r.plan_rc = request_footprint(S->opts.precision, sensor, grid, eir, &r.need);  // host only, outside the locks
+    std::lock_guard<std::mutex> pl(S->plan_mu);
+    if (S->plans.size() >= 4096) S->plans.clear();  // bounded
+    S->plans[key] = {r.plan_rc, r.need};
+  }
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->stop) return OAM_ERR_BUSY;
   r.id = S->next_id++;
