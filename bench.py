@@ -356,7 +356,7 @@ def _serve_reference_proc(workdir, threads, cfgs):
 
 
 def run_serve(args):
-    """Served workload (SURVEY C4): requests drawn from a pool of prepared
+    """Served workload: requests drawn from a pool of prepared
     instances (sizes as the batched workload plus occasional 200x200x300
     volumes), submitted at Poisson arrival times to one request server with a
     150 GB device-memory budget.  Requests on small instances (64x64 scans,

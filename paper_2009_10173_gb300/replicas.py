@@ -1,7 +1,7 @@
 """Host logic of multi-process runs: one process per GPU, independent replicas.
 
-The reconstruction of one volume does not shard in this build (every GPU
-runs whole reconstructions), so ranks split independent work items and the
+The reconstruction of one volume is not split across GPUs (every GPU runs
+whole reconstructions), so ranks split independent work items and the
 only collective is the timing reduction (max over ranks).
 """
 
