@@ -52,19 +52,30 @@ __global__ void __launch_bounds__(256) k_fwd_fp32(const float *__restrict__ H, f
 #pragma unroll
         for (int j = 0; j < 4; ++j) tap_acc[i][j] = 0.0f;
       const float4 *P4 = reinterpret_cast<const float4 *>(P + off[oi]);
-      for (int kc = klo; kc < khi; kc += kDepthTile) {
+      // this thread's share of a 16-depth chunk (4 volume values, 4 slab values),
+      // fetched one chunk ahead so the loads run during the previous chunk's FMAs
+      float hv[4];
+      float4 pv;
+      auto fetch = [&](int kc) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const int e = tid + 256 * r, p = e >> 4, kk = e & 15;
           const int x = xs + p, k = kc + kk;
-          Hs[p][kk] = (x >= 0 && x < px && k < khi) ? H[((size_t)yy * px + x) * nz + k] : 0.0f;
+          hv[r] = (x >= 0 && x < px && k < khi) ? H[((size_t)yy * px + x) * nz + k] : 0.0f;
         }
-        {
-          const int row = tid >> 4, c4 = tid & 15;
-          Ps[row][c4] = (kc + row < khi) ? P4[(size_t)(kc - klo + row) * (kTimeTile / 4) + c4]
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int row = tid >> 4, c4 = tid & 15;
+        pv = (kc + row < khi) ? P4[(size_t)(kc - klo + row) * (kTimeTile / 4) + c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      };
+      fetch(klo);
+      for (int kc = klo; kc < khi; kc += kDepthTile) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int e = tid + 256 * r;
+          Hs[e >> 4][e & 15] = hv[r];
         }
+        Ps[tid >> 4][tid & 15] = pv;
         __syncthreads();
+        if (kc + kDepthTile < khi) fetch(kc + kDepthTile);
         // four depths per step: 4 + 4 16-byte reads for 64 FMAs, each
         // accumulator still taking its depths in increasing order
 #pragma unroll
