@@ -74,3 +74,63 @@ def test_two_rank_replicas_on_gloo():
     assert sorted(res[0][0] + res[1][0]) == list(range(10))
     assert res[0][1] != res[1][1]
     assert res[0][2] == res[1][2] == [2.0, 10.0]
+
+
+def test_served_rate_driver_accounts_every_request(monkeypatch):
+    """serve.run_rate against a stand-in for the C server (no GPU): every
+    request is submitted once into its own preallocated output pair, latency
+    from arrival is never below latency from submission, and the deferred
+    checks see each checked instance's requests with their own images."""
+    import types
+
+    import numpy as np
+
+    from paper_2009_10173_gb300 import serve
+
+    submitted = []
+
+    class Info:
+        def __init__(self, rid):
+            self.state, self.latency_s = 2, 0.001 * rid
+
+    def submit(server, s, g, e, h_s, x2, x1):
+        submitted.append((x2.data_ptr(), x1.data_ptr()))
+        rid = len(submitted)
+        x2.fill_(float(rid))  # the "result" names its request
+        x1.fill_(-float(rid))
+        return rid
+
+    class Stats:
+        peak_running, peak_reserved_bytes = 3, 5e9
+
+    fake = types.SimpleNamespace(oam_server_submit=submit, oam_server_poll=lambda sv, rid: Info(rid),
+                                 oam_server_wait=lambda sv, rid, t: 0, OAM_OK=0,
+                                 oam_server_stats=lambda sv: Stats())
+    monkeypatch.setattr(serve, "B", fake)
+
+    class Inst:
+        structs = (None, None, None)
+        h_s = None
+
+        def new_outputs(self):
+            return torch.zeros(3), torch.zeros(3)
+
+    pool = [Inst() for _ in range(4)]
+    seen = []
+
+    def check(pick, x2, x1):
+        seen.append((pick, float(x2[0]), float(x1[0])))
+        return {"e": float(x2[0])}
+
+    out = serve.run_rate(None, pool, 5000.0, 60, seed=3, check=check, check_picks={1, 2})
+    assert out["requests"] == out["completed"] == 60 and out["failed"] == 0
+    assert out["output_allocs"] == 0
+    assert len(set(submitted)) == 60  # one output pair per request
+    assert out["p50_latency_from_arrival_s"] >= out["p50_latency_s"]
+    picks = np.random.Generator(np.random.PCG64(3))
+    picks.exponential(1 / 5000.0, 60)
+    expect = picks.integers(0, 4, 60)
+    want = sorted((int(j), float(i + 1)) for i, j in enumerate(expect) if j in (1, 2))
+    assert sorted((p, r) for p, r, _ in seen) == want
+    assert all(r == -q for _, r, q in seen)
+    assert out["checked"] == len(want)
