@@ -344,8 +344,9 @@ oam_status oam_model_set_tiles(oam_model *model, int32_t direction, int32_t fold
  * output; a tile that wraps w scan rows stages 128 + (w + 2) R rows, so it
  * needs w + 2 <= 128 / R and more shared memory), 0 = automatic (the scan grid
  * unless it leaves a shallower item ring).  get returns the tiling in use (1
- * or 2); set returns OAM_ERR_UNSUPPORTED and leaves the model unchanged when
- * the tiling does not fit.  oam_model_autotune searches it too.  Results do not
+ * or 2); set returns OAM_ERR_INVALID_ARG for other values and
+ * OAM_ERR_UNSUPPORTED when the tiling does not fit, leaving the model
+ * unchanged in both cases.  oam_model_autotune searches it too.  Results do not
  * depend on it. */
 oam_status oam_model_get_tiling(const oam_model *model, int32_t direction, int32_t *tiling);
 oam_status oam_model_set_tiling(oam_model *model, int32_t direction, int32_t tiling);
