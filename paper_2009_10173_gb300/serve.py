@@ -71,13 +71,14 @@ def make_server(budget_bytes=150 * 10 ** 9, slots=8, precision=B.OAM_PREC_BF16X3
 
 
 def run_rate(server, pool, rate, n_requests, seed, timeout_s=3600.0, check=None, check_picks=None,
-             buffers_per_instance=None):
+             buffers_per_instance=None, host_bytes=48e9):
     """Submit n_requests at Poisson arrival times (rate per second), wait for all.
 
     Output images go into pinned host buffers allocated before the clock
     starts: ``buffers_per_instance`` pairs per prepared instance, or by default
     one pair per request of the schedule (no allocation while the clock runs,
-    at the cost of host memory for every request's images).  A pair is reused
+    at the cost of host memory for every request's images; scaled down, to at
+    least two pairs per instance, when that would exceed ``host_bytes``).  A pair is reused
     once the request that held it has completed, and a new pair is allocated
     only when every pair of that instance is still in flight (counted in
     ``output_allocs``).  Latency is reported from submission (the
@@ -91,9 +92,15 @@ def run_rate(server, pool, rate, n_requests, seed, timeout_s=3600.0, check=None,
     gaps = rng.exponential(1.0 / rate, n_requests)
     picks = rng.integers(0, len(pool), n_requests)
     counts = np.bincount(picks, minlength=len(pool))
-    free = {j: [inst.new_outputs() for _ in range(int(counts[j]) if buffers_per_instance is None
-                                                  else min(int(counts[j]), buffers_per_instance))]
-            for j, inst in enumerate(pool)}
+    if buffers_per_instance is None:
+        pairs = [int(c) for c in counts]
+        pair_bytes = [8 * int(np.prod(getattr(inst, "vol_shape", (0,)))) for inst in pool]
+        total = sum(n * b for n, b in zip(pairs, pair_bytes))
+        if total > host_bytes:
+            pairs = [min(n, max(2, int(n * host_bytes / total))) for n in pairs]
+    else:
+        pairs = [min(int(c), buffers_per_instance) for c in counts]
+    free = {j: [inst.new_outputs() for _ in range(pairs[j])] for j, inst in enumerate(pool)}
     busy = {j: [] for j in range(len(pool))}  # (request id, submit lag, x2, x1), oldest first
     lat, lat_arrival, to_check = [], [], []
     state = {"failed": 0, "allocs": 0}

@@ -134,3 +134,37 @@ def test_served_rate_driver_accounts_every_request(monkeypatch):
     assert sorted((p, r) for p, r, _ in seen) == want
     assert all(r == -q for _, r, q in seen)
     assert out["checked"] == len(want)
+
+
+def test_served_rate_driver_bounds_its_host_buffers(monkeypatch):
+    """With a host-memory bound below one pair per request, the driver
+    preallocates fewer pairs (at least two per instance) and reuses pairs of
+    completed requests; every request still completes."""
+    import types
+
+    from paper_2009_10173_gb300 import serve
+
+    class Info:
+        state, latency_s = 2, 0.001
+
+    fake = types.SimpleNamespace(oam_server_submit=lambda *a: 1, oam_server_poll=lambda sv, rid: Info(),
+                                 oam_server_wait=lambda sv, rid, t: 0, OAM_OK=0,
+                                 oam_server_stats=lambda sv: types.SimpleNamespace(peak_running=1,
+                                                                                   peak_reserved_bytes=0))
+    monkeypatch.setattr(serve, "B", fake)
+    made = []
+
+    class Inst:
+        structs = (None, None, None)
+        h_s = None
+        vol_shape = (10, 10, 10)  # 8 KB per output pair
+
+        def new_outputs(self):
+            made.append(1)
+            return torch.zeros(3), torch.zeros(3)
+
+    pool = [Inst(), Inst()]
+    out = serve.run_rate(None, pool, 5000.0, 40, seed=5, host_bytes=8000 * 6)
+    assert out["completed"] == 40 and out["failed"] == 0
+    assert len(made) - out["output_allocs"] <= 8  # preallocated: at most 6 pairs, at least 2 per instance
+    assert len(made) - out["output_allocs"] >= 4
